@@ -1,0 +1,360 @@
+"""Benchmark: per-tick k-NN spatial join on 1M moving objects, k = 16.
+
+Workload (one "step" = one tick = every hot-path stage): 1,000,000 objects
+uniform in [0,1)^2 (seed 0); each tick every object moves by N(0, 1e-3) per
+coordinate (clamped) and every object issues a k=16 query at its own position.
+Ten ticks are generated once and stay resident in HBM; steps cycle through
+them.  The L2 cache is flushed (a 256 MiB write) between timed steps, outside
+the timed events.
+
+Prints one JSON line.  ``--impl reference`` times the CPU oracle (brute force
+on the host cores) on a bounded sample of the same workload instead.
+Under torchrun each rank runs an independent replica of the workload on its
+own GPU ("replicas only": one world does not shard); value = all ranks'
+queries / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "queries/s (1M obj, k=16) + p99 tick latency: served vs plain, ids exact"
+N_OBJ = 1_000_000
+K = 16
+N_TICKS = 10
+WORKLOAD = "uniform 1M objects, k=16, all objects query, N(0,1e-3) moves, 10 ticks cycled"
+# Algorithmic bytes per query of the expansion kernel (query 12 B + each object
+# read once amortised 12 B * n/q + k results of 8 B).
+ALGO_BYTES_PER_QUERY = 12 + 12 * N_OBJ / N_OBJ + 8 * K
+FALLBACK_HBM_GBS = 6800.0
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:  # noqa: BLE001
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:  # noqa: BLE001
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:  # noqa: BLE001
+                self.proc.kill()
+                out = ""
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(workload, target_s: float = 12.0):
+    """Time the oracle (brute force over all objects, all host cores) on a bounded
+    sample of tick 1's queries; returns the cpu_baseline object."""
+    import numpy as np
+
+    import oracle
+    t = workload.ticks[0]
+    x, y, _ = oracle.apply_updates(workload.x0, workload.y0, t.upd_id, t.upd_x, t.upd_y)
+    cores = os.cpu_count() or 1
+    probe = min(t.q_id.shape[0], max(256, 32 * cores))
+    t0 = time.perf_counter()
+    oracle.knn(x, y, t.q_id[:probe], t.k)
+    dt = time.perf_counter() - t0
+    count = int(min(t.q_id.shape[0], max(probe, probe * target_s / max(dt, 1e-3))))
+    rows = np.linspace(0, t.q_id.shape[0] - 1, count).astype(np.int64)
+    t0 = time.perf_counter()
+    oracle.knn(x, y, t.q_id[rows], t.k)
+    dt = time.perf_counter() - t0
+    return {"value": count / dt, "unit": "queries/s", "cores": cores, "kind": "oracle",
+            "sample": f"{count} of tick 1's {t.q_id.shape[0]} queries (evenly spaced), "
+                      f"brute force over all {workload.n} objects, {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_1412_6170_gb300 import synth
+    w = synth.plain_uniform_moving(n=N_OBJ, k=K, ticks=1, seed=0)
+    import numpy as np
+
+    import oracle
+    t = w.ticks[0]
+    x, y, _ = oracle.apply_updates(w.x0, w.y0, t.upd_id, t.upd_x, t.upd_y)
+    cores = os.cpu_count() or 1
+    sample = max(64, 16 * cores)
+    rows = np.linspace(0, N_OBJ - 1, sample).astype(np.int64)
+    for _ in range(args.warmup):
+        oracle.knn(x, y, t.q_id[rows[:cores]], K)
+    times = []
+    for s in range(args.steps):
+        r = rows if s % 2 == 0 else rows[::-1]
+        t0 = time.perf_counter()
+        oracle.knn(x, y, t.q_id[r], K)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = sample * args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_objects": N_OBJ, "k": K,
+                       "path": "cpu oracle (brute force)",
+                       "step": f"{sample} sampled queries of one tick"},
+            "cpu_baseline": {"value": value, "unit": "queries/s", "cores": cores,
+                             "kind": "oracle",
+                             "sample": f"{sample} evenly spaced queries per step over "
+                                       f"{N_OBJ} objects"},
+            "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_1412_6170_gb300 import knnq, synth
+    import __graft_entry__
+
+    rank, world_size, local = dist_env()
+    dist = None
+    if world_size > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        __graft_entry__.build()
+    if dist is not None:
+        dist.barrier()
+    knnq.lib()
+
+    wl = synth.plain_uniform_moving(n=N_OBJ, k=K, ticks=N_TICKS, seed=0)
+    stream = torch.cuda.current_stream()
+    x0 = torch.from_numpy(wl.x0).to(dev)
+    y0 = torch.from_numpy(wl.y0).to(dev)
+    ids_d = torch.from_numpy(wl.ticks[0].upd_id).to(dev)          # 0..n-1, shared by ticks
+    ux = [torch.from_numpy(t.upd_x).to(dev) for t in wl.ticks]
+    uy = [torch.from_numpy(t.upd_y).to(dev) for t in wl.ticks]
+    qid = ids_d
+    out_ids = torch.empty((N_OBJ, K), dtype=torch.int32, device=dev)
+    out_d2 = torch.empty((N_OBJ, K), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    world = knnq.World(x0, y0, k_max=K, max_queries=N_OBJ)
+    world.set_profiling(True)
+
+    def tick(i):
+        world.tick(K, qid, ids_d, ux[i % N_TICKS], uy[i % N_TICKS], out_ids=out_ids,
+                   out_d2=out_d2)
+
+    for i in range(args.warmup):
+        tick(i)
+    torch.cuda.synchronize()
+    st, bits = world.status()
+    if st != knnq.KNN_OK:
+        raise RuntimeError(f"device status {st} bits {bits} after warm-up")
+
+    # quick exactness spot check of the last warm-up tick against the oracle
+    spot = None
+    if rank == 0 and not args.no_check:
+        import oracle
+        t = wl.ticks[(args.warmup - 1) % N_TICKS]
+        rows = np.linspace(0, N_OBJ - 1, 512).astype(np.int64)
+        x, y, _ = oracle.apply_updates(wl.x0, wl.y0, t.upd_id, t.upd_x, t.upd_y)
+        rid, rd2, _ = oracle.knn(x, y, t.q_id[rows], K)
+        gid = out_ids.cpu().numpy()[rows]
+        gd2 = out_d2.cpu().numpy()[rows]
+        spot = bool(np.array_equal(gid, rid) and np.array_equal(gd2.view(np.uint32),
+                                                                rd2.view(np.uint32)))
+        if not spot:
+            raise RuntimeError("GPU result differs from the oracle on the spot check")
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    stage_sums = None
+    launches0 = world.launches()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        wall0 = time.perf_counter()
+        for s in range(args.steps):
+            flush.zero_()
+            a, b = ev[s]
+            a.record(stream)
+            tick(args.warmup + s)
+            b.record(stream)
+            b.synchronize()
+            st_ms = world.stage_times()
+            stage_sums = {k: stage_sums.get(k, 0.0) + v for k, v in st_ms.items()} \
+                if stage_sums else dict(st_ms)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    if dist is not None:
+        dist.barrier()
+    launches = world.launches() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    st, bits = world.status()
+    if st != knnq.KNN_OK:
+        raise RuntimeError(f"device status {st} bits {bits} after timed steps")
+
+    # end-to-end through the public host-buffer API (pinned host arrays)
+    import ctypes
+    h_uid = torch.from_numpy(wl.ticks[0].upd_id).pin_memory()
+    h_ux = [torch.from_numpy(t.upd_x).pin_memory() for t in wl.ticks[:2]]
+    h_uy = [torch.from_numpy(t.upd_y).pin_memory() for t in wl.ticks[:2]]
+    h_oid = torch.empty((N_OBJ, K), dtype=torch.int32).pin_memory()
+    h_od = torch.empty((N_OBJ, K), dtype=torch.float32).pin_memory()
+    vp = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+    e2e_steps = max(3, min(args.steps, 10))
+    for i in range(2):  # warm-up (first call allocates the staging buffers)
+        knnq.knn_tick_host(world.handle, vp(h_uid), vp(h_ux[i]), vp(h_uy[i]), N_OBJ,
+                           vp(h_uid), None, None, N_OBJ, K, vp(h_oid), vp(h_od),
+                           stream.cuda_stream)
+    torch.cuda.synchronize()
+    e2e_t = []
+    for s in range(e2e_steps):
+        t0 = time.perf_counter()
+        knnq.knn_tick_host(world.handle, vp(h_uid), vp(h_ux[s % 2]), vp(h_uy[s % 2]), N_OBJ,
+                           vp(h_uid), None, None, N_OBJ, K, vp(h_oid), vp(h_od),
+                           stream.cuda_stream)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_total = sum(e2e_t)
+    if dist is not None:
+        t = torch.tensor([e2e_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+
+    world.close()
+    if rank != 0:
+        return
+    n_gpus = world_size
+    value = n_gpus * N_OBJ * args.steps / (total_ms / 1e3)
+    srt = sorted(step_ms)
+    p99 = srt[min(len(srt) - 1, int(round(0.99 * (len(srt) - 1))))]
+    p50 = statistics.median(step_ms)
+    exp_ms = stage_sums["expand"] / args.steps
+    hbm, hbm_kind = peaks()
+    achieved = ALGO_BYTES_PER_QUERY * N_OBJ / (exp_ms / 1e3) / 1e9
+    traffic = None
+    line = {
+        "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": n_gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_objects": N_OBJ, "k": K, "queries_per_tick": N_OBJ,
+                   "path": "plain (one knn_tick per tick)", "l2": "flushed between steps",
+                   "parallelism": "replicas" if n_gpus > 1 else "single GPU"},
+        "p50_tick_ms": p50, "p99_tick_ms": p99,
+        "stages_ms": {k: v / args.steps for k, v in stage_sums.items()},
+        "roofline": {"kernel": "k_expand", "bound": "hbm", "achieved": achieved, "peak": hbm,
+                     "peak_kind": hbm_kind, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": traffic,
+                     "algorithmic_bytes_per_query": ALGO_BYTES_PER_QUERY},
+        "e2e": {"value": n_gpus * N_OBJ * e2e_steps / e2e_total, "unit": "queries/s",
+                "h2d_bytes_per_step": N_OBJ * 12 + N_OBJ * 4,
+                "d2h_bytes_per_step": N_OBJ * K * 8,
+                "api": "knn_tick_host (pinned host buffers, synchronous)"},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "exact_spot_check": spot,
+        "wall_s": wall,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-check", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 1:
+        args.warmup = 1
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

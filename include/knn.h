@@ -1,0 +1,179 @@
+/*
+ * knn.h -- C ABI of the GB300-native repeated k-NN library.
+ *
+ * Repeated k-NN queries over moving objects (Lettich, Orlando, Silvestri,
+ * "Manycore processing of repeated k-NN queries over massive moving objects
+ * observations", arXiv 1412.6170).  A "world" holds the last known positions
+ * of n moving objects on one GPU.  Each tick applies a batch of position
+ * updates and answers a batch of k-NN queries against the updated positions
+ * (the paper's iterated batch processing, Section 2.3):
+ *
+ *   1. updates are applied in array order, the last one per object wins
+ *      (Section 2.2, timeslice batching);
+ *   2. a PR-quadtree over the positions is rebuilt on the device: Morton codes
+ *      at level max_depth, a radix sort, and a leaf split at leaf_capacity
+ *      (Section 4.1.1);
+ *   3. every query expands over the quadtree leaves around it, keeping its k
+ *      best objects, until the disc of its k-th distance is covered by the
+ *      leaves already visited (Sections 4.2.1-4.2.2);
+ *   4. results are written in the caller's query order, one row of k per query
+ *      (Section 3.3.2, linear result layout).
+ *
+ * Result definition (Def. 1, Section 2.1): for query i issued by object s
+ * (q_id[i] = s, or -1 for an anonymous query) and centred at c, every object
+ * j != s is ranked by the key (d(c, o_j), j) where
+ *     d = dx*dx + dy*dy,  dx = c.x - x_j,  dy = c.y - y_j,
+ * evaluated in IEEE binary32 with every operation rounded to nearest-even and
+ * no fused multiply-add.  Row i holds the k smallest keys, ascending, padded
+ * with (id -1, d2 +inf) when fewer than k objects are eligible.  The output is
+ * unique, so it is bit-exact against any correct implementation.
+ *
+ * Conventions
+ *  - All sizes are int64_t.  Object ids are 0..n-1 (int32).  n <= 2^30.
+ *  - Pointers named *_dev are device pointers of the world's GPU; the caller
+ *    owns them and keeps inputs valid (and outputs unread) until the stream
+ *    reaches the end of the call.  *_host are host pointers.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  knn_tick and knn_world_* calls on one world must be ordered on
+ *    the device (one stream, or event-ordered streams): the world owns one set
+ *    of scratch buffers.
+ *  - Host-detectable errors return immediately and launch nothing.  Errors
+ *    that only the device can see (an update id outside [0, n), a non-finite
+ *    coordinate, an invalid query) never fault: the offending entry is
+ *    skipped (an invalid query gets a padded row), an error bit is set in
+ *    the world, and knn_tick_status reports it.
+ *  - knn_last_error() returns a thread-local message for the last failure.
+ *  - Every device-side wait is bounded; running out sets KNN_ERR_TIMEOUT.
+ */
+#ifndef KNN_H
+#define KNN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct knn_world_s *knn_world;
+
+typedef enum {
+    KNN_OK = 0,
+    KNN_ERR_INVALID = -1,      /* bad argument, detected on the host */
+    KNN_ERR_OOM = -2,          /* device allocation failed */
+    KNN_ERR_CUDA = -3,         /* a CUDA runtime call failed */
+    KNN_ERR_TIMEOUT = -4,      /* a bounded device-side wait ran out */
+    KNN_ERR_ADMISSION = -5,    /* reserved for request admission */
+    KNN_ERR_DEVICE_INPUT = -6  /* the device skipped invalid input entries */
+} knn_status;
+
+/* World description.  The domain is the square [x0, x0+side) x [y0, y0+side)
+ * that the virtual full quadtree covers (the paper's MBR G, Section 3.3).
+ * Positions outside it are legal: they fall into the border cells for the
+ * index, and distances always use the true coordinates. */
+typedef struct {
+    float x0, y0, side;      /* side > 0 and finite */
+    int32_t leaf_capacity;   /* th_quad: max objects per leaf; 0 = automatic; <= 4096 */
+    int32_t max_depth;       /* l_max in [1, 16]; 0 = 16 */
+    int32_t k_max;           /* largest k a tick may ask for, in [1, 64] */
+    int64_t max_queries;     /* largest n_q a tick may pass, >= 0 */
+} knn_world_desc;
+
+/* Create a world of n objects (ids 0..n-1) at the positions x_dev[i], y_dev[i]
+ * (device arrays of n floats, copied; all must be finite).  Allocates every
+ * device buffer the ticks need (sized from n, k_max, max_queries), so ticks
+ * never allocate.  May synchronize `stream`.  Returns KNN_ERR_INVALID for a
+ * bad description, n outside [1, 2^30] or a non-finite position. */
+knn_status knn_world_create(const knn_world_desc *desc, const float *x_dev,
+                            const float *y_dev, int64_t n, void *stream,
+                            knn_world *out);
+
+/* One tick (Sections 2.2-2.3 and 4): apply n_upd updates (upd_id[i] moves to
+ * (upd_x[i], upd_y[i]); later entries win; invalid entries are skipped), then
+ * answer n_q k-NN queries.  Query i is issued by q_id[i] (-1 = anonymous) and
+ * centred at (q_x[i], q_y[i]), or, when q_x and q_y are both NULL, at its
+ * issuer's post-update position.  Writes out_ids_dev[i*k + r] and
+ * out_d2_dev[i*k + r], r < k (row-major, caller order).  Asynchronous on
+ * `stream`; performs no host synchronisation and no allocation.
+ * KNN_ERR_INVALID for: k outside [1, k_max], n_q outside [0, max_queries],
+ * n_upd outside [0, 2^31), a NULL array whose count is non-zero, or only one
+ * of q_x / q_y given. */
+knn_status knn_tick(knn_world w, const int32_t *upd_id_dev, const float *upd_x_dev,
+                    const float *upd_y_dev, int64_t n_upd, const int32_t *q_id_dev,
+                    const float *q_x_dev, const float *q_y_dev, int64_t n_q, int32_t k,
+                    int32_t *out_ids_dev, float *out_d2_dev, void *stream);
+
+/* The same tick with every array in host memory (pageable or pinned): the
+ * inputs are copied to world-owned device staging buffers, the tick runs on
+ * `stream`, the results are copied back, and the call returns after the
+ * stream has finished.  The first call that needs larger staging buffers
+ * allocates them (so that call is not allocation-free). */
+knn_status knn_tick_host(knn_world w, const int32_t *upd_id_host, const float *upd_x_host,
+                         const float *upd_y_host, int64_t n_upd, const int32_t *q_id_host,
+                         const float *q_x_host, const float *q_y_host, int64_t n_q,
+                         int32_t k, int32_t *out_ids_host, float *out_d2_host,
+                         void *stream);
+
+/* Waits for the world's last tick and reports device-detected problems since
+ * the previous call: KNN_ERR_TIMEOUT, then KNN_ERR_DEVICE_INPUT (skipped
+ * updates, non-finite coordinates, invalid queries), else KNN_OK.  Clears the
+ * recorded bits.  If `bits_out` is non-NULL it receives the raw bit set
+ * (1 = bad update id, 2 = non-finite update, 4 = invalid query, 8 = timeout). */
+knn_status knn_tick_status(knn_world w, uint32_t *bits_out);
+
+/* Release every device buffer of the world (synchronizes its device). */
+knn_status knn_world_destroy(knn_world w);
+
+/* Thread-local description of the last error returned on this thread. */
+const char *knn_last_error(void);
+
+/* ---- tuning and introspection ------------------------------------------ */
+
+/* Index and expansion parameters; none of them changes any result.
+ * leaf_capacity: th_quad (Section 4.1.1), 1..4096.
+ * grid_level: level G of the uniform cell map over the leaves (the paper's
+ *   z_map, Section 4.1.1); leaves are never coarser than G.  1..10.
+ * packet_level: queries are packed 32 to a warp within one cell of this
+ *   level (<= grid_level).
+ * Any field set to 0 keeps (or restores) the automatic choice. */
+typedef struct {
+    int32_t leaf_capacity;
+    int32_t grid_level;
+    int32_t packet_level;
+    int32_t reserved;
+} knn_tuning;
+
+knn_status knn_world_set_tuning(knn_world w, const knn_tuning *t);
+/* The parameters the next tick with query count n_q and k will use. */
+knn_status knn_world_get_tuning(knn_world w, int64_t n_q, int32_t k, knn_tuning *out);
+
+/* Copy the leaves built by the last tick (non-empty PR-quadtree leaves in
+ * Morton order, never coarser than grid_level) into caller device buffers of
+ * `cap` entries: level, code z at that level, start and count in the sorted
+ * object order; sorted_ids_dev (n entries, may be NULL) receives that order.
+ * Synchronizes `stream`; *m_host receives the number of leaves. */
+knn_status knn_world_leaves(knn_world w, int32_t *level_dev, uint32_t *z_dev,
+                            int32_t *start_dev, int32_t *count_dev,
+                            int32_t *sorted_ids_dev, int64_t cap, int64_t *m_host,
+                            void *stream);
+
+/* Copy the current positions (after the last tick's updates) into caller
+ * device arrays of n floats; a world re-created from them answers every later
+ * tick identically (checkpoint / resume). */
+knn_status knn_world_positions(knn_world w, float *x_dev, float *y_dev, void *stream);
+
+/* Number of CUDA kernels this world's ticks have launched so far (host-side
+ * count; memsets and copies are not kernels and are not counted). */
+knn_status knn_world_launches(knn_world w, int64_t *count);
+
+/* Per-stage device times of ticks.  When enabled, each tick records CUDA
+ * events around its stages on its stream; knn_world_stage_times synchronizes
+ * and writes up to n_stages milliseconds for the last tick.  Stage names come
+ * from knn_stage_name (NULL past the last stage). */
+knn_status knn_world_set_profiling(knn_world w, int32_t enable);
+knn_status knn_world_stage_times(knn_world w, float *ms_host, int32_t n_stages);
+const char *knn_stage_name(int32_t i);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KNN_H */

@@ -1,0 +1,458 @@
+// C ABI (include/knn.h): argument validation, the world's device arena, the
+// order of the per-tick stages, host-buffer ticks, status and introspection.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "knn.h"
+#include "knn_internal.h"
+
+using knnq::Plan;
+using knnq::World;
+
+struct knn_world_s {
+    World w;
+};
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+knn_status fail(knn_status st, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+knn_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(KNN_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+const char *kStageNames[] = {"update", "keys+sort", "leaves", "query order", "packets",
+                             "expand"};
+constexpr int kNumStages = 6;
+
+int round_log4(double v) {
+    if (v <= 1.0) return 0;
+    return (int)std::floor(std::log(v) / std::log(4.0) + 0.5);
+}
+
+int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// Automatic index parameters (none changes a result):
+//  leaf capacity th = 2k in [8, 256] (the paper ties th_quad to k);
+//  grid level G with about th/2 objects per cell, so most leaves are cells;
+//  packet level with about 48 queries per cell.
+Plan make_plan(const World &w, int64_t n_q, int k) {
+    Plan p{};
+    p.L = w.L;
+    p.passes = (2 * p.L + 7) / 8;
+    p.th = w.tuning.leaf_capacity > 0 ? w.tuning.leaf_capacity : clampi(2 * k, 8, 256);
+    p.th = clampi(p.th, 1, knnq::kMaxLeafCapacity);
+    const int gmax = p.L < knnq::kMaxGridLevel ? p.L : knnq::kMaxGridLevel;
+    int G = w.tuning.grid_level > 0 ? w.tuning.grid_level
+                                    : round_log4(2.0 * (double)w.n / (double)p.th);
+    p.G = clampi(G, 1, gmax);
+    int Gp = w.tuning.packet_level > 0 ? w.tuning.packet_level
+                                       : round_log4((double)(n_q > 0 ? n_q : 1) / 48.0);
+    p.Gp = clampi(Gp, 0, p.G);
+    return p;
+}
+
+size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
+
+struct Carve {
+    char *base;
+    size_t off = 0;
+    template <class T>
+    T *take(size_t count) {
+        T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+        off += align_up(sizeof(T) * (count ? count : 1));
+        return p;
+    }
+};
+
+// Lay out (base == nullptr: size only) every tick buffer in one arena.
+size_t carve(World &w, char *base) {
+    const int64_t n = w.n, R = w.max_rows(), Q = w.desc.max_queries;
+    const int64_t ncell = (1ll << (2 * knnq::kMaxGridLevel)) + 2;
+    const int64_t sort_tiles = (R + knnq::kSortTile - 1) / knnq::kSortTile;
+    int64_t status = sort_tiles * 256;
+    const int64_t others[] = {(n + knnq::kLeafTile - 1) / knnq::kLeafTile,
+                              (n + 1 + knnq::kScanTile - 1) / knnq::kScanTile,
+                              (ncell + knnq::kScanTile - 1) / knnq::kScanTile};
+    for (int64_t o : others) status = status > o ? status : o;
+    Carve c{base};
+    w.px = c.take<float>(n);
+    w.py = c.take<float>(n);
+    w.stamp = c.take<unsigned long long>(n);
+    w.key[0] = c.take<uint32_t>(R);
+    w.key[1] = c.take<uint32_t>(R);
+    w.val[0] = c.take<int32_t>(R);
+    w.val[1] = c.take<int32_t>(R);
+    w.xs = c.take<float>(n);
+    w.ys = c.take<float>(n);
+    w.sid = c.take<int32_t>(n);
+    w.inv = c.take<int32_t>(n);
+    w.bstart = c.take<int32_t>(n + 1);
+    w.bcode = c.take<uint32_t>(n);
+    w.blevel = c.take<uint8_t>(n);
+    w.baabb = c.take<float4>(n);
+    w.cb = c.take<int32_t>(ncell);
+    w.qcnt = c.take<int32_t>(n + 1);
+    w.qs_x = c.take<float>(Q);
+    w.qs_y = c.take<float>(Q);
+    w.qs_id = c.take<int32_t>(Q);
+    w.qs_orig = c.take<int32_t>(Q);
+    w.qs_key = c.take<uint32_t>(Q);
+    w.qcs = c.take<int32_t>(ncell);
+    w.npk = c.take<int32_t>(ncell);
+    w.pk_off = c.take<int32_t>(ncell);
+    w.pk_start = c.take<int32_t>(Q + Q / 32 + 2);
+    w.pk_len = c.take<int32_t>(Q + Q / 32 + 2);
+    w.status = c.take<uint64_t>(status);
+    w.status_words = (size_t)status;
+    w.hist = c.take<uint32_t>(4 * 256);
+    w.counters = c.take<uint32_t>(knnq::kNumCounters);
+    w.scalars = c.take<int32_t>(knnq::kNumScalars);
+    w.err = c.take<uint32_t>(4);
+    return c.off;
+}
+
+void release(World &w) {
+    if (w.arena) cudaFree(w.arena);
+    if (w.stage) cudaFree(w.stage);
+    for (int i = 0; i <= knnq::kMaxStages; ++i)
+        if (w.ev[i]) cudaEventDestroy(w.ev[i]);
+    w.arena = nullptr;
+    w.stage = nullptr;
+}
+
+void mark(World &w, int i, cudaStream_t s) {
+    if (w.profiling && i <= knnq::kMaxStages) {
+        cudaEventRecord(w.ev[i], s);
+        w.n_stage_events = i + 1;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *knn_last_error(void) { return g_err; }
+
+const char *knn_stage_name(int32_t i) {
+    return (i >= 0 && i < kNumStages) ? kStageNames[i] : nullptr;
+}
+
+knn_status knn_world_create(const knn_world_desc *desc, const float *x_dev, const float *y_dev,
+                            int64_t n, void *stream, knn_world *out) {
+    if (!desc || !out) return fail(KNN_ERR_INVALID, "knn_world_create: NULL desc or out");
+    *out = nullptr;
+    if (!(desc->side > 0.f) || !std::isfinite(desc->side) || !std::isfinite(desc->x0) ||
+        !std::isfinite(desc->y0))
+        return fail(KNN_ERR_INVALID, "knn_world_create: domain must be finite with side > 0");
+    if (n < 1 || n > (1ll << 30))
+        return fail(KNN_ERR_INVALID, "knn_world_create: n=%lld outside [1, 2^30]", (long long)n);
+    if (desc->k_max < 1 || desc->k_max > knnq::kMaxK)
+        return fail(KNN_ERR_INVALID, "knn_world_create: k_max=%d outside [1, 64]", desc->k_max);
+    if (desc->max_depth < 0 || desc->max_depth > 16)
+        return fail(KNN_ERR_INVALID, "knn_world_create: max_depth=%d outside [0, 16]",
+                    desc->max_depth);
+    if (desc->leaf_capacity < 0 || desc->leaf_capacity > knnq::kMaxLeafCapacity)
+        return fail(KNN_ERR_INVALID, "knn_world_create: leaf_capacity=%d outside [0, 4096]",
+                    desc->leaf_capacity);
+    if (desc->max_queries < 0 || desc->max_queries > (1ll << 30))
+        return fail(KNN_ERR_INVALID, "knn_world_create: max_queries outside [0, 2^30]");
+    if (!x_dev || !y_dev) return fail(KNN_ERR_INVALID, "knn_world_create: NULL positions");
+
+    knn_world_s *h = new (std::nothrow) knn_world_s();
+    if (!h) return fail(KNN_ERR_OOM, "knn_world_create: host allocation failed");
+    World &w = h->w;
+    cudaGetDevice(&w.device);
+    w.desc = *desc;
+    w.n = n;
+    w.L = desc->max_depth > 0 ? desc->max_depth : 16;
+    w.scale = (float)(1u << w.L) / desc->side;
+    w.tuning.leaf_capacity = desc->leaf_capacity;
+    cudaStream_t s = (cudaStream_t)stream;
+
+    w.arena_bytes = carve(w, nullptr);
+    cudaError_t e = cudaMalloc(&w.arena, w.arena_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return fail(KNN_ERR_OOM, "knn_world_create: cudaMalloc(%zu) failed: %s", w.arena_bytes,
+                    cudaGetErrorString(e));
+    }
+    carve(w, static_cast<char *>(w.arena));
+    cudaMemsetAsync(w.stamp, 0, sizeof(unsigned long long) * (size_t)n, s);
+    cudaMemsetAsync(w.err, 0, 16, s);
+    cudaMemsetAsync(w.scalars, 0, sizeof(int32_t) * knnq::kNumScalars, s);
+    cudaMemcpyAsync(w.px, x_dev, sizeof(float) * (size_t)n, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(w.py, y_dev, sizeof(float) * (size_t)n, cudaMemcpyDeviceToDevice, s);
+    knnq::launch_validate_positions(w.px, w.py, n, w.err + 1, s);
+    uint32_t bad = 0;
+    cudaMemcpyAsync(&bad, w.err + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        release(w);
+        delete h;
+        return cuda_fail(e, "knn_world_create");
+    }
+    if (bad) {
+        release(w);
+        delete h;
+        return fail(KNN_ERR_INVALID, "knn_world_create: non-finite initial position");
+    }
+    cudaMemsetAsync(w.err, 0, 16, s);
+    w.last_stream = s;
+    *out = h;
+    return KNN_OK;
+}
+
+knn_status knn_world_destroy(knn_world h) {
+    if (!h) return fail(KNN_ERR_INVALID, "knn_world_destroy: NULL world");
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(h->w.device);
+    cudaDeviceSynchronize();
+    release(h->w);
+    cudaSetDevice(prev);
+    delete h;
+    return KNN_OK;
+}
+
+knn_status knn_world_set_tuning(knn_world h, const knn_tuning *t) {
+    if (!h || !t) return fail(KNN_ERR_INVALID, "knn_world_set_tuning: NULL argument");
+    if (t->leaf_capacity < 0 || t->leaf_capacity > knnq::kMaxLeafCapacity)
+        return fail(KNN_ERR_INVALID, "leaf_capacity outside [0, 4096]");
+    if (t->grid_level < 0 || t->grid_level > knnq::kMaxGridLevel || t->grid_level > h->w.L)
+        return fail(KNN_ERR_INVALID, "grid_level outside [0, min(10, max_depth)]");
+    if (t->packet_level < 0 || t->packet_level > knnq::kMaxGridLevel)
+        return fail(KNN_ERR_INVALID, "packet_level outside [0, 10]");
+    h->w.tuning = *t;
+    return KNN_OK;
+}
+
+knn_status knn_world_get_tuning(knn_world h, int64_t n_q, int32_t k, knn_tuning *out) {
+    if (!h || !out) return fail(KNN_ERR_INVALID, "knn_world_get_tuning: NULL argument");
+    Plan p = make_plan(h->w, n_q, k);
+    out->leaf_capacity = p.th;
+    out->grid_level = p.G;
+    out->packet_level = p.Gp;
+    out->reserved = 0;
+    return KNN_OK;
+}
+
+knn_status knn_tick(knn_world h, const int32_t *upd_id, const float *upd_x, const float *upd_y,
+                    int64_t n_upd, const int32_t *q_id, const float *q_x, const float *q_y,
+                    int64_t n_q, int32_t k, int32_t *out_ids, float *out_d2, void *stream) {
+    if (!h) return fail(KNN_ERR_INVALID, "knn_tick: NULL world");
+    World &w = h->w;
+    if (k < 1 || k > w.desc.k_max)
+        return fail(KNN_ERR_INVALID, "knn_tick: k=%d outside [1, k_max=%d]", k, w.desc.k_max);
+    if (n_q < 0 || n_q > w.desc.max_queries)
+        return fail(KNN_ERR_INVALID, "knn_tick: n_q=%lld outside [0, max_queries=%lld]",
+                    (long long)n_q, (long long)w.desc.max_queries);
+    if (n_upd < 0 || n_upd >= (1ll << 31))
+        return fail(KNN_ERR_INVALID, "knn_tick: n_upd=%lld outside [0, 2^31)", (long long)n_upd);
+    if (n_upd > 0 && (!upd_id || !upd_x || !upd_y))
+        return fail(KNN_ERR_INVALID, "knn_tick: NULL update array with n_upd > 0");
+    if ((q_x == nullptr) != (q_y == nullptr))
+        return fail(KNN_ERR_INVALID, "knn_tick: q_x and q_y must both be given or both NULL");
+    if (n_q > 0 && (!q_id || !out_ids || !out_d2))
+        return fail(KNN_ERR_INVALID, "knn_tick: NULL query or output array with n_q > 0");
+
+    cudaSetDevice(w.device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const Plan p = make_plan(w, n_q, k);
+    cudaMemsetAsync(w.counters, 0, sizeof(uint32_t) * knnq::kNumCounters, s);
+    cudaMemsetAsync(w.err + 2, 0, sizeof(uint32_t), s);
+    mark(w, 0, s);
+    knnq::launch_updates(w, upd_id, upd_x, upd_y, n_upd, s);
+    mark(w, 1, s);
+    knnq::launch_object_sort(w, p, s);
+    mark(w, 2, s);
+    knnq::launch_leaves(w, p, s);
+    mark(w, 3, s);
+    if (n_q > 0) {
+        if (q_x == nullptr)
+            knnq::launch_queries_at_issuers(w, p, q_id, n_q, k, out_ids, out_d2, s);
+        else
+            knnq::launch_queries_explicit(w, p, q_id, q_x, q_y, n_q, k, out_ids, out_d2, s);
+    }
+    mark(w, 4, s);
+    if (n_q > 0) knnq::launch_packets(w, p, n_q, s);
+    mark(w, 5, s);
+    if (n_q > 0) knnq::launch_expand(w, p, k, n_q, out_ids, out_d2, s);
+    mark(w, 6, s);
+    w.last_stream = s;
+    w.last_plan = p;
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "knn_tick launch");
+    return KNN_OK;
+}
+
+knn_status knn_tick_host(knn_world h, const int32_t *upd_id, const float *upd_x,
+                         const float *upd_y, int64_t n_upd, const int32_t *q_id,
+                         const float *q_x, const float *q_y, int64_t n_q, int32_t k,
+                         int32_t *out_ids, float *out_d2, void *stream) {
+    if (!h) return fail(KNN_ERR_INVALID, "knn_tick_host: NULL world");
+    World &w = h->w;
+    if (n_upd < 0 || n_q < 0 || k < 1 || k > w.desc.k_max)
+        return fail(KNN_ERR_INVALID, "knn_tick_host: bad sizes");
+    const bool explicit_q = q_x != nullptr;
+    const size_t b_upd = align_up(sizeof(int32_t) * (size_t)n_upd) +
+                         2 * align_up(sizeof(float) * (size_t)n_upd);
+    const size_t b_q = align_up(sizeof(int32_t) * (size_t)n_q) +
+                       (explicit_q ? 2 * align_up(sizeof(float) * (size_t)n_q) : 0);
+    const size_t b_out = align_up(sizeof(int32_t) * (size_t)n_q * k) +
+                         align_up(sizeof(float) * (size_t)n_q * k);
+    const size_t need = b_upd + b_q + b_out;
+    cudaSetDevice(w.device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (need > w.stage_bytes) {
+        cudaStreamSynchronize(s);
+        if (w.stage) cudaFree(w.stage);
+        w.stage = nullptr;
+        w.stage_bytes = 0;
+        if (cudaMalloc(&w.stage, need) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(KNN_ERR_OOM, "knn_tick_host: staging allocation of %zu bytes failed",
+                        need);
+        }
+        w.stage_bytes = need;
+    }
+    Carve c{static_cast<char *>(w.stage)};
+    int32_t *d_uid = c.take<int32_t>((size_t)n_upd);
+    float *d_ux = c.take<float>((size_t)n_upd);
+    float *d_uy = c.take<float>((size_t)n_upd);
+    int32_t *d_qid = c.take<int32_t>((size_t)n_q);
+    float *d_qx = explicit_q ? c.take<float>((size_t)n_q) : nullptr;
+    float *d_qy = explicit_q ? c.take<float>((size_t)n_q) : nullptr;
+    int32_t *d_oid = c.take<int32_t>((size_t)n_q * k);
+    float *d_od = c.take<float>((size_t)n_q * k);
+    if (n_upd > 0) {
+        if (!upd_id || !upd_x || !upd_y)
+            return fail(KNN_ERR_INVALID, "knn_tick_host: NULL update array with n_upd > 0");
+        cudaMemcpyAsync(d_uid, upd_id, sizeof(int32_t) * n_upd, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d_ux, upd_x, sizeof(float) * n_upd, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d_uy, upd_y, sizeof(float) * n_upd, cudaMemcpyHostToDevice, s);
+    }
+    if (n_q > 0) {
+        if (!q_id || !out_ids || !out_d2 || (explicit_q && !q_y))
+            return fail(KNN_ERR_INVALID, "knn_tick_host: NULL query or output array");
+        cudaMemcpyAsync(d_qid, q_id, sizeof(int32_t) * n_q, cudaMemcpyHostToDevice, s);
+        if (explicit_q) {
+            cudaMemcpyAsync(d_qx, q_x, sizeof(float) * n_q, cudaMemcpyHostToDevice, s);
+            cudaMemcpyAsync(d_qy, q_y, sizeof(float) * n_q, cudaMemcpyHostToDevice, s);
+        }
+    }
+    knn_status st = knn_tick(h, n_upd ? d_uid : nullptr, n_upd ? d_ux : nullptr,
+                             n_upd ? d_uy : nullptr, n_upd, n_q ? d_qid : nullptr, d_qx, d_qy,
+                             n_q, k, n_q ? d_oid : nullptr, n_q ? d_od : nullptr, stream);
+    if (st != KNN_OK) return st;
+    if (n_q > 0) {
+        cudaMemcpyAsync(out_ids, d_oid, sizeof(int32_t) * n_q * k, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(out_d2, d_od, sizeof(float) * n_q * k, cudaMemcpyDeviceToHost, s);
+    }
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "knn_tick_host");
+    return KNN_OK;
+}
+
+knn_status knn_tick_status(knn_world h, uint32_t *bits_out) {
+    if (!h) return fail(KNN_ERR_INVALID, "knn_tick_status: NULL world");
+    World &w = h->w;
+    cudaSetDevice(w.device);
+    uint32_t bits = 0;
+    cudaError_t e = cudaStreamSynchronize(w.last_stream);
+    if (e == cudaSuccess) e = cudaMemcpy(&bits, w.err, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(w.err, 0, sizeof(uint32_t));
+    if (e != cudaSuccess) return cuda_fail(e, "knn_tick_status");
+    if (bits_out) *bits_out = bits;
+    if (bits & 8u) return fail(KNN_ERR_TIMEOUT, "a bounded device wait ran out");
+    if (bits) return fail(KNN_ERR_DEVICE_INPUT, "device skipped invalid input (bits 0x%x)", bits);
+    return KNN_OK;
+}
+
+knn_status knn_world_leaves(knn_world h, int32_t *level, uint32_t *z, int32_t *start,
+                            int32_t *count, int32_t *sorted_ids, int64_t cap, int64_t *m_host,
+                            void *stream) {
+    if (!h || !m_host) return fail(KNN_ERR_INVALID, "knn_world_leaves: NULL argument");
+    World &w = h->w;
+    cudaSetDevice(w.device);
+    cudaStream_t s = (cudaStream_t)stream;
+    int32_t m = 0;
+    cudaMemcpyAsync(&m, w.scalars + knnq::kScalarLeaves, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                    s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "knn_world_leaves");
+    *m_host = m;
+    const int64_t c = m < cap ? m : cap;
+    if (c > 0 && level && z && start && count)
+        knnq::launch_export_leaves(w, c, level, z, start, count, s);
+    if (sorted_ids)
+        cudaMemcpyAsync(sorted_ids, w.sid, sizeof(int32_t) * (size_t)w.n,
+                        cudaMemcpyDeviceToDevice, s);
+    e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "knn_world_leaves");
+    return KNN_OK;
+}
+
+knn_status knn_world_positions(knn_world h, float *x_dev, float *y_dev, void *stream) {
+    if (!h || !x_dev || !y_dev) return fail(KNN_ERR_INVALID, "knn_world_positions: NULL argument");
+    World &w = h->w;
+    cudaSetDevice(w.device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaMemcpyAsync(x_dev, w.px, sizeof(float) * (size_t)w.n, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(y_dev, w.py, sizeof(float) * (size_t)w.n, cudaMemcpyDeviceToDevice, s);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "knn_world_positions");
+    return KNN_OK;
+}
+
+knn_status knn_world_launches(knn_world h, int64_t *count) {
+    if (!h || !count) return fail(KNN_ERR_INVALID, "knn_world_launches: NULL argument");
+    *count = h->w.launches;
+    return KNN_OK;
+}
+
+knn_status knn_world_set_profiling(knn_world h, int32_t enable) {
+    if (!h) return fail(KNN_ERR_INVALID, "knn_world_set_profiling: NULL world");
+    World &w = h->w;
+    cudaSetDevice(w.device);
+    if (enable && !w.ev[0]) {
+        for (int i = 0; i <= knnq::kMaxStages; ++i) {
+            if (cudaEventCreate(&w.ev[i]) != cudaSuccess)
+                return cuda_fail(cudaGetLastError(), "knn_world_set_profiling");
+        }
+    }
+    w.profiling = enable != 0;
+    w.n_stage_events = 0;
+    return KNN_OK;
+}
+
+knn_status knn_world_stage_times(knn_world h, float *ms, int32_t n_stages) {
+    if (!h || !ms) return fail(KNN_ERR_INVALID, "knn_world_stage_times: NULL argument");
+    World &w = h->w;
+    if (!w.profiling || w.n_stage_events < 2)
+        return fail(KNN_ERR_INVALID, "knn_world_stage_times: profiling is off or no tick ran");
+    cudaSetDevice(w.device);
+    cudaError_t e = cudaEventSynchronize(w.ev[w.n_stage_events - 1]);
+    if (e != cudaSuccess) return cuda_fail(e, "knn_world_stage_times");
+    for (int i = 0; i < n_stages; ++i) {
+        ms[i] = 0.f;
+        if (i + 1 < w.n_stage_events) cudaEventElapsedTime(&ms[i], w.ev[i], w.ev[i + 1]);
+    }
+    return KNN_OK;
+}
+
+}  // extern "C"

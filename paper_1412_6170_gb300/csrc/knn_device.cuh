@@ -1,0 +1,205 @@
+// Device-side helpers shared by the index and expansion kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace knnq {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// Error bits recorded in the world's device error word.
+enum : uint32_t {
+    kErrBadUpdateId = 1u << 0,
+    kErrNonFiniteUpdate = 1u << 1,
+    kErrBadQuery = 1u << 2,
+    kErrTimeout = 1u << 3,
+};
+
+// Bounded spins: a wait gives up after this many polls (each poll after the
+// first few sleeps ~0.1-1 us), records kErrTimeout and continues; once the
+// timeout bit is set every other wait gives up within 64 polls, so a broken
+// tick ends in milliseconds.  Results are then invalid (the status says so)
+// but every index stays clamped to its buffer.
+constexpr uint32_t kSpinLimit = 1u << 16;
+
+// ---------------------------------------------------------------------------
+// Morton codes (Section 4.1.1): the level-L cell of a coordinate is
+// floor((v - v0) * scale) with scale = 2^L / side, clamped to [0, 2^L - 1];
+// x goes to the even bits, y to the odd bits.  Every operation is rounded on
+// its own (the _rn intrinsics are never contracted).
+__device__ __forceinline__ uint32_t cell_coord(float v, float v0, float scale, int L) {
+    float t = __fmul_rn(__fsub_rn(v, v0), scale);
+    float lim = (float)(1u << L);
+    if (!(t >= 0.0f)) return 0u;
+    if (t >= lim) return (1u << L) - 1u;
+    return (uint32_t)t;
+}
+
+__device__ __forceinline__ uint32_t spread_bits(uint32_t v) {
+    v &= 0xFFFFu;
+    v = (v | (v << 8)) & 0x00FF00FFu;
+    v = (v | (v << 4)) & 0x0F0F0F0Fu;
+    v = (v | (v << 2)) & 0x33333333u;
+    v = (v | (v << 1)) & 0x55555555u;
+    return v;
+}
+
+__device__ __forceinline__ uint32_t interleave(uint32_t cx, uint32_t cy) {
+    return spread_bits(cx) | (spread_bits(cy) << 1);
+}
+
+__device__ __forceinline__ uint32_t morton_key(float x, float y, float x0, float y0,
+                                               float scale, int L) {
+    return interleave(cell_coord(x, x0, scale, L), cell_coord(y, y0, scale, L));
+}
+
+// Number of leading 2-bit digits (quadtree levels) shared by two level-L codes.
+__device__ __forceinline__ int common_levels(uint32_t a, uint32_t b, int L) {
+    uint32_t d = a ^ b;
+    if (d == 0u) return L;
+    return (__clz(d) - (32 - 2 * L)) >> 1;
+}
+
+// ---------------------------------------------------------------------------
+// Decoupled look-back (single pass scans).  A status word packs
+// [63:34] epoch (30 bits) | [33:32] flag | [31:0] value.  Every launch uses a
+// fresh epoch, so words left by earlier launches read as "not ready" and the
+// arrays never need clearing.
+constexpr uint32_t kFlagAgg = 1u, kFlagPrefix = 2u;
+
+__device__ __forceinline__ uint64_t pack_status(uint32_t epoch, uint32_t flag, uint32_t v) {
+    return ((uint64_t)(epoch & 0x3FFFFFFFu) << 34) | ((uint64_t)flag << 32) | (uint64_t)v;
+}
+__device__ __forceinline__ bool status_ready(uint64_t s, uint32_t epoch) {
+    return (uint32_t)(s >> 34) == (epoch & 0x3FFFFFFFu) && ((s >> 32) & 3u) != 0u;
+}
+__device__ __forceinline__ uint32_t status_flag(uint64_t s) { return (uint32_t)(s >> 32) & 3u; }
+__device__ __forceinline__ uint32_t status_value(uint64_t s) { return (uint32_t)s; }
+
+__device__ __forceinline__ void st_status(uint64_t *p, uint64_t v) {
+    *reinterpret_cast<volatile uint64_t *>(p) = v;
+}
+__device__ __forceinline__ uint64_t ld_status(const uint64_t *p) {
+    return *reinterpret_cast<const volatile uint64_t *>(p);
+}
+
+// err[0] holds the sticky error bits the host reads; err[2] is this tick's
+// abort flag (cleared by the host before every tick).
+__device__ __forceinline__ bool ld_abort(const uint32_t *err) {
+    return *reinterpret_cast<const volatile uint32_t *>(err + 2) != 0u;
+}
+__device__ __forceinline__ void raise_timeout(uint32_t *err) {
+    atomicOr(err, kErrTimeout);
+    atomicOr(err + 2, 1u);
+}
+
+__device__ __forceinline__ uint32_t warp_sum_u32(uint32_t v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// Exclusive prefix of `agg` over all earlier tiles; called by one full warp.
+// Publishes this tile's aggregate, looks back 32 predecessors at a time and
+// publishes the inclusive prefix.  Returns the exclusive prefix in all lanes.
+__device__ __forceinline__ uint32_t lookback_warp(uint64_t *status, uint32_t tile,
+                                                  uint32_t epoch, uint32_t agg,
+                                                  uint32_t *err) {
+    const int lane = threadIdx.x & 31;
+    if (tile == 0) {
+        if (lane == 0) st_status(&status[0], pack_status(epoch, kFlagPrefix, agg));
+        return 0u;
+    }
+    if (lane == 0) st_status(&status[tile], pack_status(epoch, kFlagAgg, agg));
+    uint32_t excl = 0;
+    int64_t t = (int64_t)tile - 1;
+    uint32_t spins = 0;
+    for (;;) {
+        const int64_t idx = t - lane;
+        uint64_t s = idx >= 0 ? ld_status(&status[idx]) : pack_status(epoch, kFlagPrefix, 0u);
+        const bool ready = status_ready(s, epoch);
+        const unsigned rm = __ballot_sync(kFull, ready);
+        const unsigned pm = __ballot_sync(kFull, ready && status_flag(s) == kFlagPrefix);
+        if (pm) {
+            const int p = __ffs(pm) - 1;
+            const unsigned need = p == 31 ? kFull : ((1u << (p + 1)) - 1u);
+            if ((rm & need) == need) {
+                excl += warp_sum_u32(lane <= p ? status_value(s) : 0u);
+                break;
+            }
+        } else if (rm == kFull) {
+            excl += warp_sum_u32(status_value(s));
+            t -= 32;
+            continue;
+        }
+        ++spins;
+        const bool give_up = spins > kSpinLimit || ((spins & 63u) == 0u && ld_abort(err));
+        if (__any_sync(kFull, give_up)) {
+            if (lane == 0) raise_timeout(err);
+            break;
+        }
+        if (spins > 8) __nanosleep(100);
+    }
+    if (lane == 0) st_status(&status[tile], pack_status(epoch, kFlagPrefix, excl + agg));
+    return excl;
+}
+
+// Sequential per-thread look-back over a strided status array (one digit of a
+// radix pass per thread): status[t * stride].
+__device__ __forceinline__ uint32_t lookback_thread(uint64_t *status, uint32_t tile,
+                                                    uint32_t stride, uint32_t epoch,
+                                                    uint32_t agg, uint32_t *err) {
+    if (tile == 0) {
+        st_status(&status[0], pack_status(epoch, kFlagPrefix, agg));
+        return 0u;
+    }
+    st_status(&status[(uint64_t)tile * stride], pack_status(epoch, kFlagAgg, agg));
+    uint32_t excl = 0;
+    for (int64_t t = (int64_t)tile - 1; t >= 0; --t) {
+        uint64_t s = ld_status(&status[(uint64_t)t * stride]);
+        uint32_t spins = 0;
+        while (!status_ready(s, epoch)) {
+            ++spins;
+            if (spins > kSpinLimit || ((spins & 63u) == 0u && ld_abort(err))) {
+                raise_timeout(err);
+                s = pack_status(epoch, kFlagPrefix, 0u);
+                break;
+            }
+            if (spins > 8) __nanosleep(100);
+            s = ld_status(&status[(uint64_t)t * stride]);
+        }
+        excl += status_value(s);
+        if (status_flag(s) == kFlagPrefix) break;
+    }
+    st_status(&status[(uint64_t)tile * stride], pack_status(epoch, kFlagPrefix, excl + agg));
+    return excl;
+}
+
+// Block-wide exclusive scan of one uint32 per thread for blockDim.x == 256.
+// `tmp` needs 8 words of shared memory.  Returns the exclusive prefix; the
+// block total is written to *total (shared) when non-null.
+__device__ __forceinline__ uint32_t block_excl_scan_256(uint32_t v, uint32_t *tmp,
+                                                        uint32_t *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) tmp[warp] = x;
+    __syncthreads();
+    uint32_t wpre = 0, all = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+        uint32_t t = tmp[w];
+        wpre += (w < warp) ? t : 0u;
+        all += t;
+    }
+    if (total && threadIdx.x == 0) *total = all;
+    __syncthreads();
+    return wpre + x - v;
+}
+
+}  // namespace knnq

@@ -1,0 +1,699 @@
+// Index construction for one tick (Sections 2.2, 4.1.1, 4.1.2, 4.2.1):
+// update scatter, Morton keys, onesweep radix sort, PR-quadtree leaf split,
+// leaf bounding boxes, the uniform cell map, query ordering and packets.
+#include <algorithm>
+#include <cstdio>
+
+#include "knn_device.cuh"
+#include "knn_internal.h"
+
+namespace knnq {
+
+static inline int grid_for(int64_t work, int threads, int cap) {
+    int64_t b = (work + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (int)b;
+}
+
+// ---------------------------------------------------------------------------
+// Position validation (world creation).
+
+__global__ void k_validate_positions(const float *__restrict__ x, const float *__restrict__ y,
+                                     int64_t n, uint32_t *flag) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (!isfinite(x[i]) || !isfinite(y[i])) atomicOr(flag, 1u);
+    }
+}
+
+void launch_validate_positions(const float *x, const float *y, int64_t n, uint32_t *flag,
+                               cudaStream_t s) {
+    k_validate_positions<<<grid_for(n, 256, 4096), 256, 0, s>>>(x, y, n, flag);
+}
+
+// ---------------------------------------------------------------------------
+// a1 -- updates (Section 2.2): the most recent valid update of an object in the
+// batch wins.  Pass 1 stamps each object with the largest (tick, index) of a
+// valid entry; pass 2 lets only that entry write.
+
+__global__ void k_update_stamp(const int32_t *__restrict__ id, const float *__restrict__ ux,
+                               const float *__restrict__ uy, int64_t n_upd, int64_t n,
+                               unsigned long long *stamp, unsigned long long tick,
+                               uint32_t *err) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_upd;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t o = id[i];
+        if (o < 0 || o >= n) {
+            atomicOr(err, kErrBadUpdateId);
+            continue;
+        }
+        if (!isfinite(ux[i]) || !isfinite(uy[i])) {
+            atomicOr(err, kErrNonFiniteUpdate);
+            continue;
+        }
+        atomicMax(&stamp[o], (tick << 32) | (unsigned long long)i);
+    }
+}
+
+__global__ void k_update_apply(const int32_t *__restrict__ id, const float *__restrict__ ux,
+                               const float *__restrict__ uy, int64_t n_upd, int64_t n,
+                               const unsigned long long *__restrict__ stamp,
+                               unsigned long long tick, float *px, float *py) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_upd;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t o = id[i];
+        if (o < 0 || o >= n) continue;
+        if (stamp[o] == ((tick << 32) | (unsigned long long)i)) {
+            px[o] = ux[i];
+            py[o] = uy[i];
+        }
+    }
+}
+
+void launch_updates(World &w, const int32_t *id, const float *ux, const float *uy,
+                    int64_t n_upd, cudaStream_t s) {
+    if (n_upd <= 0) return;
+    ++w.tick;
+    const int g = grid_for(n_upd, 256, num_sms(w.device) * 8);
+    k_update_stamp<<<g, 256, 0, s>>>(id, ux, uy, n_upd, w.n, w.stamp, w.tick, w.err);
+    k_update_apply<<<g, 256, 0, s>>>(id, ux, uy, n_upd, w.n, w.stamp, w.tick, w.px, w.py);
+    w.launches += 2;
+}
+
+// ---------------------------------------------------------------------------
+// a2 -- Morton keys at level L plus the digit histograms of every radix pass.
+
+__global__ void __launch_bounds__(256) k_keys_hist(
+    const float *__restrict__ px, const float *__restrict__ py, int64_t n, float x0, float y0,
+    float scale, int L, int passes, uint32_t *__restrict__ key, int32_t *__restrict__ val,
+    uint32_t *hist) {
+    __shared__ uint32_t h[4][256];
+    for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) (&h[0][0])[i] = 0;
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t k = morton_key(px[i], py[i], x0, y0, scale, L);
+        key[i] = k;
+        val[i] = (int32_t)i;
+        for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(k >> (8 * p)) & 255u], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) {
+        const uint32_t c = (&h[0][0])[i];
+        if (c) atomicAdd(&hist[i], c);
+    }
+}
+
+// Query centres given explicitly: key of the centre, value = caller index.
+// Invalid queries (issuer outside [-1, n) or non-finite centre) get a padded
+// row now, the largest level-L key and value -1 - i so that later stages skip
+// them.
+__global__ void __launch_bounds__(256) k_query_keys_hist(
+    const int32_t *__restrict__ q_id, const float *__restrict__ q_x,
+    const float *__restrict__ q_y, int64_t n_q, int64_t n, float x0, float y0, float scale,
+    int L, int passes, int k, uint32_t *__restrict__ key, int32_t *__restrict__ val,
+    uint32_t *hist, int32_t *out_ids, float *out_d2, uint32_t *err) {
+    __shared__ uint32_t h[4][256];
+    for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) (&h[0][0])[i] = 0;
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_q;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t s = q_id[i];
+        const float qx = q_x[i], qy = q_y[i];
+        const bool ok = s >= -1 && s < n && isfinite(qx) && isfinite(qy);
+        uint32_t kk = (uint32_t)((1ull << (2 * L)) - 1ull);  // last level-L cell
+        if (ok) {
+            kk = morton_key(qx, qy, x0, y0, scale, L);
+            val[i] = (int32_t)i;
+        } else {
+            val[i] = -1 - (int32_t)i;
+            atomicOr(err, kErrBadQuery);
+            for (int r = 0; r < k; ++r) {
+                out_ids[i * k + r] = -1;
+                out_d2[i * k + r] = __int_as_float(0x7f800000);
+            }
+        }
+        key[i] = kk;
+        for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(kk >> (8 * p)) & 255u], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) {
+        const uint32_t c = (&h[0][0])[i];
+        if (c) atomicAdd(&hist[i], c);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a3 -- one stable LSD radix pass over 8 bits (onesweep: ranks within the tile
+// by warp multi-split, digit offsets across tiles by decoupled look-back).
+
+__global__ void __launch_bounds__(kSortThreads) k_onesweep(
+    const uint32_t *__restrict__ kin, const int32_t *__restrict__ vin,
+    uint32_t *__restrict__ kout, int32_t *__restrict__ vout, int64_t n, int shift,
+    const uint32_t *__restrict__ hist, uint64_t *status, uint32_t *ticket, uint32_t epoch,
+    uint32_t *err) {
+    __shared__ uint32_t s_wcnt[8][256];
+    __shared__ uint32_t s_texcl[256];
+    __shared__ uint32_t s_gbase[256];
+    __shared__ uint32_t s_keys[kSortTile];
+    __shared__ int32_t s_vals[kSortTile];
+    __shared__ uint32_t s_tmp[8];
+    __shared__ uint32_t s_tile;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_tile = atomicAdd(ticket, 1u);
+    for (int i = tid; i < 8 * 256; i += kSortThreads) (&s_wcnt[0][0])[i] = 0;
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const int64_t base = (int64_t)tile * kSortTile;
+    const int64_t wbase = base + (int64_t)warp * (32 * kSortItems);
+
+    uint32_t k[kSortItems];
+    int32_t v[kSortItems];
+    uint32_t r[kSortItems];
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+        const int64_t idx = wbase + j * 32 + lane;
+        k[j] = idx < n ? kin[idx] : 0u;
+        v[j] = idx < n ? vin[idx] : 0;
+        r[j] = 0;
+    }
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+        const bool valid = wbase + j * 32 + lane < n;
+        const unsigned vm = __ballot_sync(kFull, valid);
+        const uint32_t d = (k[j] >> shift) & 255u;
+        unsigned peers = 0;
+        uint32_t before = 0;
+        if (valid) {
+            peers = __match_any_sync(vm, d);
+            before = s_wcnt[warp][d];
+            r[j] = before + __popc(peers & lt);
+        }
+        __syncwarp();
+        if (valid && (peers & lt) == 0u) s_wcnt[warp][d] = before + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+
+    const int d = tid;  // one digit per thread
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+        const uint32_t c = s_wcnt[w][d];
+        s_wcnt[w][d] = run;
+        run += c;
+    }
+    const uint32_t tcnt = run;
+    const uint32_t texcl = block_excl_scan_256(tcnt, s_tmp, nullptr);
+    const uint32_t gdig = block_excl_scan_256(hist[d], s_tmp, nullptr);
+    s_texcl[d] = texcl;
+    const uint32_t back = lookback_thread(status + d, tile, 256u, epoch, tcnt, err);
+    s_gbase[d] = gdig + back;
+    __syncthreads();
+
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+        if (wbase + j * 32 + lane < n) {
+            const uint32_t dd = (k[j] >> shift) & 255u;
+            const uint32_t lpos = s_texcl[dd] + s_wcnt[warp][dd] + r[j];
+            s_keys[lpos] = k[j];
+            s_vals[lpos] = v[j];
+        }
+    }
+    __syncthreads();
+    const int64_t rem = n - base;
+    const int tn = rem < kSortTile ? (int)rem : kSortTile;
+    for (int i = tid; i < tn; i += kSortThreads) {
+        const uint32_t key = s_keys[i];
+        const uint32_t dd = (key >> shift) & 255u;
+        const uint32_t dst = s_gbase[dd] + (uint32_t)(i - (int)s_texcl[dd]);
+        if (dst < (uint64_t)n) {  // always true unless a look-back timed out
+            kout[dst] = key;
+            vout[dst] = s_vals[i];
+        }
+    }
+}
+
+// Sort (key[0], val[0]) of n entries; the result lands in buffer (passes & 1).
+static void radix_sort(World &w, int64_t n, int passes, int counter_base, cudaStream_t s) {
+    if (n <= 0) return;
+    const int tiles = (int)((n + kSortTile - 1) / kSortTile);
+    for (int p = 0; p < passes; ++p) {
+        const int src = p & 1, dst = src ^ 1;
+        k_onesweep<<<tiles, kSortThreads, 0, s>>>(w.key[src], w.val[src], w.key[dst],
+                                                   w.val[dst], n, 8 * p, w.hist + 256 * p,
+                                                   w.status, w.counters + counter_base + p,
+                                                   w.epoch++, w.err);
+        ++w.launches;
+    }
+}
+
+void launch_object_sort(World &w, const Plan &p, cudaStream_t s) {
+    cudaMemsetAsync(w.hist, 0, sizeof(uint32_t) * 4 * 256, s);
+    k_keys_hist<<<grid_for(w.n, 256, num_sms(w.device) * 4), 256, 0, s>>>(
+        w.px, w.py, w.n, w.desc.x0, w.desc.y0, w.scale, p.L, p.passes, w.key[0], w.val[0],
+        w.hist);
+    ++w.launches;
+    radix_sort(w, w.n, p.passes, kCtrObjSort, s);
+}
+
+// ---------------------------------------------------------------------------
+// a4 + a5 -- PR-quadtree leaves over the sorted keys, and the leaf-ordered SoA.
+//
+// The quadrant at level l holding sorted element i has more than th objects
+// exactly when some run of th + 1 consecutive elements containing i shares the
+// level-l prefix, i.e. when  W_i = max_{i-th <= j <= i} lcp(key_j, key_{j+th})
+// is at least l.  So the leaf level of i is lambda_i = min(W_i + 1, L) (raised
+// to the cell-map level G, below which every quadrant is split), and the leaf
+// is the level-lambda_i quadrant holding key_i.  This is the same leaf set that
+// the level-by-level splitting of Section 4.1.1 produces, computed in one pass.
+// Leaves start where (lambda, code) changes; a look-back scan numbers them.
+
+__global__ void __launch_bounds__(256) k_leaves(
+    const uint32_t *__restrict__ skeys, const int32_t *__restrict__ svals, int64_t n, int L,
+    int th, int G, const float *__restrict__ px, const float *__restrict__ py,
+    float *__restrict__ xs, float *__restrict__ ys, int32_t *__restrict__ sid,
+    int32_t *__restrict__ inv, int32_t *__restrict__ bstart, uint32_t *__restrict__ bcode,
+    uint8_t *__restrict__ blevel, int32_t *scalars, uint64_t *status, uint32_t *ticket,
+    uint32_t epoch, uint32_t *err) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ uint32_t s_tile, s_tmp[8], s_excl;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_tile = atomicAdd(ticket, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const int64_t t0 = (int64_t)tile * kLeafTile;
+    const int B = th + 1;            // window length
+    int S = 1;
+    while (S * 2 <= B) S *= 2;       // largest power of two <= B
+    const int nk = kLeafTile + 2 * th + 1;
+    const int nw = kLeafTile + th + 1;
+    const int64_t o = t0 - th - 1;   // global index of local slot 0
+
+    uint32_t *s_key = reinterpret_cast<uint32_t *>(smem);
+    int8_t *s_w0 = reinterpret_cast<int8_t *>(s_key + nk);
+    int8_t *s_w1 = s_w0 + nw + S;
+    int8_t *s_lam = s_w1 + nw + S;                          // kLeafTile + 1 entries
+    uint32_t *s_code = reinterpret_cast<uint32_t *>(
+        (reinterpret_cast<uintptr_t>(s_lam + kLeafTile + 1) + 3) & ~uintptr_t(3));
+
+    for (int u = tid; u < nk; u += 256) {
+        const int64_t j = o + u;
+        s_key[u] = (j >= 0 && j < n) ? skeys[j] : 0u;
+    }
+    __syncthreads();
+    for (int u = tid; u < nw + S; u += 256) {
+        const int64_t j = o + u;
+        int8_t wv = -1;
+        if (u < nw && j >= 0 && j + th < n) wv = (int8_t)common_levels(s_key[u], s_key[u + th], L);
+        s_w0[u] = wv;
+        s_w1[u] = -1;
+    }
+    __syncthreads();
+    // running maxima over power-of-two spans: after the loop src[u] = max w[u .. u+S-1]
+    int8_t *src = s_w0, *dst = s_w1;
+    for (int span = 1; span < S; span *= 2) {
+        for (int u = tid; u < nw; u += 256) {
+            const int8_t a = src[u], b = src[u + span];
+            dst[u] = a > b ? a : b;
+        }
+        __syncthreads();
+        int8_t *t = src;
+        src = dst;
+        dst = t;
+    }
+    // leaf level and code for elements t0-1 .. t0+kLeafTile-1
+    for (int e = tid - 1; e < kLeafTile; e += 256) {
+        const int64_t i = t0 + e;
+        int lam = 0;
+        uint32_t code = 0;
+        if (i >= 0 && i < n) {
+            const int u = e + th + 1;
+            const int8_t a = src[u - th], b = src[u + 1 - S];
+            const int W = a > b ? a : b;
+            lam = W + 1 < L ? W + 1 : L;
+            if (lam < G) lam = G;
+            code = (uint32_t)((uint64_t)s_key[e + th + 1] >> (2 * (L - lam)));
+        }
+        s_lam[e + 1] = (int8_t)lam;
+        s_code[e + 1] = code;
+    }
+    __syncthreads();
+    // flags: 4 consecutive elements per thread
+    uint32_t fl = 0, cnt = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int e = tid * 4 + q;
+        const int64_t i = t0 + e;
+        bool f = false;
+        if (i < n)
+            f = (i == 0) || s_lam[e + 1] != s_lam[e] || s_code[e + 1] != s_code[e];
+        fl |= (f ? 1u : 0u) << q;
+        cnt += f ? 1u : 0u;
+    }
+    uint32_t tile_total;
+    __shared__ uint32_t s_total;
+    const uint32_t off = block_excl_scan_256(cnt, s_tmp, &s_total);
+    tile_total = s_total;
+    if (tid < 32) {
+        const uint32_t ex = lookback_warp(status, tile, epoch, tile_total, err);
+        if (tid == 0) s_excl = ex;
+    }
+    __syncthreads();
+    const uint32_t excl = s_excl;
+    uint32_t b = excl + off;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if ((fl & (1u << q)) && b < (uint64_t)n) {
+            const int e = tid * 4 + q;
+            const int lam = s_lam[e + 1];
+            bstart[b] = (int32_t)(t0 + e);
+            bcode[b] = (uint32_t)((uint64_t)s_code[e + 1] << (2 * (L - lam)));
+            blevel[b] = (uint8_t)lam;
+            ++b;
+        }
+    }
+    if (t0 + kLeafTile >= n && tid == 0) {
+        const uint32_t m = excl + tile_total <= (uint64_t)n ? excl + tile_total : (uint32_t)n;
+        scalars[kScalarLeaves] = (int32_t)m;
+        bstart[m] = (int32_t)n;
+    }
+    // leaf-ordered SoA (a5)
+    for (int e = tid; e < kLeafTile; e += 256) {
+        const int64_t i = t0 + e;
+        if (i >= n) break;
+        int32_t id = svals[i];
+        if (id < 0 || id >= n) id = 0;  // only after a timed-out look-back
+        xs[i] = px[id];
+        ys[i] = py[id];
+        sid[i] = id;
+        inv[id] = (int32_t)i;
+    }
+}
+
+static size_t leaves_smem(int th) {
+    const int nk = kLeafTile + 2 * th + 1;
+    int S = 1;
+    while (S * 2 <= th + 1) S *= 2;
+    const int nw = kLeafTile + th + 1;
+    size_t bytes = (size_t)nk * 4 + 2 * (size_t)(nw + S) + kLeafTile + 1 + 4;
+    bytes = (bytes + 3) & ~size_t(3);
+    bytes += (size_t)(kLeafTile + 1) * 4;
+    return bytes;
+}
+
+// Tight bounding box of every leaf's members (used as conservative lower
+// bounds of member distances by the expansion).
+__global__ void k_leaf_aabb(const int32_t *__restrict__ bstart, const int32_t *__restrict__ scalars,
+                            const float *__restrict__ xs, const float *__restrict__ ys,
+                            float4 *__restrict__ baabb, int64_t n) {
+    const int32_t m = scalars[kScalarLeaves];
+    for (int32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < m; b += gridDim.x * blockDim.x) {
+        const int32_t s = bstart[b], e = bstart[b + 1];
+        if (s < 0 || e <= s || e > n) {  // leaves are never empty
+            baabb[b] = make_float4(0.f, 0.f, -1.f, -1.f);
+            continue;
+        }
+        float x0 = xs[s], x1 = x0, y0 = ys[s], y1 = y0;
+        for (int32_t i = s + 1; i < e; ++i) {
+            const float x = xs[i], y = ys[i];
+            x0 = fminf(x0, x);
+            x1 = fmaxf(x1, x);
+            y0 = fminf(y0, y);
+            y1 = fmaxf(y1, y);
+        }
+        baabb[b] = make_float4(x0, y0, x1, y1);
+    }
+}
+
+// Uniform cell map at level G (the paper's z_map): cb[c] = first leaf whose
+// level-G cell is >= c, so the leaves of cell c are [cb[c], cb[c+1]).
+__global__ void k_cellmap(const uint32_t *__restrict__ bcode, const int32_t *__restrict__ scalars,
+                          int L, int G, int32_t *__restrict__ cb, int64_t ncell) {
+    const int32_t m = scalars[kScalarLeaves];  // <= n by construction
+    const int sh = 2 * (L - G);
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c <= ncell;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int32_t lo = 0, hi = m;
+        while (lo < hi) {
+            const int32_t mid = (lo + hi) >> 1;
+            if ((int64_t)(bcode[mid] >> sh) < c) lo = mid + 1;
+            else hi = mid;
+        }
+        cb[c] = lo;
+    }
+}
+
+void launch_leaves(World &w, const Plan &p, cudaStream_t s) {
+    const int r = p.passes & 1;
+    const int tiles = (int)((w.n + kLeafTile - 1) / kLeafTile);
+    const size_t sm = leaves_smem(p.th);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_leaves, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)leaves_smem(kMaxLeafCapacity));
+        attr_set = true;
+    }
+    k_leaves<<<tiles, 256, sm, s>>>(w.key[r], w.val[r], w.n, p.L, p.th, p.G, w.px, w.py, w.xs,
+                                    w.ys, w.sid, w.inv, w.bstart, w.bcode, w.blevel, w.scalars,
+                                    w.status, w.counters + kCtrLeaves, w.epoch++, w.err);
+    const int g = grid_for(w.n, 256, num_sms(w.device) * 8);
+    k_leaf_aabb<<<g, 256, 0, s>>>(w.bstart, w.scalars, w.xs, w.ys, w.baabb, w.n);
+    const int64_t ncell = 1ll << (2 * p.G);
+    k_cellmap<<<grid_for(ncell + 1, 256, num_sms(w.device) * 16), 256, 0, s>>>(
+        w.bcode, w.scalars, p.L, p.G, w.cb, ncell);
+    w.launches += 3;
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan of int32 (single pass, look-back).  In place is allowed.
+
+__global__ void __launch_bounds__(256) k_scan_excl(const int32_t *in, int32_t *out, int64_t len,
+                                                   int32_t *total, uint64_t *status,
+                                                   uint32_t *ticket, uint32_t epoch,
+                                                   uint32_t *err) {
+    __shared__ uint32_t s_tile, s_tmp[8], s_total, s_excl;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_tile = atomicAdd(ticket, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const int64_t base = (int64_t)tile * kScanTile + tid * 8;
+    int32_t v[8];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        v[q] = base + q < len ? in[base + q] : 0;
+        sum += (uint32_t)v[q];
+    }
+    const uint32_t off = block_excl_scan_256(sum, s_tmp, &s_total);
+    if (tid < 32) {
+        const uint32_t ex = lookback_warp(status, tile, epoch, s_total, err);
+        if (tid == 0) s_excl = ex;
+    }
+    __syncthreads();
+    uint32_t run = s_excl + off;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        if (base + q < len) out[base + q] = (int32_t)run;
+        run += (uint32_t)v[q];
+    }
+    if ((int64_t)(tile + 1) * kScanTile >= len && tid == 255 && total) *total = (int32_t)run;
+}
+
+static void scan_excl(World &w, const int32_t *in, int32_t *out, int64_t len, int32_t *total,
+                      int counter, cudaStream_t s) {
+    const int tiles = (int)((len + kScanTile - 1) / kScanTile);
+    k_scan_excl<<<tiles, 256, 0, s>>>(in, out, len, total, w.status, w.counters + counter,
+                                      w.epoch++, w.err);
+    ++w.launches;
+}
+
+// ---------------------------------------------------------------------------
+// a6 -- query ordering (Section 4.2.1).  Queries centred at their issuers are
+// ordered by the issuer's place in the sorted object order (a counting sort),
+// which is the Morton order of their centres.
+
+__global__ void k_query_count(const int32_t *__restrict__ q_id, int64_t n_q, int64_t n,
+                              const int32_t *__restrict__ inv, int32_t *qcnt, int k,
+                              int32_t *out_ids, float *out_d2, uint32_t *err) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_q;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t s = q_id[i];
+        if (s < 0 || s >= n) {
+            atomicOr(err, kErrBadQuery);
+            for (int r = 0; r < k; ++r) {
+                out_ids[i * k + r] = -1;
+                out_d2[i * k + r] = __int_as_float(0x7f800000);
+            }
+            continue;
+        }
+        atomicAdd(&qcnt[inv[s]], 1);
+    }
+}
+
+__global__ void k_query_scatter(const int32_t *__restrict__ q_id, int64_t n_q, int64_t n,
+                                const int32_t *__restrict__ inv, int32_t *qoff,
+                                const float *__restrict__ xs, const float *__restrict__ ys,
+                                const uint32_t *__restrict__ skey, float *qs_x, float *qs_y,
+                                int32_t *qs_id, int32_t *qs_orig, uint32_t *qs_key) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_q;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t s = q_id[i];
+        if (s < 0 || s >= n) continue;
+        const int32_t p = inv[s];
+        const int32_t j = atomicAdd(&qoff[p], 1);
+        if (j < 0 || j >= n_q) continue;  // only after a timed-out look-back
+        qs_x[j] = xs[p];
+        qs_y[j] = ys[p];
+        qs_id[j] = s;
+        qs_orig[j] = (int32_t)i;
+        qs_key[j] = skey[p];
+    }
+}
+
+void launch_queries_at_issuers(World &w, const Plan &p, const int32_t *q_id, int64_t n_q,
+                               int32_t k, int32_t *out_ids, float *out_d2, cudaStream_t s) {
+    cudaMemsetAsync(w.qcnt, 0, sizeof(int32_t) * (size_t)(w.n + 1), s);
+    const int g = grid_for(n_q, 256, num_sms(w.device) * 8);
+    k_query_count<<<g, 256, 0, s>>>(q_id, n_q, w.n, w.inv, w.qcnt, k, out_ids, out_d2, w.err);
+    scan_excl(w, w.qcnt, w.qcnt, w.n, w.scalars + kScalarValidQueries, kCtrQueryScan, s);
+    const uint32_t *skey = w.key[p.passes & 1];
+    k_query_scatter<<<g, 256, 0, s>>>(q_id, n_q, w.n, w.inv, w.qcnt, w.xs, w.ys, skey, w.qs_x,
+                                      w.qs_y, w.qs_id, w.qs_orig, w.qs_key);
+    w.launches += 2;
+}
+
+__global__ void k_query_gather(const uint32_t *__restrict__ skey, const int32_t *__restrict__ sval,
+                               int64_t n_q, const int32_t *__restrict__ q_id,
+                               const float *__restrict__ q_x, const float *__restrict__ q_y,
+                               float *qs_x, float *qs_y, int32_t *qs_id, int32_t *qs_orig,
+                               uint32_t *qs_key, int32_t *scalars) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t == 0) scalars[kScalarValidQueries] = (int32_t)n_q;
+    for (int64_t j = t; j < n_q; j += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = sval[j];
+        qs_key[j] = skey[j];
+        qs_orig[j] = v;
+        if (v >= 0) {
+            qs_x[j] = q_x[v];
+            qs_y[j] = q_y[v];
+            qs_id[j] = q_id[v];
+        } else {
+            qs_x[j] = 0.f;
+            qs_y[j] = 0.f;
+            qs_id[j] = -1;
+        }
+    }
+}
+
+void launch_queries_explicit(World &w, const Plan &p, const int32_t *q_id, const float *q_x,
+                             const float *q_y, int64_t n_q, int32_t k, int32_t *out_ids,
+                             float *out_d2, cudaStream_t s) {
+    cudaMemsetAsync(w.hist, 0, sizeof(uint32_t) * 4 * 256, s);
+    const int g = grid_for(n_q, 256, num_sms(w.device) * 4);
+    k_query_keys_hist<<<g, 256, 0, s>>>(q_id, q_x, q_y, n_q, w.n, w.desc.x0, w.desc.y0, w.scale,
+                                        p.L, p.passes, k, w.key[0], w.val[0], w.hist, out_ids,
+                                        out_d2, w.err);
+    radix_sort(w, n_q, p.passes, kCtrQuerySort, s);
+    const int r = p.passes & 1;
+    k_query_gather<<<grid_for(n_q, 256, num_sms(w.device) * 8), 256, 0, s>>>(
+        w.key[r], w.val[r], n_q, q_id, q_x, q_y, w.qs_x, w.qs_y, w.qs_id, w.qs_orig, w.qs_key,
+        w.scalars);
+    w.launches += 2;
+}
+
+// ---------------------------------------------------------------------------
+// Packets: at most 32 consecutive sorted queries inside one level-Gp cell,
+// one packet per warp of the expansion (the paper's per-cell tasks).
+
+__global__ void k_query_cells(const uint32_t *__restrict__ qs_key, const int32_t *__restrict__ scalars,
+                              int L, int Gp, int64_t ncell, int64_t nq_cap, int32_t *qcs,
+                              int32_t *npk) {
+    int32_t nv = scalars[kScalarValidQueries];
+    if (nv < 0) nv = 0;
+    if (nv > nq_cap) nv = (int32_t)nq_cap;
+    const int sh = 2 * (L - Gp);
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c <= ncell;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int32_t lo = 0, hi = nv;
+        while (lo < hi) {
+            const int32_t mid = (lo + hi) >> 1;
+            if ((int64_t)((uint64_t)qs_key[mid] >> sh) < c) lo = mid + 1;
+            else hi = mid;
+        }
+        int32_t lo2 = lo, hi2 = nv;
+        while (lo2 < hi2) {
+            const int32_t mid = (lo2 + hi2) >> 1;
+            if ((int64_t)((uint64_t)qs_key[mid] >> sh) < c + 1) lo2 = mid + 1;
+            else hi2 = mid;
+        }
+        qcs[c] = lo;
+        npk[c] = c < ncell ? (lo2 - lo + 31) / 32 : 0;
+    }
+}
+
+__global__ void k_packets(const int32_t *__restrict__ qcs, const int32_t *__restrict__ pk_off,
+                          int64_t ncell, int64_t pk_cap, int32_t *pk_start, int32_t *pk_len) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t s = qcs[c], e = qcs[c + 1];
+        int32_t o = pk_off[c];
+        for (int32_t q = s; q < e && o >= 0 && o < pk_cap; q += 32, ++o) {
+            pk_start[o] = q;
+            pk_len[o] = e - q < 32 ? e - q : 32;
+        }
+    }
+}
+
+void launch_packets(World &w, const Plan &p, int64_t n_q, cudaStream_t s) {
+    const int64_t ncell = 1ll << (2 * p.Gp);
+    const int g = grid_for(ncell + 1, 256, num_sms(w.device) * 16);
+    k_query_cells<<<g, 256, 0, s>>>(w.qs_key, w.scalars, p.L, p.Gp, ncell, n_q, w.qcs, w.npk);
+    scan_excl(w, w.npk, w.pk_off, ncell + 1, w.scalars + kScalarPackets, kCtrPacketScan, s);
+    k_packets<<<g, 256, 0, s>>>(w.qcs, w.pk_off, ncell, packet_capacity(w), w.pk_start,
+                                w.pk_len);
+    w.launches += 2;
+}
+
+int num_sms(int device) {
+    static int cached[64] = {0};
+    if (device < 0 || device >= 64) device = 0;
+    if (!cached[device]) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
+        cached[device] = v > 0 ? v : 1;
+    }
+    return cached[device];
+}
+
+}  // namespace knnq
+
+namespace knnq {
+
+// Leaves of the last tick in the exported layout (level, own-level code,
+// start, count) and the sorted object order.
+__global__ void k_export_leaves(const int32_t *__restrict__ bstart,
+                                const uint32_t *__restrict__ bcode,
+                                const uint8_t *__restrict__ blevel, int64_t m, int L,
+                                int32_t *level, uint32_t *z, int32_t *start, int32_t *count) {
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < m;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        const int lv = blevel[b];
+        level[b] = lv;
+        z[b] = (uint32_t)((uint64_t)bcode[b] >> (2 * (L - lv)));
+        start[b] = bstart[b];
+        count[b] = bstart[b + 1] - bstart[b];
+    }
+}
+
+void launch_export_leaves(World &w, int64_t m, int32_t *level, uint32_t *z, int32_t *start,
+                          int32_t *count, cudaStream_t s) {
+    if (m <= 0) return;
+    k_export_leaves<<<grid_for(m, 256, 4096), 256, 0, s>>>(w.bstart, w.bcode, w.blevel, m, w.L,
+                                                          level, z, start, count);
+}
+
+}  // namespace knnq

@@ -1,0 +1,127 @@
+// Host-side internals: the world object and the kernel launchers.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "knn.h"
+
+namespace knnq {
+
+constexpr int kMaxK = 64;
+constexpr int kMaxGridLevel = 10;
+constexpr int kMaxLeafCapacity = 4096;
+constexpr int kMaxStages = 12;
+constexpr int kNumCounters = 32;
+
+// Radix sort tile (onesweep): 256 threads x 16 keys.
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;
+// Leaf split tile.
+constexpr int kLeafTile = 1024;
+// Single-value scan tile.
+constexpr int kScanTile = 2048;
+
+// Device scalars written by kernels and read by later kernels.
+enum Scalar : int { kScalarLeaves = 0, kScalarValidQueries = 1, kScalarPackets = 2,
+                    kNumScalars = 8 };
+
+// Ticket counters (one per single-pass launch site in a tick).
+enum Counter : int { kCtrObjSort = 0, kCtrQuerySort = 4, kCtrLeaves = 8, kCtrQueryScan = 9,
+                     kCtrPacketScan = 10, kCtrExpand = 11 };
+
+struct Plan {
+    int L;           // max depth (key has 2L bits)
+    int th;          // leaf capacity
+    int G;           // cell-map level (min leaf level)
+    int Gp;          // packet level
+    int passes;      // radix passes over 2L bits
+};
+
+struct World {
+    int device = 0;
+    knn_world_desc desc{};
+    int64_t n = 0;
+    int L = 16;
+    float scale = 0.f;     // 2^L / side, binary32
+    knn_tuning tuning{};   // user overrides (0 = auto)
+    uint32_t epoch = 1;    // look-back epoch, fresh per single-pass launch
+    uint64_t tick = 0;     // update stamp counter
+    cudaStream_t last_stream = nullptr;
+    Plan last_plan{};
+
+    // one device arena
+    void *arena = nullptr;
+    size_t arena_bytes = 0;
+
+    float *px = nullptr, *py = nullptr;
+    unsigned long long *stamp = nullptr;
+    uint32_t *key[2] = {nullptr, nullptr};
+    int32_t *val[2] = {nullptr, nullptr};
+    float *xs = nullptr, *ys = nullptr;
+    int32_t *sid = nullptr, *inv = nullptr;
+    uint32_t *skey = nullptr;  // sorted object keys (copy kept for queries)
+    int32_t *bstart = nullptr;
+    uint32_t *bcode = nullptr;
+    uint8_t *blevel = nullptr;
+    float4 *baabb = nullptr;
+    int32_t *cb = nullptr;
+    int32_t *qcnt = nullptr;
+    float *qs_x = nullptr, *qs_y = nullptr;
+    int32_t *qs_id = nullptr, *qs_orig = nullptr;
+    uint32_t *qs_key = nullptr;
+    int32_t *qcs = nullptr, *npk = nullptr, *pk_off = nullptr;
+    int32_t *pk_start = nullptr, *pk_len = nullptr;
+    uint64_t *status = nullptr;
+    size_t status_words = 0;
+    uint32_t *hist = nullptr;
+    uint32_t *counters = nullptr;
+    int32_t *scalars = nullptr;
+    uint32_t *err = nullptr;
+
+    // host-pointer tick staging (grown on demand)
+    void *stage = nullptr;
+    size_t stage_bytes = 0;
+
+    // kernels launched by this world's ticks so far
+    int64_t launches = 0;
+
+    // profiling
+    bool profiling = false;
+    cudaEvent_t ev[kMaxStages + 1] = {};
+    int n_stage_events = 0;
+
+    int64_t max_rows() const { return n > desc.max_queries ? n : desc.max_queries; }
+};
+
+// Packets never exceed n_q/32 + (non-empty packet cells) <= n_q + n_q/32 + 1.
+inline int64_t packet_capacity(const World &w) {
+    return w.desc.max_queries + w.desc.max_queries / 32 + 2;
+}
+
+
+
+// ---- launchers (knn_index.cu) ----------------------------------------------
+void launch_validate_positions(const float *x, const float *y, int64_t n, uint32_t *flag,
+                               cudaStream_t s);
+void launch_updates(World &w, const int32_t *id, const float *ux, const float *uy,
+                    int64_t n_upd, cudaStream_t s);
+void launch_object_sort(World &w, const Plan &p, cudaStream_t s);
+void launch_leaves(World &w, const Plan &p, cudaStream_t s);
+void launch_queries_at_issuers(World &w, const Plan &p, const int32_t *q_id, int64_t n_q,
+                               int32_t k, int32_t *out_ids, float *out_d2, cudaStream_t s);
+void launch_queries_explicit(World &w, const Plan &p, const int32_t *q_id, const float *q_x,
+                             const float *q_y, int64_t n_q, int32_t k, int32_t *out_ids,
+                             float *out_d2, cudaStream_t s);
+void launch_packets(World &w, const Plan &p, int64_t n_q, cudaStream_t s);
+void launch_export_leaves(World &w, int64_t m, int32_t *level, uint32_t *z, int32_t *start,
+                          int32_t *count, cudaStream_t s);
+
+// ---- launcher (knn_expand.cu) -----------------------------------------------
+void launch_expand(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t *out_ids,
+                   float *out_d2, cudaStream_t s);
+
+int num_sms(int device);
+
+}  // namespace knnq

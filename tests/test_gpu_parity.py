@@ -1,0 +1,281 @@
+"""Parity of the CUDA path with the CPU oracle (GPU).  Every comparison is
+bit-exact: ids equal and squared distances equal as binary32 bit patterns."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1412_6170_gb300 import knnq, synth
+from tests.gpu_util import (assert_rows_equal, gpu_tick, make_world, oracle_rows, sample_rows,
+                            to_dev, torch_dev)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def run_and_compare(w, k_max=64, tuning=None, sample=None, world_kw=None, what=""):
+    """Replay all ticks of workload ``w`` on the GPU and compare every tick with
+    the oracle (all rows, or ``sample`` rows per tick)."""
+    world = make_world(w.x0, w.y0, k_max=k_max,
+                       max_queries=max(t.q_id.shape[0] for t in w.ticks), **(world_kw or {}))
+    try:
+        if tuning:
+            world.set_tuning(**tuning)
+        x, y = w.x0.copy(), w.y0.copy()
+        for ti, t in enumerate(w.ticks):
+            x, y, _ = oracle.apply_updates(x, y, t.upd_id, t.upd_x, t.upd_y)
+            ids, d2 = gpu_tick(world, t)
+            rows = np.arange(t.q_id.shape[0]) if sample is None else \
+                sample_rows(t.q_id.shape[0], sample, seed=ti)
+            rid, rd2 = oracle_rows(x, y, t, rows)
+            assert_rows_equal(ids, d2, rid, rd2, rows, what=f"{what} tick {ti}")
+        st, bits = world.status()
+        assert st == knnq.KNN_OK, (st, bits)
+    finally:
+        world.close()
+
+
+# -------------------------------------------------------------------------
+# The five workload shapes
+
+
+def test_uniform_10k_k8_one_tick_full():
+    run_and_compare(synth.plain_uniform_one_tick(), what="10k uniform k=8")
+
+
+@pytest.mark.parametrize("k", [1, 5, 16, 33, 64])
+def test_uniform_ragged_several_ticks_full(k):
+    # 30011 objects: many sort tiles and leaf tiles, ragged tails everywhere
+    w = synth.plain_uniform_moving(n=30011, k=k, ticks=2, seed=5)
+    run_and_compare(w, what=f"30011 uniform k={k}")
+
+
+@pytest.mark.parametrize("k", [4, 32])
+def test_clustered_subset_queries_full(k):
+    w = synth.skewed_moving(n=60000, k=k, ticks=2, seed=9)
+    run_and_compare(w, what=f"60k clustered k={k}")
+
+
+def test_uniform_1m_k16_full_size_sampled():
+    w = synth.plain_uniform_moving(n=1_000_000, k=16, ticks=2, seed=0)
+    run_and_compare(w, k_max=16, sample=20000, what="1M uniform k=16")
+
+
+def test_clustered_4m_k32_full_size_sampled():
+    w = synth.skewed_moving(n=4_000_000, k=32, ticks=2, seed=0)
+    run_and_compare(w, k_max=32, sample=8000, what="4M clustered k=32")
+
+
+# -------------------------------------------------------------------------
+# Index parameters never change a result
+
+
+@pytest.mark.parametrize("tuning", [dict(leaf_capacity=1), dict(leaf_capacity=3, grid_level=2),
+                                    dict(leaf_capacity=200, grid_level=4, packet_level=1),
+                                    dict(leaf_capacity=4096, grid_level=1, packet_level=0),
+                                    dict(leaf_capacity=16, grid_level=10, packet_level=10)])
+def test_tuning_invariance(tuning):
+    w = synth.skewed_moving(n=20000, k=16, ticks=1, seed=11, query_frac=0.5)
+    run_and_compare(w, tuning=tuning, what=f"tuning {tuning}")
+
+
+def test_max_depth_invariance():
+    w = synth.skewed_moving(n=20000, k=8, ticks=1, seed=12)
+    for depth in (1, 3, 9):
+        run_and_compare(w, world_kw=dict(max_depth=depth), what=f"max_depth {depth}")
+
+
+# -------------------------------------------------------------------------
+# Degenerate and edge cases
+
+
+def tick(q_id, k, upd=None, q_x=None, q_y=None):
+    uid, ux, uy = upd if upd is not None else (np.zeros(0, np.int32), np.zeros(0, np.float32),
+                                               np.zeros(0, np.float32))
+    return synth.Tick(np.asarray(uid, np.int32), np.asarray(ux, np.float32),
+                      np.asarray(uy, np.float32), np.asarray(q_id, np.int32), k,
+                      None if q_x is None else np.asarray(q_x, np.float32),
+                      None if q_y is None else np.asarray(q_y, np.float32))
+
+
+def compare_ticks(x0, y0, ticks, k_max=64, tuning=None, expect_status=knnq.KNN_OK):
+    x0, y0 = np.asarray(x0, np.float32), np.asarray(y0, np.float32)
+    world = make_world(x0, y0, k_max=k_max, max_queries=max(1, max(t.q_id.shape[0] for t in ticks)))
+    try:
+        if tuning:
+            world.set_tuning(**tuning)
+        x, y = np.asarray(x0, np.float32), np.asarray(y0, np.float32)
+        for t in ticks:
+            x, y, _ = oracle.apply_updates(x, y, t.upd_id, t.upd_x, t.upd_y)
+            ids, d2 = gpu_tick(world, t)
+            if t.q_id.shape[0]:
+                rid, rd2, _ = oracle.knn(x, y, t.q_id, t.k, t.q_x, t.q_y)
+                assert_rows_equal(ids, d2, rid, rd2)
+        st, bits = world.status()
+        assert st == expect_status, (st, bits)
+        return bits
+    finally:
+        world.close()
+
+
+def test_single_object_pads():
+    compare_ticks([0.5], [0.5], [tick([0], 3)])
+
+
+@pytest.mark.parametrize("n,k", [(2, 1), (2, 5), (5, 4), (5, 5), (7, 64)])
+def test_fewer_objects_than_k(n, k):
+    r = np.random.default_rng(n * 100 + k)
+    x, y = r.random(n).astype(np.float32), r.random(n).astype(np.float32)
+    compare_ticks(x, y, [tick(np.arange(n), k)])
+
+
+def test_all_coincident_objects():
+    n = 5000
+    x = np.full(n, 0.25, np.float32)
+    compare_ticks(x, x.copy(), [tick(np.arange(n), 16), tick(np.arange(0, n, 7), 64)])
+
+
+def test_duplicates_and_lattice_ties():
+    g = 70
+    ii, jj = np.meshgrid(np.arange(g), np.arange(g), indexing="ij")
+    x = np.concatenate([ii.ravel() / 128.0, ii.ravel()[:500] / 128.0]).astype(np.float32)
+    y = np.concatenate([jj.ravel() / 128.0, jj.ravel()[:500] / 128.0]).astype(np.float32)
+    n = x.shape[0]
+    for k in (4, 5, 12, 13, 40):
+        compare_ticks(x, y, [tick(np.arange(n), k)], tuning=dict(leaf_capacity=2))
+
+
+def test_duplicate_update_ids_last_wins():
+    r = np.random.default_rng(3)
+    n = 3000
+    x, y = r.random(n).astype(np.float32), r.random(n).astype(np.float32)
+    uid = np.concatenate([np.arange(n), r.integers(0, n, 4000)]).astype(np.int32)
+    ux, uy = r.random(uid.shape[0]).astype(np.float32), r.random(uid.shape[0]).astype(np.float32)
+    compare_ticks(x, y, [tick(np.arange(n), 8, (uid, ux, uy)),
+                         tick(np.arange(n)[::-1], 8, (uid[::-1], ux, uy))])
+
+
+def test_invalid_updates_skipped_and_reported():
+    r = np.random.default_rng(4)
+    n = 2000
+    x, y = r.random(n).astype(np.float32), r.random(n).astype(np.float32)
+    uid = np.array([5, -1, n, 7, 7, 9], np.int32)
+    ux = np.array([0.5, 0.1, 0.1, 0.2, np.nan, np.inf], np.float32)
+    uy = np.array([0.5, 0.1, 0.1, 0.2, 0.3, 0.1], np.float32)
+    bits = compare_ticks(x, y, [tick(np.arange(n), 8, (uid, ux, uy))],
+                         expect_status=knnq.KNN_ERR_DEVICE_INPUT)
+    assert bits & knnq.ERR_BAD_UPDATE_ID and bits & knnq.ERR_NONFINITE_UPDATE
+
+
+def test_invalid_queries_padded_and_reported():
+    r = np.random.default_rng(5)
+    n = 2000
+    x, y = r.random(n).astype(np.float32), r.random(n).astype(np.float32)
+    bits = compare_ticks(x, y, [tick([0, -1, n, 3, -7, 3], 4)],
+                         expect_status=knnq.KNN_ERR_DEVICE_INPUT)
+    assert bits & knnq.ERR_BAD_QUERY
+    q = [0, -1, 5, n, -1]
+    qx = [0.3, 0.2, np.nan, 0.5, 0.9]
+    bits = compare_ticks(x, y, [tick(q, 4, None, qx, qx)], expect_status=knnq.KNN_ERR_DEVICE_INPUT)
+    assert bits & knnq.ERR_BAD_QUERY
+
+
+def test_explicit_and_anonymous_centres_outside_domain():
+    r = np.random.default_rng(6)
+    n = 20000
+    x, y = r.random(n).astype(np.float32), r.random(n).astype(np.float32)
+    x[:300] = (r.random(300) * 6 - 3).astype(np.float32)   # objects outside [0,1)
+    y[:300] = (r.random(300) * 6 - 3).astype(np.float32)
+    nq = 5000
+    qid = np.where(r.random(nq) < 0.5, -1, r.integers(0, n, nq)).astype(np.int32)
+    qx = (r.random(nq) * 1.4 - 0.2).astype(np.float32)
+    qy = (r.random(nq) * 1.4 - 0.2).astype(np.float32)
+    qx[:50] = 7.5
+    compare_ticks(x, y, [tick(qid, 16, None, qx, qy), tick(qid[::2], 3, None, qx[::2], qy[::2])])
+
+
+def test_repeated_query_ids_and_empty_tick():
+    r = np.random.default_rng(7)
+    n = 5000
+    x, y = r.random(n).astype(np.float32), r.random(n).astype(np.float32)
+    q = r.integers(0, n, 3000).astype(np.int32)
+    q[:100] = 17
+    compare_ticks(x, y, [tick(q, 10), tick(np.zeros(0, np.int32), 4), tick(q[:1], 1)])
+
+
+def test_domain_offset_and_scale():
+    r = np.random.default_rng(8)
+    n = 20000
+    x = (1000.0 + 50.0 * r.random(n)).astype(np.float32)
+    y = (-20.0 + 50.0 * r.random(n)).astype(np.float32)
+    torch, dev = torch_dev()
+    from paper_1412_6170_gb300 import knnq as K
+    world = K.World(to_dev(x), to_dev(y), k_max=16, domain=(1000.0, -20.0, 50.0))
+    try:
+        ids, d2 = world.tick(16, to_dev(np.arange(n, dtype=np.int32)))
+        torch.cuda.synchronize()
+        rid, rd2, _ = oracle.knn(x, y, np.arange(n, dtype=np.int32), 16)
+        assert_rows_equal(ids.cpu().numpy(), d2.cpu().numpy(), rid, rd2)
+    finally:
+        world.close()
+
+
+# -------------------------------------------------------------------------
+# API paths
+
+
+def test_host_buffer_tick_matches_device_tick():
+    import ctypes
+    w = synth.plain_uniform_moving(n=50000, k=16, ticks=1, seed=2)
+    t = w.ticks[0]
+    a = make_world(w.x0, w.y0, k_max=16)
+    b = make_world(w.x0, w.y0, k_max=16)
+    try:
+        ids, d2 = gpu_tick(a, t)
+        nq = t.q_id.shape[0]
+        hid = np.empty((nq, 16), np.int32)
+        hd2 = np.empty((nq, 16), np.float32)
+        p = lambda arr: arr.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+        knnq.knn_tick_host(b.handle, p(t.upd_id), p(t.upd_x), p(t.upd_y), t.upd_id.shape[0],
+                           p(t.q_id), None, None, nq, 16, p(hid), p(hd2), 0)
+        assert np.array_equal(ids, hid) and np.array_equal(d2.view(np.uint32), hd2.view(np.uint32))
+    finally:
+        a.close()
+        b.close()
+
+
+def test_checkpoint_resume_bit_identical():
+    w = synth.plain_uniform_moving(n=40000, k=8, ticks=6, seed=4)
+    a = make_world(w.x0, w.y0, k_max=8)
+    try:
+        for t in w.ticks[:3]:
+            gpu_tick(a, t)
+        px, py = a.positions()
+        from paper_1412_6170_gb300 import knnq as K
+        b = K.World(px, py, k_max=8)
+        try:
+            for t in w.ticks[3:]:
+                ra = gpu_tick(a, t)
+                rb = gpu_tick(b, t)
+                assert np.array_equal(ra[0], rb[0]) and np.array_equal(ra[1], rb[1])
+        finally:
+            b.close()
+    finally:
+        a.close()
+
+
+def test_stage_profiling_reports_every_stage():
+    w = synth.plain_uniform_moving(n=100000, k=16, ticks=1, seed=1)
+    world = make_world(w.x0, w.y0, k_max=16)
+    try:
+        world.set_profiling(True)
+        gpu_tick(world, w.ticks[0])
+        st = world.stage_times()
+        assert list(st) == knnq.stage_names()
+        assert all(v >= 0 for v in st.values()) and st["expand"] > 0
+    finally:
+        world.close()
