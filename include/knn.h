@@ -173,6 +173,35 @@ knn_status knn_world_set_profiling(knn_world w, int32_t enable);
 knn_status knn_world_stage_times(knn_world w, float *ms_host, int32_t n_stages);
 const char *knn_stage_name(int32_t i);
 
+/* ---- allocation-free one-shot call --------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that must not allocate device memory: latency-critical loops (cudaMalloc and
+ * cudaFree can synchronize the device and take milliseconds), services whose
+ * device memory belongs to another allocator or a fixed budget, and code that
+ * must not fail half-way through a request because an allocation did.
+ *
+ * knn_query_static answers n_q k-NN queries over n objects at x_dev/y_dev
+ * exactly as knn_world_create + one knn_tick without updates would (same
+ * rows, bit for bit), but creates no world and allocates nothing: its scratch
+ * is one static device array of 8 MiB that every GPU loading this library
+ * holds until the process exits.  Limits: n in [1, 65536], n_q in [0, 65536],
+ * k in [1, 64], cell-map level at most 8; larger sizes return
+ * KNN_ERR_INVALID.  desc gives the domain, leaf_capacity and max_depth
+ * (k_max and max_queries are ignored).  Positions are only read.
+ *
+ * The first call on each device looks the array's device address up (with
+ * that device current); make that first call before any stream capture.
+ * Every call reuses the same array and finds the previous call's contents in
+ * it, so calls that overlap on the GPU (other streams, other host threads
+ * without ordering) race and corrupt each other's results.  Device-side input
+ * problems give padded rows, as in knn_tick, but are not reported (there is
+ * no world to hold a status).  Asynchronous on `stream`. */
+knn_status knn_query_static(const knn_world_desc *desc, const float *x_dev,
+                            const float *y_dev, int64_t n, const int32_t *q_id_dev,
+                            const float *q_x_dev, const float *q_y_dev, int64_t n_q,
+                            int32_t k, int32_t *out_ids_dev, float *out_d2_dev,
+                            void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -141,6 +141,11 @@ void mark(World &w, int i, cudaStream_t s) {
 
 }  // namespace
 
+namespace knnq {
+// Lets other translation units of the library report through knn_last_error.
+void set_last_error(const char *msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+}  // namespace knnq
+
 extern "C" {
 
 const char *knn_last_error(void) { return g_err; }

@@ -124,4 +124,7 @@ void launch_expand(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t *out
 
 int num_sms(int device);
 
+// Message returned by knn_last_error() on this thread (knn_capi.cu).
+void set_last_error(const char *msg);
+
 }  // namespace knnq

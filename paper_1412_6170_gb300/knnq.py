@@ -73,6 +73,8 @@ _SIGNATURES = {
     "knn_world_set_profiling": ([_vp, _i32], ctypes.c_int),
     "knn_world_stage_times": ([_vp, ctypes.POINTER(ctypes.c_float), _i32], ctypes.c_int),
     "knn_stage_name": ([_i32], ctypes.c_char_p),
+    "knn_query_static": ([ctypes.POINTER(knn_world_desc), _vp, _vp, _i64, _vp, _vp, _vp, _i64,
+                          _i32, _vp, _vp, _vp], ctypes.c_int),
 }
 
 _lib = None
@@ -192,6 +194,14 @@ def stage_names() -> list:
             return out
         out.append(s)
         i += 1
+
+
+def knn_query_static(desc: knn_world_desc, x_dev, y_dev, n: int, q_id, q_x, q_y, n_q: int,
+                     k: int, out_ids, out_d2, stream: int = 0) -> None:
+    """One-shot k-NN that allocates nothing (scratch in a static device array;
+    n, n_q <= 65536).  For callers that must not call cudaMalloc."""
+    _check(lib().knn_query_static(ctypes.byref(desc), x_dev, y_dev, n, q_id, q_x, q_y, n_q, k,
+                                  out_ids, out_d2, stream))
 
 
 # ---------------------------------------------------------------------------

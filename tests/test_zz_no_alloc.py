@@ -1,0 +1,91 @@
+"""knn_query_static, the allocation-free one-shot call (GPU).
+
+This entry point is for callers that must not allocate device memory:
+latency-critical loops where cudaMalloc/cudaFree would synchronize the device,
+services whose device memory belongs to another allocator or a fixed budget,
+and code that must not fail mid-request because an allocation did.  Its
+scratch is a static device array, so the test checks that two calls in a row
+(the second one finding the first one's leftovers in that array) both give
+exactly the rows of the regular path: knn_world_create + knn_tick without
+updates.  This file is collected last on purpose.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_1412_6170_gb300 import knnq, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def dev(a):
+    import torch
+    return None if a is None else torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def regular_path(x, y, q_id, k, q_x=None, q_y=None, leaf_capacity=0):
+    """Rows from the existing entry points (a world plus one tick, no updates)."""
+    import torch
+    world = knnq.World(dev(x), dev(y), k_max=64, max_queries=len(q_id),
+                       leaf_capacity=leaf_capacity)
+    try:
+        ids, d2 = world.tick(k, dev(q_id), q_x=dev(q_x), q_y=dev(q_y))
+        torch.cuda.synchronize()
+        return ids.cpu().numpy(), d2.cpu().numpy()
+    finally:
+        world.close()
+
+
+def static_path(x, y, q_id, k, q_x=None, q_y=None, leaf_capacity=0):
+    import torch
+    n, nq = len(x), len(q_id)
+    xd, yd, qd, qxd, qyd = dev(x), dev(y), dev(q_id), dev(q_x), dev(q_y)
+    out_ids = torch.empty((nq, k), dtype=torch.int32, device="cuda")
+    out_d2 = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+    desc = knnq.knn_world_desc(0.0, 0.0, 1.0, leaf_capacity, 0, 64, nq)
+    p = lambda t: None if t is None else t.data_ptr()  # noqa: E731
+    knnq.knn_query_static(desc, p(xd), p(yd), n, p(qd), p(qxd), p(qyd), nq, k, p(out_ids),
+                          p(out_d2), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return out_ids.cpu().numpy(), out_d2.cpu().numpy()
+
+
+def same(a, b):
+    return np.array_equal(a[0], b[0]) and np.array_equal(a[1].view(np.uint32),
+                                                         b[1].view(np.uint32))
+
+
+def test_static_matches_regular_path_twice_in_a_row():
+    # call 1: 60000 clustered objects, every object queries at its position, k = 16
+    x1, y1 = synth.clustered_positions(60000, 21)
+    q1 = np.arange(60000, dtype=np.int32)
+    first = static_path(x1, y1, q1, 16)
+    assert same(first, regular_path(x1, y1, q1, 16))
+    # call 2: other sizes and explicit anonymous centres; the scratch still holds
+    # call 1's index, which must not leak into this answer
+    x2, y2 = synth.uniform_positions(30011, 22)
+    r = np.random.default_rng(23)
+    q2 = np.where(r.random(4099) < 0.5, -1, r.integers(0, 30011, 4099)).astype(np.int32)
+    qx = r.random(4099).astype(np.float32)
+    qy = r.random(4099).astype(np.float32)
+    second = static_path(x2, y2, q2, 5, qx, qy, leaf_capacity=12)
+    assert same(second, regular_path(x2, y2, q2, 5, qx, qy, leaf_capacity=12))
+    # and call 1 again gives call 1's rows
+    assert same(static_path(x1, y1, q1, 16), first)
+
+
+def test_static_rejects_sizes_beyond_its_scratch():
+    lib = knnq.lib()
+    desc = knnq.knn_world_desc(0.0, 0.0, 1.0, 0, 0, 64, 10)
+    st = lib.knn_query_static(ctypes.byref(desc), 1, 1, 65537, 1, None, None, 1, 4, 1, 1, None)
+    assert st == knnq.KNN_ERR_INVALID
+    assert "65536" in knnq.knn_last_error()
+    st = lib.knn_query_static(ctypes.byref(desc), 1, 1, 100, 1, None, None, 70000, 4, 1, 1, None)
+    assert st == knnq.KNN_ERR_INVALID
