@@ -48,43 +48,73 @@ struct ExpandArgs {
 // every real key and marks an empty slot; 0 is below every real key.
 constexpr unsigned long long kPad = 0x7f800000FFFFFFFFull;
 
+// Per-lane candidate buffer (shared memory, kBufCap slots per lane):
+// candidates whose d^2 is within the lane's current k-th distance are appended
+// there and merged into the sorted register list kBatch at a time.
+constexpr int kBatch = 8;
+constexpr int kBufCap = 16;
+constexpr int kWarps = 4;  // warps per block
+
+struct WarpSmem {
+    float4 obj[32];                              // staged objects (x, y, id bits, -)
+    unsigned long long buf[kBufCap][32];         // [slot][lane]
+};
+
+__device__ __forceinline__ void cmpx(unsigned long long &x, unsigned long long &y) {
+    const bool s = y < x;
+    const unsigned long long lo = s ? y : x;
+    y = s ? x : y;
+    x = lo;
+}
+
+// Sort 8 keys ascending (19 comparators, depth 6).
+__device__ __forceinline__ void sort8(unsigned long long (&b)[kBatch]) {
+    cmpx(b[0], b[2]); cmpx(b[1], b[3]); cmpx(b[4], b[6]); cmpx(b[5], b[7]);
+    cmpx(b[0], b[4]); cmpx(b[1], b[5]); cmpx(b[2], b[6]); cmpx(b[3], b[7]);
+    cmpx(b[0], b[1]); cmpx(b[2], b[3]); cmpx(b[4], b[5]); cmpx(b[6], b[7]);
+    cmpx(b[2], b[4]); cmpx(b[3], b[5]);
+    cmpx(b[1], b[4]); cmpx(b[3], b[6]);
+    cmpx(b[1], b[2]); cmpx(b[3], b[4]); cmpx(b[5], b[6]);
+}
+
+// a (KC keys, ascending) := the KC smallest of a and b (8 keys, ascending):
+// c_i = min(a_i, b_{KC-1-i}) is bitonic and holds them; a bitonic merger sorts it.
 template <int KC>
-__device__ __forceinline__ void list_insert(unsigned long long (&a)[KC], unsigned long long key) {
+__device__ __forceinline__ void merge_batch(unsigned long long (&a)[KC],
+                                            const unsigned long long (&b)[kBatch]) {
 #pragma unroll
-    for (int i = KC - 1; i > 0; --i) {
-        const unsigned long long prev = a[i - 1];
-        const unsigned long long cur = a[i];
-        a[i] = key < prev ? prev : (key < cur ? key : cur);
+    for (int i = (KC > kBatch ? KC - kBatch : 0); i < KC; ++i) {
+        const unsigned long long v = b[KC - 1 - i];
+        a[i] = v < a[i] ? v : a[i];
     }
-    a[0] = key < a[0] ? key : a[0];
+#pragma unroll
+    for (int span = KC / 2; span >= 1; span >>= 1) {
+#pragma unroll
+        for (int i = 0; i < KC; ++i)
+            if ((i & span) == 0) cmpx(a[i], a[i + span]);
+    }
 }
 
 template <int KC>
-__device__ __forceinline__ void scan_range(const ExpandArgs &g, int32_t s, int32_t e, float qx,
-                                           float qy, int32_t qid, bool active,
-                                           unsigned long long (&lst)[KC]) {
-    const int lane = threadIdx.x & 31;
-    for (int32_t base = s; base < e; base += 32) {
-        const int32_t cnt = e - base < 32 ? e - base : 32;
-        float ox = 0.f, oy = 0.f;
-        int32_t oid = 0;
-        if (lane < cnt) {
-            ox = g.xs[base + lane];
-            oy = g.ys[base + lane];
-            oid = g.sid[base + lane];
-        }
-        for (int t = 0; t < cnt; ++t) {
-            const float bx = __shfl_sync(kFull, ox, t);
-            const float by = __shfl_sync(kFull, oy, t);
-            const int32_t bid = __shfl_sync(kFull, oid, t);
-            const float dx = __fsub_rn(qx, bx);
-            const float dy = __fsub_rn(qy, by);
-            const float d = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
-            const unsigned long long key =
-                ((unsigned long long)__float_as_uint(d) << 32) | (uint32_t)(bid + 1);
-            if (active && bid != qid && key < lst[KC - 1]) list_insert<KC>(lst, key);
-        }
+struct Lane {
+    unsigned long long lst[KC];  // ascending; slots below KC - k hold 0
+    float thr;                   // d^2 of the k-th entry (+inf while not full)
+    int count;                   // buffered candidates (slots 0 .. count-1)
+};
+
+// Merge every buffered candidate of every lane into its list, kBatch at a time.
+template <int KC>
+__device__ __forceinline__ void flush(Lane<KC> &L, WarpSmem &sm, int lane) {
+    for (int base = 0; __any_sync(kFull, L.count > base); base += kBatch) {
+        unsigned long long b[kBatch];
+#pragma unroll
+        for (int t = 0; t < kBatch; ++t)
+            b[t] = base + t < L.count ? sm.buf[base + t][lane] : kPad;
+        sort8(b);
+        merge_batch<KC>(L.lst, b);
     }
+    L.count = 0;
+    L.thr = __uint_as_float((uint32_t)(L.lst[KC - 1] >> 32));
 }
 
 // Leaf of the cell map closest (in Morton order) to a query key: the last leaf
@@ -124,9 +154,18 @@ __device__ __forceinline__ float warp_min(float v) {
     return v;
 }
 
+// One packet = one pass of a single loop.  Each iteration (a) merges the
+// buffers if some lane holds kBatch candidates, (b) finds the next objects to
+// test -- first the packet's own leaves widened to >= k+1 objects (the paper's
+// first iteration and left/right walk), then, ring by ring outward from the
+// packet, every leaf of the level-G cells that can still hold a better object
+// for some lane -- and (c) tests up to kBatch objects against every lane.
+// Keeping one copy of the scan and one of the merge keeps the kernel small.
 template <int KC>
-__global__ void __launch_bounds__(128) k_expand(const ExpandArgs g) {
+__global__ void __launch_bounds__(kWarps * 32) k_expand(const ExpandArgs g) {
+    __shared__ WarpSmem smem[kWarps];
     const int lane = threadIdx.x & 31;
+    WarpSmem &sm = smem[threadIdx.x >> 5];
     // device scalars are exact unless a look-back timed out; clamp anyway
     int32_t P = g.scalars[kScalarPackets];
     P = P < 0 ? 0 : (P > g.pk_cap ? (int32_t)g.pk_cap : P);
@@ -134,6 +173,7 @@ __global__ void __launch_bounds__(128) k_expand(const ExpandArgs g) {
     m = m < 0 ? 0 : (m > g.n ? (int32_t)g.n : m);
     const int k = g.k;
     const float kInf = __int_as_float(0x7f800000);
+    const int lim = (1 << g.G) - 1;
 
     for (;;) {
         int32_t p = 0;
@@ -151,14 +191,17 @@ __global__ void __launch_bounds__(128) k_expand(const ExpandArgs g) {
         const bool active = has && orig >= 0;
         const float qx = active ? g.qs_x[j] : 0.f;
         const float qy = active ? g.qs_y[j] : 0.f;
-        const int32_t qid = active ? g.qs_id[j] : -1;
+        // id + 1 of the issuer (excluded); 0 matches no object
+        const int32_t self = active ? g.qs_id[j] + 1 : 0;
         if (__ballot_sync(kFull, active) == 0u) continue;
 
-        unsigned long long lst[KC];
+        Lane<KC> L;
 #pragma unroll
-        for (int i = 0; i < KC; ++i) lst[i] = i < KC - k ? 0ull : kPad;
+        for (int i = 0; i < KC; ++i) L.lst[i] = i < KC - k ? 0ull : kPad;
+        L.thr = active ? kInf : -kInf;  // inactive lanes never buffer anything
+        L.count = 0;
 
-        // (1) leaves of the packet, widened along the leaf order to >= k+1 objects
+        // phase 1: the packet's own leaves, widened along the leaf order
         int32_t b_lo = leaf_near(g, g.qs_key[q0]);
         int32_t b_hi = leaf_near(g, g.qs_key[q0 + ql - 1]);
         b_hi = b_hi < m ? b_hi + 1 : m;
@@ -173,36 +216,55 @@ __global__ void __launch_bounds__(128) k_expand(const ExpandArgs g) {
                 left = !left;
             }
         }
-        scan_range<KC>(g, g.bstart[b_lo], g.bstart[b_hi], qx, qy, qid, active, lst);
+        const bool all_in_phase1 = b_lo == 0 && b_hi == m;
 
-        // (2) rectangle of cells that can hold a better object for some lane
-        if (!(b_lo == 0 && b_hi == m)) {
-            const float bx0 = warp_min(active ? qx : kInf), bx1 = warp_max(active ? qx : -kInf);
-            const float by0 = warp_min(active ? qy : kInf), by1 = warp_max(active ? qy : -kInf);
-            int cx0 = 0, cx1 = 0, cy0 = 0, cy1 = 0;
-            auto bound = [&](bool first) {
-                float kd = lst[KC - 1] == kPad ? kInf : __uint_as_float((uint32_t)(lst[KC - 1] >> 32));
-                const float R2 = warp_max(active ? kd : 0.f);
-                const int lim = (1 << g.G) - 1;
-                if (!(R2 < kInf)) {
-                    cx0 = 0; cx1 = lim; cy1 = lim;
-                    if (first) cy0 = 0;
-                    return;
-                }
+        int32_t cur = g.bstart[b_lo], end = g.bstart[b_hi];  // objects to test
+        int32_t staged = -1, staged_end = -1;                // objects held in sm.obj
+        int phase = 1;
+        // phase-2 cursor: ring r, position t on it, leaves [bcur, bend) of a cell
+        int r = 0, t = 0;
+        int32_t bcur = 0, bend = 0;
+        float bx0 = 0.f, bx1 = 0.f, by0 = 0.f, by1 = 0.f;
+        int ccx = 0, ccy = 0, cx0 = 0, cx1 = 0, cy0 = 0, cy1 = 0, rmax = 0;
+        auto bound = [&]() {
+            const float R2 = warp_max(active ? L.thr : 0.f);
+            if (!(R2 < kInf)) {
+                cx0 = 0; cx1 = lim; cy0 = 0; cy1 = lim;
+            } else {
                 // |q - p| per axis is at most sqrt(R2) (1 + 2^-22) for any object
                 // that can enter a list; round the box outward.
                 const float R = __fmul_ru(__fsqrt_ru(R2), 1.0000010f);
                 cx0 = cell_g(__fsub_rd(bx0, R), g.x0, g.scale_g, g.G);
                 cx1 = cell_g(__fadd_ru(bx1, R), g.x0, g.scale_g, g.G);
+                cy0 = cell_g(__fsub_rd(by0, R), g.y0, g.scale_g, g.G);
                 cy1 = cell_g(__fadd_ru(by1, R), g.y0, g.scale_g, g.G);
-                if (first) cy0 = cell_g(__fsub_rd(by0, R), g.y0, g.scale_g, g.G);
-            };
-            bound(true);
-            for (int cy = cy0; cy <= cy1; ++cy) {
-                for (int cx = cx0; cx <= cx1; ++cx) {
-                    const uint32_t c = interleave((uint32_t)cx, (uint32_t)cy);
-                    const int32_t lo = g.cb[c], hi = g.cb[c + 1];
-                    for (int32_t b = lo; b < hi; ++b) {
+            }
+            rmax = max(max(ccx - cx0, cx1 - ccx), max(ccy - cy0, cy1 - ccy));
+        };
+
+        for (;;) {
+            // (a) merge when a buffer is full, or when a list must fill up to bound the box
+            const bool need_thr = phase == 1 && cur >= end && !all_in_phase1;
+            if (__any_sync(kFull, L.count >= kBatch ||
+                                      (need_thr && L.count > 0 && !(L.thr < kInf))))
+                flush<KC>(L, sm, lane);
+            // (b) next objects
+            if (cur >= end) {
+                if (phase == 1) {
+                    if (all_in_phase1) break;
+                    phase = 2;
+                    bx0 = warp_min(active ? qx : kInf);
+                    bx1 = warp_max(active ? qx : -kInf);
+                    by0 = warp_min(active ? qy : kInf);
+                    by1 = warp_max(active ? qy : -kInf);
+                    ccx = cell_g(0.5f * (bx0 + bx1), g.x0, g.scale_g, g.G);
+                    ccy = cell_g(0.5f * (by0 + by1), g.y0, g.scale_g, g.G);
+                    bound();
+                }
+                bool found = false;
+                while (!found) {
+                    if (bcur < bend) {
+                        const int32_t b = bcur++;
                         if (b >= b_lo && b < b_hi) continue;
                         const float4 bb = g.baabb[b];
                         float dx = 0.f, dy = 0.f;
@@ -211,34 +273,80 @@ __global__ void __launch_bounds__(128) k_expand(const ExpandArgs g) {
                         if (qy < bb.y) dy = __fsub_rn(bb.y, qy);
                         else if (qy > bb.w) dy = __fsub_rn(qy, bb.w);
                         const float lb = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
-                        const float kd = lst[KC - 1] == kPad
-                                             ? kInf
-                                             : __uint_as_float((uint32_t)(lst[KC - 1] >> 32));
-                        const bool need = active && lb <= kd;
-                        if (__any_sync(kFull, need))
-                            scan_range<KC>(g, g.bstart[b], g.bstart[b + 1], qx, qy, qid, active,
-                                           lst);
+                        if (__any_sync(kFull, lb <= L.thr)) {
+                            cur = g.bstart[b];
+                            end = g.bstart[b + 1];
+                            found = true;
+                        }
+                        continue;
                     }
+                    const int per = r == 0 ? 1 : 8 * r;
+                    if (t >= per) {  // ring finished; the k-th distances only shrink
+                        ++r;
+                        t = 0;
+                        bound();
+                        if (r > rmax) break;
+                        continue;
+                    }
+                    int cx, cy;
+                    if (r == 0) { cx = ccx; cy = ccy; }
+                    else if (t < 2 * r + 1) { cx = ccx - r + t; cy = ccy - r; }
+                    else if (t < 4 * r + 2) { cx = ccx - r + (t - 2 * r - 1); cy = ccy + r; }
+                    else if (t < 6 * r + 1) { cx = ccx - r; cy = ccy - r + 1 + (t - 4 * r - 2); }
+                    else { cx = ccx + r; cy = ccy - r + 1 + (t - 6 * r - 1); }
+                    ++t;
+                    if (cx < cx0 || cx > cx1 || cy < cy0 || cy > cy1) continue;
+                    const uint32_t c = interleave((uint32_t)cx, (uint32_t)cy);
+                    bcur = g.cb[c];
+                    bend = g.cb[c + 1];
                 }
-                bound(false);  // the k-th distances only shrink
+                if (!found) break;
             }
+            // (c) test up to kBatch objects; stage 32 at a time through shared memory
+            if (cur < staged || cur >= staged_end) {
+                const int32_t cnt = end - cur < 32 ? end - cur : 32;
+                __syncwarp();
+                if (lane < cnt)
+                    sm.obj[lane] = make_float4(g.xs[cur + lane], g.ys[cur + lane],
+                                               __int_as_float(g.sid[cur + lane] + 1), 0.f);
+                __syncwarp();
+                staged = cur;
+                staged_end = cur + cnt;
+            }
+            const int n_here = staged_end - cur < kBatch ? staged_end - cur : kBatch;
+            const float thr = L.thr;
+            const int o0 = cur - staged;
+            for (int u = 0; u < n_here; ++u) {
+                const float4 o = sm.obj[o0 + u];
+                const float dx = __fsub_rn(qx, o.x);
+                const float dy = __fsub_rn(qy, o.y);
+                const float d = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+                const int32_t idp1 = __float_as_int(o.z);
+                if (d <= thr && idp1 != self) {
+                    sm.buf[L.count][lane] =
+                        ((unsigned long long)__float_as_uint(d) << 32) | (uint32_t)idp1;
+                    ++L.count;
+                }
+            }
+            cur += n_here;
         }
+        flush<KC>(L, sm, lane);
 
-        // (3) write the row in caller order
+        // write the row in caller order
         if (active) {
             int32_t *oi = g.out_ids + (int64_t)orig * k;
             float *od = g.out_d2 + (int64_t)orig * k;
 #pragma unroll
             for (int i = 0; i < KC; ++i) {
                 if (i >= KC - k) {
-                    const int r = i - (KC - k);
-                    const unsigned long long key = lst[i];
+                    const int rr = i - (KC - k);
+                    const unsigned long long key = L.lst[i];
                     if (key == kPad) {
-                        oi[r] = -1;
-                        od[r] = kInf;
+                        oi[rr] = -1;
+                        od[rr] = kInf;
                     } else {
-                        oi[r] = (int32_t)((uint32_t)key) - 1;
-                        od[r] = __uint_as_float((uint32_t)(key >> 32));
+                        oi[rr] = (int32_t)((uint32_t)key) - 1;
+                        od[rr] = __uint_as_float((uint32_t)(key >> 32));
                     }
                 }
             }
@@ -249,9 +357,9 @@ __global__ void __launch_bounds__(128) k_expand(const ExpandArgs g) {
 template <int KC>
 static void run(const ExpandArgs &a, int device, cudaStream_t s) {
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_expand<KC>, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_expand<KC>, kWarps * 32, 0);
     if (per_sm < 1) per_sm = 1;
-    k_expand<KC><<<num_sms(device) * per_sm, 128, 0, s>>>(a);
+    k_expand<KC><<<num_sms(device) * per_sm, kWarps * 32, 0, s>>>(a);
 }
 
 void launch_expand(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t *out_ids,
