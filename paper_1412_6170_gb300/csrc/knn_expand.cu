@@ -28,6 +28,7 @@ struct ExpandArgs {
     const int32_t *sid;
     const int32_t *bstart;
     const uint32_t *bcode;
+    const uint8_t *blevel;
     const float4 *baabb;
     const int32_t *cb;
     const float *qs_x, *qs_y;
@@ -38,7 +39,8 @@ struct ExpandArgs {
     uint32_t *pk_counter;
     int32_t *out_ids;
     float *out_d2;
-    float x0, y0, scale_g;
+    float x0, y0, scale_g, side;
+    float spec2;  // alpha^2 of the speculative first threshold (0: none)
     int L, G, k;
     int64_t n, n_q, pk_cap;
 };
@@ -49,10 +51,12 @@ struct ExpandArgs {
 constexpr unsigned long long kPad = 0x7f800000FFFFFFFFull;
 
 // Per-lane candidate buffer (shared memory, kBufCap slots per lane):
-// candidates whose d^2 is within the lane's current k-th distance are appended
-// there and merged into the sorted register list kBatch at a time.
+// candidates whose d^2 is within the lane's current threshold are appended
+// there and merged into the sorted register list kBatch at a time, once some
+// lane holds kFlushAt of them (late merges keep the batches full).
 constexpr int kBatch = 8;
-constexpr int kBufCap = 16;
+constexpr int kBufCap = 32;
+constexpr int kFlushAt = kBufCap - kBatch;
 constexpr int kWarps = 4;  // warps per block
 
 struct WarpSmem {
@@ -103,6 +107,8 @@ struct Lane {
 };
 
 // Merge every buffered candidate of every lane into its list, kBatch at a time.
+// The threshold becomes the list's k-th distance once the list is full (it
+// never rises above the threshold the walk started with).
 template <int KC>
 __device__ __forceinline__ void flush(Lane<KC> &L, WarpSmem &sm, int lane) {
     for (int base = 0; __any_sync(kFull, L.count > base); base += kBatch) {
@@ -114,7 +120,7 @@ __device__ __forceinline__ void flush(Lane<KC> &L, WarpSmem &sm, int lane) {
         merge_batch<KC>(L.lst, b);
     }
     L.count = 0;
-    L.thr = __uint_as_float((uint32_t)(L.lst[KC - 1] >> 32));
+    L.thr = fminf(L.thr, __uint_as_float((uint32_t)(L.lst[KC - 1] >> 32)));
 }
 
 // Leaf of the cell map closest (in Morton order) to a query key: the last leaf
@@ -195,12 +201,6 @@ __global__ void __launch_bounds__(kWarps * 32) k_expand(const ExpandArgs g) {
         const int32_t self = active ? g.qs_id[j] + 1 : 0;
         if (__ballot_sync(kFull, active) == 0u) continue;
 
-        Lane<KC> L;
-#pragma unroll
-        for (int i = 0; i < KC; ++i) L.lst[i] = i < KC - k ? 0ull : kPad;
-        L.thr = active ? kInf : -kInf;  // inactive lanes never buffer anything
-        L.count = 0;
-
         // phase 1: the packet's own leaves, widened along the leaf order
         int32_t b_lo = leaf_near(g, g.qs_key[q0]);
         int32_t b_hi = leaf_near(g, g.qs_key[q0 + ql - 1]);
@@ -218,12 +218,29 @@ __global__ void __launch_bounds__(kWarps * 32) k_expand(const ExpandArgs g) {
         }
         const bool all_in_phase1 = b_lo == 0 && b_hi == m;
 
-        int32_t cur = g.bstart[b_lo], end = g.bstart[b_hi];  // objects to test
-        int32_t staged = -1, staged_end = -1;                // objects held in sm.obj
-        int phase = 1;
+        // Speculative first threshold: alpha^2 times the area that holds k objects
+        // at the density of the packet's own leaves (objects / quadtree area).  A
+        // lane that finds fewer than k objects within it is redone exactly below.
+        float spec = kInf;
+        if (g.spec2 > 0.f && !all_in_phase1 && b_hi - b_lo <= 64) {
+            float area = 0.f;
+            for (int32_t b = b_lo; b < b_hi; ++b) area += ldexpf(1.f, -2 * (int)g.blevel[b]);
+            const float cnt1 = (float)(g.bstart[b_hi] - g.bstart[b_lo]);
+            spec = g.spec2 * (float)k * area * g.side * g.side / (3.14159265f * cnt1);
+        }
+
+        Lane<KC> L;
+#pragma unroll
+        for (int i = 0; i < KC; ++i) L.lst[i] = i < KC - k ? 0ull : kPad;
+        L.thr = active ? spec : -kInf;  // inactive lanes never buffer anything
+        L.count = 0;
+
+        int32_t cur, end;                     // objects to test
+        int32_t staged, staged_end;           // objects held in sm.obj
+        int phase;
         // phase-2 cursor: ring r, position t on it, leaves [bcur, bend) of a cell
-        int r = 0, t = 0;
-        int32_t bcur = 0, bend = 0;
+        int r, t;
+        int32_t bcur, bend;
         float bx0 = 0.f, bx1 = 0.f, by0 = 0.f, by1 = 0.f;
         int ccx = 0, ccy = 0, cx0 = 0, cx1 = 0, cy0 = 0, cy1 = 0, rmax = 0;
         auto bound = [&]() {
@@ -242,10 +259,20 @@ __global__ void __launch_bounds__(kWarps * 32) k_expand(const ExpandArgs g) {
             rmax = max(max(ccx - cx0, cx1 - ccx), max(ccy - cy0, cy1 - ccy));
         };
 
+        for (int attempt = 0;; ++attempt) {
+        cur = g.bstart[b_lo];
+        end = g.bstart[b_hi];
+        staged = -1;
+        staged_end = -1;
+        phase = 1;
+        r = 0;
+        t = 0;
+        bcur = 0;
+        bend = 0;
         for (;;) {
             // (a) merge when a buffer is full, or when a list must fill up to bound the box
             const bool need_thr = phase == 1 && cur >= end && !all_in_phase1;
-            if (__any_sync(kFull, L.count >= kBatch ||
+            if (__any_sync(kFull, L.count >= kFlushAt ||
                                       (need_thr && L.count > 0 && !(L.thr < kInf))))
                 flush<KC>(L, sm, lane);
             // (b) next objects
@@ -331,6 +358,23 @@ __global__ void __launch_bounds__(kWarps * 32) k_expand(const ExpandArgs g) {
             cur += n_here;
         }
         flush<KC>(L, sm, lane);
+        // a lane whose speculative threshold held fewer than k objects starts over
+        // with no threshold; lanes that are done take no part in the second walk
+        if (attempt == 0 && spec < kInf) {
+            const bool redo = active && L.lst[KC - 1] == kPad;
+            if (__any_sync(kFull, redo)) {
+                if (redo) {
+#pragma unroll
+                    for (int i = 0; i < KC; ++i) L.lst[i] = i < KC - k ? 0ull : kPad;
+                    L.thr = kInf;
+                } else {
+                    L.thr = -kInf;
+                }
+                continue;
+            }
+        }
+        break;
+        }
 
         // write the row in caller order
         if (active) {
@@ -386,6 +430,9 @@ void launch_expand(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t *out
     a.out_d2 = out_d2;
     a.x0 = w.desc.x0;
     a.y0 = w.desc.y0;
+    a.side = w.desc.side;
+    a.spec2 = 2.25f;
+    a.blevel = w.blevel;
     a.scale_g = ldexpf(w.scale, -(p.L - p.G));
     a.L = p.L;
     a.G = p.G;
