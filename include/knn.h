@@ -102,6 +102,19 @@ knn_status knn_tick(knn_world w, const int32_t *upd_id_dev, const float *upd_x_d
                     const float *q_x_dev, const float *q_y_dev, int64_t n_q, int32_t k,
                     int32_t *out_ids_dev, float *out_d2_dev, void *stream);
 
+/* Arguments of one world's tick, as for knn_tick (device pointers). */
+typedef struct {
+    const int32_t *upd_id_dev;
+    const float *upd_x_dev, *upd_y_dev;
+    int64_t n_upd;
+    const int32_t *q_id_dev;
+    const float *q_x_dev, *q_y_dev;
+    int64_t n_q;
+    int32_t k;
+    int32_t *out_ids_dev;
+    float *out_d2_dev;
+} knn_tick_args;
+
 /* The same tick with every array in host memory (pageable or pinned): the
  * inputs are copied to world-owned device staging buffers, the tick runs on
  * `stream`, the results are copied back, and the call returns after the
@@ -112,6 +125,19 @@ knn_status knn_tick_host(knn_world w, const int32_t *upd_id_host, const float *u
                          const float *q_x_host, const float *q_y_host, int64_t n_q,
                          int32_t k, int32_t *out_ids_host, float *out_d2_host,
                          void *stream);
+
+/* Batch processing over many worlds (Section 2.3 per world): one tick of every
+ * world in `worlds` (distinct handles on the current device), with args[i]
+ * for worlds[i] exactly as knn_tick takes them; the rows are bit-identical to
+ * separate knn_tick calls.  The batch is recorded into one CUDA graph (each
+ * world an independent chain, spread over internal streams between a fork and
+ * a join on `stream`) and launched as one graph; while the same worlds, sizes
+ * and pointers come back, the recorded graph is replayed without recording.
+ * Asynchronous on `stream`; a call that has to record the batch again does
+ * host work proportional to the number of worlds.  Not thread-safe with other
+ * batch calls on the same device. */
+knn_status knn_batch_tick(int32_t n_worlds, const knn_world *worlds, const knn_tick_args *args,
+                          void *stream);
 
 /* Waits for the world's last tick and reports device-detected problems since
  * the previous call: KNN_ERR_TIMEOUT, then KNN_ERR_DEVICE_INPUT (skipped
@@ -143,6 +169,17 @@ typedef struct {
 } knn_tuning;
 
 knn_status knn_world_set_tuning(knn_world w, const knn_tuning *t);
+/* Autotuner: runs `trials` ticks without updates for each of a small set of
+ * leaf capacities, cell-map levels and packet levels around the automatic
+ * choice, with the given queries (device arrays as for knn_tick; the output
+ * arrays receive the rows, identical for every setting), keeps the fastest
+ * in the world and writes it to *chosen (may be NULL).  Synchronizes
+ * `stream`.  The world's positions are unchanged. */
+knn_status knn_world_autotune(knn_world w, const int32_t *q_id_dev, const float *q_x_dev,
+                              const float *q_y_dev, int64_t n_q, int32_t k,
+                              int32_t *out_ids_dev, float *out_d2_dev, int32_t trials,
+                              knn_tuning *chosen, void *stream);
+
 /* The parameters the next tick with query count n_q and k will use. */
 knn_status knn_world_get_tuning(knn_world w, int64_t n_q, int32_t k, knn_tuning *out);
 

@@ -12,10 +12,6 @@
 using knnq::Plan;
 using knnq::World;
 
-struct knn_world_s {
-    World w;
-};
-
 namespace {
 
 thread_local char g_err[512] = "";
@@ -118,6 +114,7 @@ size_t carve(World &w, char *base) {
     w.status_words = (size_t)status;
     w.hist = c.take<uint32_t>(4 * 256);
     w.counters = c.take<uint32_t>(knnq::kNumCounters);
+    w.tickinfo = c.take<uint32_t>(4);
     w.scalars = c.take<int32_t>(knnq::kNumScalars);
     w.err = c.take<uint32_t>(4);
     return c.off;
@@ -144,6 +141,55 @@ void mark(World &w, int i, cudaStream_t s) {
 namespace knnq {
 // Lets other translation units of the library report through knn_last_error.
 void set_last_error(const char *msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+
+knn_status check_tick_args(const World &w, const knn_tick_args &a, const char *who) {
+    if (a.k < 1 || a.k > w.desc.k_max)
+        return fail(KNN_ERR_INVALID, "%s: k=%d outside [1, k_max=%d]", who, a.k, w.desc.k_max);
+    if (a.n_q < 0 || a.n_q > w.desc.max_queries)
+        return fail(KNN_ERR_INVALID, "%s: n_q=%lld outside [0, max_queries=%lld]", who,
+                    (long long)a.n_q, (long long)w.desc.max_queries);
+    if (a.n_upd < 0 || a.n_upd >= (1ll << 31))
+        return fail(KNN_ERR_INVALID, "%s: n_upd=%lld outside [0, 2^31)", who,
+                    (long long)a.n_upd);
+    if (a.n_upd > 0 && (!a.upd_id_dev || !a.upd_x_dev || !a.upd_y_dev))
+        return fail(KNN_ERR_INVALID, "%s: NULL update array with n_upd > 0", who);
+    if ((a.q_x_dev == nullptr) != (a.q_y_dev == nullptr))
+        return fail(KNN_ERR_INVALID, "%s: q_x and q_y must both be given or both NULL", who);
+    if (a.n_q > 0 && (!a.q_id_dev || !a.out_ids_dev || !a.out_d2_dev))
+        return fail(KNN_ERR_INVALID, "%s: NULL query or output array with n_q > 0", who);
+    return KNN_OK;
+}
+
+// The stages of one tick, in order, on stream s (no synchronisation, no allocation).
+void enqueue_tick(World &w, const knn_tick_args &a, cudaStream_t s, bool marks) {
+    const Plan p = make_plan(w, a.n_q, a.k);
+    const bool m = marks && w.profiling;
+    launch_tick_begin(w, s);
+    if (m) mark(w, 0, s);
+    launch_updates(w, a.upd_id_dev, a.upd_x_dev, a.upd_y_dev, a.n_upd, s);
+    if (m) mark(w, 1, s);
+    launch_object_sort(w, p, s);
+    if (m) mark(w, 2, s);
+    launch_leaves(w, p, s);
+    if (m) mark(w, 3, s);
+    if (a.n_q > 0) {
+        if (a.q_x_dev == nullptr)
+            launch_queries_at_issuers(w, p, a.q_id_dev, a.n_q, a.k, a.out_ids_dev,
+                                      a.out_d2_dev, s);
+        else
+            launch_queries_explicit(w, p, a.q_id_dev, a.q_x_dev, a.q_y_dev, a.n_q, a.k,
+                                    a.out_ids_dev, a.out_d2_dev, s);
+    }
+    if (m) mark(w, 4, s);
+    if (a.n_q > 0) launch_packets(w, p, a.n_q, s);
+    if (m) mark(w, 5, s);
+    if (a.n_q > 0) launch_expand(w, p, a.k, a.n_q, a.out_ids_dev, a.out_d2_dev, s);
+    if (m) mark(w, 6, s);
+    w.last_stream = s;
+    w.last_plan = p;
+}
+
+Plan plan_for(const World &w, int64_t n_q, int k) { return make_plan(w, n_q, k); }
 }  // namespace knnq
 
 extern "C" {
@@ -195,8 +241,12 @@ knn_status knn_world_create(const knn_world_desc *desc, const float *x_dev, cons
                     cudaGetErrorString(e));
     }
     carve(w, static_cast<char *>(w.arena));
+    knnq::prepare_kernels();
     cudaMemsetAsync(w.stamp, 0, sizeof(unsigned long long) * (size_t)n, s);
     cudaMemsetAsync(w.err, 0, 16, s);
+    cudaMemsetAsync(w.tickinfo, 0, 16, s);
+    // look-back status words must not hold anything that could match a live epoch
+    cudaMemsetAsync(w.status, 0, sizeof(uint64_t) * w.status_words, s);
     cudaMemsetAsync(w.scalars, 0, sizeof(int32_t) * knnq::kNumScalars, s);
     cudaMemcpyAsync(w.px, x_dev, sizeof(float) * (size_t)n, cudaMemcpyDeviceToDevice, s);
     cudaMemcpyAsync(w.py, y_dev, sizeof(float) * (size_t)n, cudaMemcpyDeviceToDevice, s);
@@ -259,46 +309,12 @@ knn_status knn_tick(knn_world h, const int32_t *upd_id, const float *upd_x, cons
                     int64_t n_upd, const int32_t *q_id, const float *q_x, const float *q_y,
                     int64_t n_q, int32_t k, int32_t *out_ids, float *out_d2, void *stream) {
     if (!h) return fail(KNN_ERR_INVALID, "knn_tick: NULL world");
+    knn_tick_args a{upd_id, upd_x, upd_y, n_upd, q_id, q_x, q_y, n_q, k, out_ids, out_d2};
+    const knn_status st = knnq::check_tick_args(h->w, a, "knn_tick");
+    if (st != KNN_OK) return st;
     World &w = h->w;
-    if (k < 1 || k > w.desc.k_max)
-        return fail(KNN_ERR_INVALID, "knn_tick: k=%d outside [1, k_max=%d]", k, w.desc.k_max);
-    if (n_q < 0 || n_q > w.desc.max_queries)
-        return fail(KNN_ERR_INVALID, "knn_tick: n_q=%lld outside [0, max_queries=%lld]",
-                    (long long)n_q, (long long)w.desc.max_queries);
-    if (n_upd < 0 || n_upd >= (1ll << 31))
-        return fail(KNN_ERR_INVALID, "knn_tick: n_upd=%lld outside [0, 2^31)", (long long)n_upd);
-    if (n_upd > 0 && (!upd_id || !upd_x || !upd_y))
-        return fail(KNN_ERR_INVALID, "knn_tick: NULL update array with n_upd > 0");
-    if ((q_x == nullptr) != (q_y == nullptr))
-        return fail(KNN_ERR_INVALID, "knn_tick: q_x and q_y must both be given or both NULL");
-    if (n_q > 0 && (!q_id || !out_ids || !out_d2))
-        return fail(KNN_ERR_INVALID, "knn_tick: NULL query or output array with n_q > 0");
-
     cudaSetDevice(w.device);
-    cudaStream_t s = (cudaStream_t)stream;
-    const Plan p = make_plan(w, n_q, k);
-    cudaMemsetAsync(w.counters, 0, sizeof(uint32_t) * knnq::kNumCounters, s);
-    cudaMemsetAsync(w.err + 2, 0, sizeof(uint32_t), s);
-    mark(w, 0, s);
-    knnq::launch_updates(w, upd_id, upd_x, upd_y, n_upd, s);
-    mark(w, 1, s);
-    knnq::launch_object_sort(w, p, s);
-    mark(w, 2, s);
-    knnq::launch_leaves(w, p, s);
-    mark(w, 3, s);
-    if (n_q > 0) {
-        if (q_x == nullptr)
-            knnq::launch_queries_at_issuers(w, p, q_id, n_q, k, out_ids, out_d2, s);
-        else
-            knnq::launch_queries_explicit(w, p, q_id, q_x, q_y, n_q, k, out_ids, out_d2, s);
-    }
-    mark(w, 4, s);
-    if (n_q > 0) knnq::launch_packets(w, p, n_q, s);
-    mark(w, 5, s);
-    if (n_q > 0) knnq::launch_expand(w, p, k, n_q, out_ids, out_d2, s);
-    mark(w, 6, s);
-    w.last_stream = s;
-    w.last_plan = p;
+    knnq::enqueue_tick(w, a, (cudaStream_t)stream, w.profiling);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "knn_tick launch");
     return KNN_OK;

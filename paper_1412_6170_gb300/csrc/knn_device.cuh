@@ -64,7 +64,8 @@ __device__ __forceinline__ int common_levels(uint32_t a, uint32_t b, int L) {
 // ---------------------------------------------------------------------------
 // Decoupled look-back (single pass scans).  A status word packs
 // [63:34] epoch (30 bits) | [33:32] flag | [31:0] value.  Every launch uses a
-// fresh epoch, so words left by earlier launches read as "not ready" and the
+// fresh epoch (the tick's device-side epoch base plus the launch's index in
+// the tick), so words left by earlier launches read as "not ready" and the
 // arrays never need clearing.
 constexpr uint32_t kFlagAgg = 1u, kFlagPrefix = 2u;
 

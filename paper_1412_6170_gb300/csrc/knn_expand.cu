@@ -399,10 +399,29 @@ __global__ void __launch_bounds__(kWarps * 32) k_expand(const ExpandArgs g) {
 }
 
 template <int KC>
+static int blocks_per_sm(int device) {
+    static int cached[64] = {0};
+    const int slot = device >= 0 && device < 64 ? device : 0;
+    int per_sm = cached[slot];
+    if (per_sm == 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_expand<KC>, kWarps * 32, 0);
+        if (per_sm < 1) per_sm = 1;
+        cached[slot] = per_sm;
+    }
+    return per_sm;
+}
+
+void prepare_expand(int device) {
+    blocks_per_sm<4>(device);
+    blocks_per_sm<8>(device);
+    blocks_per_sm<16>(device);
+    blocks_per_sm<32>(device);
+    blocks_per_sm<64>(device);
+}
+
+template <int KC>
 static void run(const ExpandArgs &a, int device, cudaStream_t s) {
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_expand<KC>, kWarps * 32, 0);
-    if (per_sm < 1) per_sm = 1;
+    const int per_sm = blocks_per_sm<KC>(device);
     k_expand<KC><<<num_sms(device) * per_sm, kWarps * 32, 0, s>>>(a);
 }
 

@@ -37,10 +37,28 @@ void launch_validate_positions(const float *x, const float *y, int64_t n, uint32
 // batch wins.  Pass 1 stamps each object with the largest (tick, index) of a
 // valid entry; pass 2 lets only that entry write.
 
+__global__ void k_tick_begin(uint32_t *tickinfo, uint32_t *counters, int n_counters,
+                             uint32_t *err) {
+    const int i = threadIdx.x;
+    if (i == 0) {
+        tickinfo[0] += 64u;  // room for 64 look-back launches per tick
+        tickinfo[1] += 1u;
+        err[2] = 0u;
+    }
+    if (i < n_counters) counters[i] = 0u;
+}
+
+void launch_tick_begin(World &w, cudaStream_t s) {
+    w.site = 0;
+    k_tick_begin<<<1, kNumCounters, 0, s>>>(w.tickinfo, w.counters, kNumCounters, w.err);
+    ++w.launches;
+}
+
 __global__ void k_update_stamp(const int32_t *__restrict__ id, const float *__restrict__ ux,
                                const float *__restrict__ uy, int64_t n_upd, int64_t n,
-                               unsigned long long *stamp, unsigned long long tick,
+                               unsigned long long *stamp, const uint32_t *__restrict__ tickinfo,
                                uint32_t *err) {
+    const unsigned long long tick = tickinfo[1];
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_upd;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t o = id[i];
@@ -59,7 +77,8 @@ __global__ void k_update_stamp(const int32_t *__restrict__ id, const float *__re
 __global__ void k_update_apply(const int32_t *__restrict__ id, const float *__restrict__ ux,
                                const float *__restrict__ uy, int64_t n_upd, int64_t n,
                                const unsigned long long *__restrict__ stamp,
-                               unsigned long long tick, float *px, float *py) {
+                               const uint32_t *__restrict__ tickinfo, float *px, float *py) {
+    const unsigned long long tick = tickinfo[1];
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_upd;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t o = id[i];
@@ -74,10 +93,9 @@ __global__ void k_update_apply(const int32_t *__restrict__ id, const float *__re
 void launch_updates(World &w, const int32_t *id, const float *ux, const float *uy,
                     int64_t n_upd, cudaStream_t s) {
     if (n_upd <= 0) return;
-    ++w.tick;
     const int g = grid_for(n_upd, 256, num_sms(w.device) * 8);
-    k_update_stamp<<<g, 256, 0, s>>>(id, ux, uy, n_upd, w.n, w.stamp, w.tick, w.err);
-    k_update_apply<<<g, 256, 0, s>>>(id, ux, uy, n_upd, w.n, w.stamp, w.tick, w.px, w.py);
+    k_update_stamp<<<g, 256, 0, s>>>(id, ux, uy, n_upd, w.n, w.stamp, w.tickinfo, w.err);
+    k_update_apply<<<g, 256, 0, s>>>(id, ux, uy, n_upd, w.n, w.stamp, w.tickinfo, w.px, w.py);
     w.launches += 2;
 }
 
@@ -151,8 +169,8 @@ __global__ void __launch_bounds__(256) k_query_keys_hist(
 __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     const uint32_t *__restrict__ kin, const int32_t *__restrict__ vin,
     uint32_t *__restrict__ kout, int32_t *__restrict__ vout, int64_t n, int shift,
-    const uint32_t *__restrict__ hist, uint64_t *status, uint32_t *ticket, uint32_t epoch,
-    uint32_t *err) {
+    const uint32_t *__restrict__ hist, uint64_t *status, uint32_t *ticket,
+    const uint32_t *__restrict__ tickinfo, uint32_t site, uint32_t *err) {
     __shared__ uint32_t s_wcnt[8][256];
     __shared__ uint32_t s_texcl[256];
     __shared__ uint32_t s_gbase[256];
@@ -166,6 +184,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     for (int i = tid; i < 8 * 256; i += kSortThreads) (&s_wcnt[0][0])[i] = 0;
     __syncthreads();
     const uint32_t tile = s_tile;
+    const uint32_t epoch = tickinfo[0] + site;
     const int64_t base = (int64_t)tile * kSortTile;
     const int64_t wbase = base + (int64_t)warp * (32 * kSortItems);
 
@@ -246,7 +265,7 @@ static void radix_sort(World &w, int64_t n, int passes, int counter_base, cudaSt
         k_onesweep<<<tiles, kSortThreads, 0, s>>>(w.key[src], w.val[src], w.key[dst],
                                                    w.val[dst], n, 8 * p, w.hist + 256 * p,
                                                    w.status, w.counters + counter_base + p,
-                                                   w.epoch++, w.err);
+                                                   w.tickinfo, w.site++, w.err);
         ++w.launches;
     }
 }
@@ -278,7 +297,7 @@ __global__ void __launch_bounds__(256) k_leaves(
     float *__restrict__ xs, float *__restrict__ ys, int32_t *__restrict__ sid,
     int32_t *__restrict__ inv, int32_t *__restrict__ bstart, uint32_t *__restrict__ bcode,
     uint8_t *__restrict__ blevel, int32_t *scalars, uint64_t *status, uint32_t *ticket,
-    uint32_t epoch, uint32_t *err) {
+    const uint32_t *__restrict__ tickinfo, uint32_t site, uint32_t *err) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t s_tile, s_tmp[8], s_excl;
     const int tid = threadIdx.x;
@@ -359,7 +378,7 @@ __global__ void __launch_bounds__(256) k_leaves(
     const uint32_t off = block_excl_scan_256(cnt, s_tmp, &s_total);
     tile_total = s_total;
     if (tid < 32) {
-        const uint32_t ex = lookback_warp(status, tile, epoch, tile_total, err);
+        const uint32_t ex = lookback_warp(status, tile, tickinfo[0] + site, tile_total, err);
         if (tid == 0) s_excl = ex;
     }
     __syncthreads();
@@ -451,15 +470,11 @@ void launch_leaves(World &w, const Plan &p, cudaStream_t s) {
     const int r = p.passes & 1;
     const int tiles = (int)((w.n + kLeafTile - 1) / kLeafTile);
     const size_t sm = leaves_smem(p.th);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_leaves, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)leaves_smem(kMaxLeafCapacity));
-        attr_set = true;
-    }
+    prepare_kernels();
     k_leaves<<<tiles, 256, sm, s>>>(w.key[r], w.val[r], w.n, p.L, p.th, p.G, w.px, w.py, w.xs,
                                     w.ys, w.sid, w.inv, w.bstart, w.bcode, w.blevel, w.scalars,
-                                    w.status, w.counters + kCtrLeaves, w.epoch++, w.err);
+                                    w.status, w.counters + kCtrLeaves, w.tickinfo, w.site++,
+                                    w.err);
     const int g = grid_for(w.n, 256, num_sms(w.device) * 8);
     k_leaf_aabb<<<g, 256, 0, s>>>(w.bstart, w.scalars, w.xs, w.ys, w.baabb, w.n);
     const int64_t ncell = 1ll << (2 * p.G);
@@ -473,8 +488,9 @@ void launch_leaves(World &w, const Plan &p, cudaStream_t s) {
 
 __global__ void __launch_bounds__(256) k_scan_excl(const int32_t *in, int32_t *out, int64_t len,
                                                    int32_t *total, uint64_t *status,
-                                                   uint32_t *ticket, uint32_t epoch,
-                                                   uint32_t *err) {
+                                                   uint32_t *ticket,
+                                                   const uint32_t *__restrict__ tickinfo,
+                                                   uint32_t site, uint32_t *err) {
     __shared__ uint32_t s_tile, s_tmp[8], s_total, s_excl;
     const int tid = threadIdx.x;
     if (tid == 0) s_tile = atomicAdd(ticket, 1u);
@@ -490,7 +506,7 @@ __global__ void __launch_bounds__(256) k_scan_excl(const int32_t *in, int32_t *o
     }
     const uint32_t off = block_excl_scan_256(sum, s_tmp, &s_total);
     if (tid < 32) {
-        const uint32_t ex = lookback_warp(status, tile, epoch, s_total, err);
+        const uint32_t ex = lookback_warp(status, tile, tickinfo[0] + site, s_total, err);
         if (tid == 0) s_excl = ex;
     }
     __syncthreads();
@@ -507,7 +523,7 @@ static void scan_excl(World &w, const int32_t *in, int32_t *out, int64_t len, in
                       int counter, cudaStream_t s) {
     const int tiles = (int)((len + kScanTile - 1) / kScanTile);
     k_scan_excl<<<tiles, 256, 0, s>>>(in, out, len, total, w.status, w.counters + counter,
-                                      w.epoch++, w.err);
+                                      w.tickinfo, w.site++, w.err);
     ++w.launches;
 }
 
@@ -656,6 +672,18 @@ void launch_packets(World &w, const Plan &p, int64_t n_q, cudaStream_t s) {
     k_packets<<<g, 256, 0, s>>>(w.qcs, w.pk_off, ncell, packet_capacity(w), w.pk_start,
                                 w.pk_len);
     w.launches += 2;
+}
+
+void prepare_kernels() {
+    static bool done[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || done[dev]) return;
+    cudaFuncSetAttribute(k_leaves, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)leaves_smem(kMaxLeafCapacity));
+    num_sms(dev);          // fill the per-device caches now: the query APIs
+    prepare_expand(dev);   // must not run while a batch is being recorded
+    done[dev] = true;
 }
 
 int num_sms(int device) {

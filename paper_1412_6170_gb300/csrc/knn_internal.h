@@ -46,8 +46,7 @@ struct World {
     int L = 16;
     float scale = 0.f;     // 2^L / side, binary32
     knn_tuning tuning{};   // user overrides (0 = auto)
-    uint32_t epoch = 1;    // look-back epoch, fresh per single-pass launch
-    uint64_t tick = 0;     // update stamp counter
+    uint32_t site = 0;     // look-back launch index within the current tick
     cudaStream_t last_stream = nullptr;
     Plan last_plan{};
 
@@ -77,6 +76,9 @@ struct World {
     size_t status_words = 0;
     uint32_t *hist = nullptr;
     uint32_t *counters = nullptr;
+    // [0] look-back epoch base, [1] update stamp tick; advanced on the device by
+    // k_tick_begin so that a recorded tick can be replayed (CUDA graphs)
+    uint32_t *tickinfo = nullptr;
     int32_t *scalars = nullptr;
     uint32_t *err = nullptr;
 
@@ -95,6 +97,15 @@ struct World {
     int64_t max_rows() const { return n > desc.max_queries ? n : desc.max_queries; }
 };
 
+}  // namespace knnq
+
+// The opaque handle of the C ABI.
+struct knn_world_s {
+    knnq::World w;
+};
+
+namespace knnq {
+
 // Packets never exceed n_q/32 + (non-empty packet cells) <= n_q + n_q/32 + 1.
 inline int64_t packet_capacity(const World &w) {
     return w.desc.max_queries + w.desc.max_queries / 32 + 2;
@@ -105,6 +116,8 @@ inline int64_t packet_capacity(const World &w) {
 // ---- launchers (knn_index.cu) ----------------------------------------------
 void launch_validate_positions(const float *x, const float *y, int64_t n, uint32_t *flag,
                                cudaStream_t s);
+// Start of a tick: advance epoch base and stamp tick, clear tickets and the abort flag.
+void launch_tick_begin(World &w, cudaStream_t s);
 void launch_updates(World &w, const int32_t *id, const float *ux, const float *uy,
                     int64_t n_upd, cudaStream_t s);
 void launch_object_sort(World &w, const Plan &p, cudaStream_t s);
@@ -123,8 +136,19 @@ void launch_expand(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t *out
                    float *out_d2, cudaStream_t s);
 
 int num_sms(int device);
+// One-time kernel attributes and cached device queries (called outside any
+// stream capture).
+void prepare_kernels();
+void prepare_expand(int device);
 
 // Message returned by knn_last_error() on this thread (knn_capi.cu).
 void set_last_error(const char *msg);
+// Host-side argument checks of one tick (sets the error message).
+knn_status check_tick_args(const World &w, const knn_tick_args &a, const char *who);
+// Enqueue every stage of one tick on s; `marks` records stage events when
+// the world's profiling is on.
+void enqueue_tick(World &w, const knn_tick_args &a, cudaStream_t s, bool marks);
+// The index / expansion parameters a tick with n_q queries and this k uses.
+Plan plan_for(const World &w, int64_t n_q, int k);
 
 }  // namespace knnq

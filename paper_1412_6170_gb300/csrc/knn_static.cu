@@ -28,13 +28,12 @@ constexpr int kStaticMaxGridLevel = 8;
 
 static __device__ __align__(256) unsigned char g_scratch[kStaticScratchBytes];
 
-// Host-side state per device: the scratch array's device address (looked up
-// once with cudaGetSymbolAddress, with that device current) and the look-back
-// epoch, which must keep increasing across calls because the status words
-// left in the scratch by the previous call are never cleared.
+// Host-side state per device: the scratch array's device address, looked up
+// once with cudaGetSymbolAddress with that device current.  The look-back
+// epoch lives in the scratch itself (it starts at zero and keeps increasing
+// across calls, because status words left by earlier calls are never cleared).
 struct Slot {
     unsigned char *base = nullptr;
-    uint32_t epoch = 1;
 };
 Slot g_slots[64];
 std::mutex g_mu;
@@ -97,6 +96,7 @@ size_t cut_scratch(knnq::World &w, unsigned char *base, int64_t n_q) {
     w.status_words = (size_t)status;
     w.hist = c.take<uint32_t>(4 * 256);
     w.counters = c.take<uint32_t>(knnq::kNumCounters);
+    w.tickinfo = c.take<uint32_t>(4);
     w.scalars = c.take<int32_t>(knnq::kNumScalars);
     w.err = c.take<uint32_t>(4);
     return c.off;
@@ -162,7 +162,6 @@ extern "C" knn_status knn_query_static(const knn_world_desc *desc, const float *
     // positions are only read (no updates in a one-shot call)
     w.px = const_cast<float *>(x_dev);
     w.py = const_cast<float *>(y_dev);
-    w.epoch = slot.epoch;
 
     knnq::Plan p{};
     p.L = w.L;
@@ -173,10 +172,11 @@ extern "C" knn_status knn_query_static(const knn_world_desc *desc, const float *
     p.Gp = clampi(round_log4((double)(n_q > 0 ? n_q : 1) / 48.0), 0, p.G);
 
     cudaStream_t s = (cudaStream_t)stream;
-    // what must start at zero: tile tickets, error words, device scalars
-    cudaMemsetAsync(w.counters, 0, sizeof(uint32_t) * knnq::kNumCounters, s);
+    // what must start at zero: error words and device scalars; tile tickets
+    // are cleared (and the epoch advanced) by the tick-begin kernel
     cudaMemsetAsync(w.err, 0, sizeof(uint32_t) * 4, s);
     cudaMemsetAsync(w.scalars, 0, sizeof(int32_t) * knnq::kNumScalars, s);
+    knnq::launch_tick_begin(w, s);
     knnq::launch_object_sort(w, p, s);
     knnq::launch_leaves(w, p, s);
     if (n_q > 0) {
@@ -188,7 +188,6 @@ extern "C" knn_status knn_query_static(const knn_world_desc *desc, const float *
         knnq::launch_packets(w, p, n_q, s);
         knnq::launch_expand(w, p, k, n_q, out_ids_dev, out_d2_dev, s);
     }
-    slot.epoch = w.epoch;
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return bad(KNN_ERR_CUDA, cudaGetErrorString(e));
     return KNN_OK;

@@ -54,6 +54,12 @@ _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
 _i32 = ctypes.c_int32
 
+
+class knn_tick_args(ctypes.Structure):
+    _fields_ = [("upd_id_dev", _vp), ("upd_x_dev", _vp), ("upd_y_dev", _vp), ("n_upd", _i64),
+                ("q_id_dev", _vp), ("q_x_dev", _vp), ("q_y_dev", _vp), ("n_q", _i64),
+                ("k", _i32), ("out_ids_dev", _vp), ("out_d2_dev", _vp)]
+
 _SIGNATURES = {
     "knn_world_create": ([ctypes.POINTER(knn_world_desc), _vp, _vp, _i64, _vp,
                           ctypes.POINTER(_vp)], ctypes.c_int),
@@ -73,6 +79,10 @@ _SIGNATURES = {
     "knn_world_set_profiling": ([_vp, _i32], ctypes.c_int),
     "knn_world_stage_times": ([_vp, ctypes.POINTER(ctypes.c_float), _i32], ctypes.c_int),
     "knn_stage_name": ([_i32], ctypes.c_char_p),
+    "knn_batch_tick": ([_i32, ctypes.POINTER(_vp), ctypes.POINTER(knn_tick_args), _vp],
+                       ctypes.c_int),
+    "knn_world_autotune": ([_vp, _vp, _vp, _vp, _i64, _i32, _vp, _vp, _i32,
+                            ctypes.POINTER(knn_tuning), _vp], ctypes.c_int),
     "knn_query_static": ([ctypes.POINTER(knn_world_desc), _vp, _vp, _i64, _vp, _vp, _vp, _i64,
                           _i32, _vp, _vp, _vp], ctypes.c_int),
 }
@@ -196,6 +206,33 @@ def stage_names() -> list:
         i += 1
 
 
+def knn_batch_tick(worlds, args, stream: int = 0) -> None:
+    """One tick of every world in ``worlds`` (handles) with ``args`` (knn_tick_args),
+    recorded into and launched as one CUDA graph."""
+    n = len(worlds)
+    wa = (_vp * n)(*worlds)
+    aa = (knn_tick_args * n)(*args)
+    _check(lib().knn_batch_tick(n, wa, aa, stream))
+
+
+def knn_world_autotune(w: int, q_id, q_x, q_y, n_q: int, k: int, out_ids, out_d2,
+                       trials: int = 2, stream: int = 0) -> dict:
+    t = knn_tuning()
+    _check(lib().knn_world_autotune(w, q_id, q_x, q_y, n_q, k, out_ids, out_d2, trials,
+                                    ctypes.byref(t), stream))
+    return {"leaf_capacity": t.leaf_capacity, "grid_level": t.grid_level,
+            "packet_level": t.packet_level}
+
+
+def tick_args(k: int, q_id=None, upd_id=None, upd_x=None, upd_y=None, q_x=None, q_y=None,
+              out_ids=None, out_d2=None) -> knn_tick_args:
+    """knn_tick_args from torch tensors (or None)."""
+    return knn_tick_args(_ptr(upd_id), _ptr(upd_x), _ptr(upd_y),
+                         0 if upd_id is None else int(upd_id.shape[0]), _ptr(q_id), _ptr(q_x),
+                         _ptr(q_y), 0 if q_id is None else int(q_id.shape[0]), k,
+                         _ptr(out_ids), _ptr(out_d2))
+
+
 def knn_query_static(desc: knn_world_desc, x_dev, y_dev, n: int, q_id, q_x, q_y, n_q: int,
                      k: int, out_ids, out_d2, stream: int = 0) -> None:
     """One-shot k-NN that allocates nothing (scratch in a static device array;
@@ -288,6 +325,14 @@ class World:
         y = torch.empty(self.n, dtype=torch.float32, device=self.device)
         knn_world_positions(self.handle, x.data_ptr(), y.data_ptr(), _stream(stream))
         return x, y
+
+    def autotune(self, k: int, q_id, q_x=None, q_y=None, trials: int = 2, stream=None) -> dict:
+        import torch
+        n_q = int(q_id.shape[0])
+        oi = torch.empty((max(n_q, 1), k), dtype=torch.int32, device=self.device)
+        od = torch.empty((max(n_q, 1), k), dtype=torch.float32, device=self.device)
+        return knn_world_autotune(self.handle, _ptr(q_id), _ptr(q_x), _ptr(q_y), n_q, k,
+                                  oi.data_ptr(), od.data_ptr(), trials, _stream(stream))
 
     def launches(self) -> int:
         return knn_world_launches(self.handle)

@@ -189,3 +189,32 @@ def skewed_moving(n: int = 4_000_000, k: int = 32, ticks: int = 10, seed: int = 
 
 def world_positions(n: int, seed: int, clustered: bool) -> tuple[np.ndarray, np.ndarray]:
     return clustered_positions(n, seed) if clustered else uniform_positions(n, seed)
+
+
+def many_worlds(n_worlds: int = 256, seed: int = 0, n_lo: int = 1_000, n_hi: int = 200_000,
+                ks=(4, 8, 16, 32), ticks: int = 2, sigma: float = 1e-3,
+                query_frac=(1.0, 1.0)) -> list:
+    """Independent worlds of uneven size: object counts log-uniform in [n_lo, n_hi],
+    uniform or clustered (as the 4M skewed workload) by a coin flip, k drawn from ``ks``,
+    a query fraction drawn uniformly from ``query_frac``; every tick moves every object
+    by N(0, sigma) and a fresh random subset (or all) of the objects query."""
+    u = uniform_f64(seed, 201, 4 * n_worlds).reshape(n_worlds, 4)
+    out = []
+    for i in range(n_worlds):
+        n = int(round(np.exp(np.log(n_lo) + u[i, 0] * (np.log(n_hi) - np.log(n_lo)))))
+        clustered = bool(u[i, 1] < 0.5)
+        k = int(ks[min(len(ks) - 1, int(u[i, 2] * len(ks)))])
+        qf = query_frac[0] + u[i, 3] * (query_frac[1] - query_frac[0])
+        ws = seed * 7919 + i + 1
+        x, y = world_positions(n, ws, clustered)
+        w = Workload(f"world {i}: n={n} k={k} {'clustered' if clustered else 'uniform'}",
+                     n, k, x, y)
+        ids = np.arange(n, dtype=np.int32)
+        cx, cy = x, y
+        nq = max(1, int(round(n * qf)))
+        for t in range(1, ticks + 1):
+            cx, cy = random_walk(cx, cy, sigma, ws, t)
+            q = ids if nq == n else random_subset(n, nq, ws, t)
+            w.ticks.append(Tick(ids, cx, cy, q, k))
+        out.append(w)
+    return out
