@@ -139,6 +139,56 @@ knn_status knn_tick_host(knn_world w, const int32_t *upd_id_host, const float *u
 knn_status knn_batch_tick(int32_t n_worlds, const knn_world *worlds, const knn_tick_args *args,
                           void *stream);
 
+/* ---- serving ---------------------------------------------------------------
+ * A request loop over many resident worlds (Sections 2.2-2.3: ticks of
+ * updates and queries under a latency requirement).  A request is one world's
+ * tick; its latency runs from knn_server_submit to the moment the dispatcher
+ * sees the tick complete on the device.  The server keeps every world's
+ * positions resident and gives a world its tick scratch only while it has
+ * work: a dispatcher thread admits the oldest request of any idle world as
+ * soon as one of n_slots streams is free and the world's scratch fits in
+ * hbm_budget_bytes, evicting idle worlds' scratch (least recently used first)
+ * when needed.  Requests of different worlds overlap on the GPU; requests of
+ * one world run in submission order.  Every request gives exactly the rows
+ * knn_tick would. */
+typedef struct knn_server_s *knn_server;
+
+typedef struct {
+    int32_t n_slots;            /* requests on the GPU at once (one stream each), 1..32 */
+    int32_t reserved;
+    int64_t hbm_budget_bytes;   /* device memory for worlds' tick scratch; 0 = no limit */
+} knn_server_desc;
+
+typedef struct {
+    int32_t worlds, resident_worlds;  /* registered / holding scratch now */
+    int64_t scratch_bytes;            /* scratch the server holds now */
+    int64_t admitted, completed, evictions, pending;
+} knn_server_counters;
+
+/* Start a server on the current device (creates its streams and dispatcher). */
+knn_status knn_server_create(const knn_server_desc *desc, knn_server *out);
+/* Register a world exactly as knn_world_create describes it; only its
+ * positions are allocated now.  KNN_ERR_ADMISSION when the world's tick
+ * scratch could never fit in the budget.  *world_index receives its index. */
+knn_status knn_server_add_world(knn_server s, const knn_world_desc *desc, const float *x_dev,
+                                const float *y_dev, int64_t n, int32_t *world_index);
+/* Queue one tick of a world (arguments as knn_tick; the arrays must stay
+ * valid, and the outputs unread, until the request is done). */
+knn_status knn_server_submit(knn_server s, int32_t world_index, const knn_tick_args *args,
+                             int64_t *request_id);
+/* State of a request (0 queued, 1 running, 2 done, 3 failed) and, once done,
+ * its latency in milliseconds (else -1). */
+knn_status knn_server_poll(knn_server s, int64_t request_id, int32_t *state,
+                           double *latency_ms);
+/* Block until a request is done; returns its latency. */
+knn_status knn_server_wait(knn_server s, int64_t request_id, double *latency_ms);
+knn_status knn_server_stats(knn_server s, knn_server_counters *out);
+/* Wait for a world's queued requests and report its device-detected input
+ * problems as knn_tick_status does. */
+knn_status knn_server_world_status(knn_server s, int32_t world_index, uint32_t *bits_out);
+/* Finish every queued request, stop the dispatcher and free everything. */
+knn_status knn_server_destroy(knn_server s);
+
 /* Waits for the world's last tick and reports device-detected problems since
  * the previous call: KNN_ERR_TIMEOUT, then KNN_ERR_DEVICE_INPUT (skipped
  * updates, non-finite coordinates, invalid queries), else KNN_OK.  Clears the
@@ -157,7 +207,9 @@ const char *knn_last_error(void);
 /* Index and expansion parameters; none of them changes any result.
  * leaf_capacity: th_quad (Section 4.1.1), 1..4096.
  * grid_level: level G of the uniform cell map over the leaves (the paper's
- *   z_map, Section 4.1.1); leaves are never coarser than G.  1..10.
+ *   z_map, Section 4.1.1); leaves are never coarser than G.  1..gmax, where a
+ *   world of n objects has gmax = min(10, max_depth, the smallest g with
+ *   4^g >= 4n) (a finer map never pays off); larger values are rejected.
  * packet_level: queries are packed 32 to a warp within one cell of this
  *   level (<= grid_level).
  * Any field set to 0 keeps (or restores) the automatic choice. */

@@ -181,7 +181,7 @@ extern "C" knn_status knn_world_autotune(knn_world h, const int32_t *q_id_dev,
     automatic.leaf_capacity = saved.leaf_capacity;  // a capacity fixed at creation stays
     w.tuning = automatic;
     const knnq::Plan p0 = knnq::plan_for(w, n_q, k);
-    const int gmax = p0.L < knnq::kMaxGridLevel ? p0.L : knnq::kMaxGridLevel;
+    const int gmax = w.gmax;
 
     // candidates: leaf capacity x cell-map level x packet level around the automatic plan
     std::vector<knn_tuning> cand;

@@ -49,7 +49,7 @@ Plan make_plan(const World &w, int64_t n_q, int k) {
     p.passes = (2 * p.L + 7) / 8;
     p.th = w.tuning.leaf_capacity > 0 ? w.tuning.leaf_capacity : clampi(2 * k, 8, 256);
     p.th = clampi(p.th, 1, knnq::kMaxLeafCapacity);
-    const int gmax = p.L < knnq::kMaxGridLevel ? p.L : knnq::kMaxGridLevel;
+    const int gmax = w.gmax;
     int G = w.tuning.grid_level > 0 ? w.tuning.grid_level
                                     : round_log4(2.0 * (double)w.n / (double)p.th);
     p.G = clampi(G, 1, gmax);
@@ -72,20 +72,34 @@ struct Carve {
     }
 };
 
-// Lay out (base == nullptr: size only) every tick buffer in one arena.
-size_t carve(World &w, char *base) {
-    const int64_t n = w.n, R = w.max_rows(), Q = w.desc.max_queries;
-    const int64_t ncell = (1ll << (2 * knnq::kMaxGridLevel)) + 2;
-    const int64_t sort_tiles = (R + knnq::kSortTile - 1) / knnq::kSortTile;
-    int64_t status = sort_tiles * 256;
-    const int64_t others[] = {(n + knnq::kLeafTile - 1) / knnq::kLeafTile,
-                              (n + 1 + knnq::kScanTile - 1) / knnq::kScanTile,
-                              (ncell + knnq::kScanTile - 1) / knnq::kScanTile};
-    for (int64_t o : others) status = status > o ? status : o;
+}  // namespace
+
+namespace knnq {
+
+// Resident part: positions, update stamps, tick counters, error words.
+size_t carve_resident(World &w, char *base) {
+    const int64_t n = w.n;
     Carve c{base};
     w.px = c.take<float>(n);
     w.py = c.take<float>(n);
     w.stamp = c.take<unsigned long long>(n);
+    w.tickinfo = c.take<uint32_t>(4);
+    w.err = c.take<uint32_t>(4);
+    return c.off;
+}
+
+// Tick scratch: sort buffers, leaf-ordered SoA, leaves, cell map, queries,
+// packets, look-back status words, histograms and tickets.
+size_t carve_scratch(World &w, char *base) {
+    const int64_t n = w.n, R = w.max_rows(), Q = w.desc.max_queries;
+    const int64_t ncell = (1ll << (2 * w.gmax)) + 2;
+    const int64_t sort_tiles = (R + kSortTile - 1) / kSortTile;
+    int64_t status = sort_tiles * 256;
+    const int64_t others[] = {(n + kLeafTile - 1) / kLeafTile,
+                              (n + 1 + kScanTile - 1) / kScanTile,
+                              (ncell + kScanTile - 1) / kScanTile};
+    for (int64_t o : others) status = status > o ? status : o;
+    Carve c{base};
     w.key[0] = c.take<uint32_t>(R);
     w.key[1] = c.take<uint32_t>(R);
     w.val[0] = c.take<int32_t>(R);
@@ -113,15 +127,86 @@ size_t carve(World &w, char *base) {
     w.status = c.take<uint64_t>(status);
     w.status_words = (size_t)status;
     w.hist = c.take<uint32_t>(4 * 256);
-    w.counters = c.take<uint32_t>(knnq::kNumCounters);
-    w.tickinfo = c.take<uint32_t>(4);
-    w.scalars = c.take<int32_t>(knnq::kNumScalars);
-    w.err = c.take<uint32_t>(4);
+    w.counters = c.take<uint32_t>(kNumCounters);
+    w.scalars = c.take<int32_t>(kNumScalars);
     return c.off;
 }
 
+void world_attach_scratch(World &w, void *base, cudaStream_t s) {
+    w.arena = base;
+    carve_scratch(w, static_cast<char *>(base));
+    cudaMemsetAsync(w.scalars, 0, sizeof(int32_t) * kNumScalars, s);
+    // look-back status words must not hold anything that could match a live epoch
+    cudaMemsetAsync(w.status, 0, sizeof(uint64_t) * w.status_words, s);
+}
+
+knn_status world_init_resident(World &w, const knn_world_desc *desc, const float *x_dev,
+                               const float *y_dev, int64_t n, cudaStream_t s) {
+    if (!desc) return fail(KNN_ERR_INVALID, "NULL world description");
+    if (!(desc->side > 0.f) || !std::isfinite(desc->side) || !std::isfinite(desc->x0) ||
+        !std::isfinite(desc->y0))
+        return fail(KNN_ERR_INVALID, "world: domain must be finite with side > 0");
+    if (n < 1 || n > (1ll << 30))
+        return fail(KNN_ERR_INVALID, "world: n=%lld outside [1, 2^30]", (long long)n);
+    if (desc->k_max < 1 || desc->k_max > kMaxK)
+        return fail(KNN_ERR_INVALID, "world: k_max=%d outside [1, 64]", desc->k_max);
+    if (desc->max_depth < 0 || desc->max_depth > 16)
+        return fail(KNN_ERR_INVALID, "world: max_depth=%d outside [0, 16]", desc->max_depth);
+    if (desc->leaf_capacity < 0 || desc->leaf_capacity > kMaxLeafCapacity)
+        return fail(KNN_ERR_INVALID, "world: leaf_capacity=%d outside [0, 4096]",
+                    desc->leaf_capacity);
+    if (desc->max_queries < 0 || desc->max_queries > (1ll << 30))
+        return fail(KNN_ERR_INVALID, "world: max_queries outside [0, 2^30]");
+    if (!x_dev || !y_dev) return fail(KNN_ERR_INVALID, "world: NULL positions");
+    cudaGetDevice(&w.device);
+    w.desc = *desc;
+    w.n = n;
+    w.L = desc->max_depth > 0 ? desc->max_depth : 16;
+    // a cell map with more than ~4 cells per object never pays off
+    int g = 1;
+    while (g < kMaxGridLevel && g < w.L && (1ll << (2 * g)) < 4 * n) ++g;
+    w.gmax = g;
+    w.scale = (float)(1u << w.L) / desc->side;
+    w.tuning.leaf_capacity = desc->leaf_capacity;
+    w.res_bytes = carve_resident(w, nullptr);
+    w.arena_bytes = carve_scratch(w, nullptr);
+    cudaError_t e = cudaMalloc(&w.arena_res, w.res_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        w.arena_res = nullptr;
+        return fail(KNN_ERR_OOM, "world: cudaMalloc(%zu) failed: %s", w.res_bytes,
+                    cudaGetErrorString(e));
+    }
+    carve_resident(w, static_cast<char *>(w.arena_res));
+    prepare_kernels();
+    cudaMemsetAsync(w.stamp, 0, sizeof(unsigned long long) * (size_t)n, s);
+    cudaMemsetAsync(w.err, 0, 16, s);
+    cudaMemsetAsync(w.tickinfo, 0, 16, s);
+    cudaMemcpyAsync(w.px, x_dev, sizeof(float) * (size_t)n, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(w.py, y_dev, sizeof(float) * (size_t)n, cudaMemcpyDeviceToDevice, s);
+    launch_validate_positions(w.px, w.py, n, w.err + 1, s);
+    uint32_t bad = 0;
+    cudaMemcpyAsync(&bad, w.err + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "world creation");
+    if (bad) return fail(KNN_ERR_INVALID, "world: non-finite initial position");
+    cudaMemsetAsync(w.err, 0, 16, s);
+    w.last_stream = s;
+    return KNN_OK;
+}
+
+}  // namespace knnq
+
+namespace {
+
 void release(World &w) {
-    if (w.arena) cudaFree(w.arena);
+    if (w.arena) {
+        if (w.arena_async) cudaFreeAsync(w.arena, w.last_stream);
+        else cudaFree(w.arena);
+    }
+    if (w.arena_res) cudaFree(w.arena_res);
+    w.arena_res = nullptr;
     if (w.stage) cudaFree(w.stage);
     for (int i = 0; i <= knnq::kMaxStages; ++i)
         if (w.ev[i]) cudaEventDestroy(w.ev[i]);
@@ -204,69 +289,32 @@ knn_status knn_world_create(const knn_world_desc *desc, const float *x_dev, cons
                             int64_t n, void *stream, knn_world *out) {
     if (!desc || !out) return fail(KNN_ERR_INVALID, "knn_world_create: NULL desc or out");
     *out = nullptr;
-    if (!(desc->side > 0.f) || !std::isfinite(desc->side) || !std::isfinite(desc->x0) ||
-        !std::isfinite(desc->y0))
-        return fail(KNN_ERR_INVALID, "knn_world_create: domain must be finite with side > 0");
-    if (n < 1 || n > (1ll << 30))
-        return fail(KNN_ERR_INVALID, "knn_world_create: n=%lld outside [1, 2^30]", (long long)n);
-    if (desc->k_max < 1 || desc->k_max > knnq::kMaxK)
-        return fail(KNN_ERR_INVALID, "knn_world_create: k_max=%d outside [1, 64]", desc->k_max);
-    if (desc->max_depth < 0 || desc->max_depth > 16)
-        return fail(KNN_ERR_INVALID, "knn_world_create: max_depth=%d outside [0, 16]",
-                    desc->max_depth);
-    if (desc->leaf_capacity < 0 || desc->leaf_capacity > knnq::kMaxLeafCapacity)
-        return fail(KNN_ERR_INVALID, "knn_world_create: leaf_capacity=%d outside [0, 4096]",
-                    desc->leaf_capacity);
-    if (desc->max_queries < 0 || desc->max_queries > (1ll << 30))
-        return fail(KNN_ERR_INVALID, "knn_world_create: max_queries outside [0, 2^30]");
-    if (!x_dev || !y_dev) return fail(KNN_ERR_INVALID, "knn_world_create: NULL positions");
-
     knn_world_s *h = new (std::nothrow) knn_world_s();
     if (!h) return fail(KNN_ERR_OOM, "knn_world_create: host allocation failed");
     World &w = h->w;
-    cudaGetDevice(&w.device);
-    w.desc = *desc;
-    w.n = n;
-    w.L = desc->max_depth > 0 ? desc->max_depth : 16;
-    w.scale = (float)(1u << w.L) / desc->side;
-    w.tuning.leaf_capacity = desc->leaf_capacity;
     cudaStream_t s = (cudaStream_t)stream;
-
-    w.arena_bytes = carve(w, nullptr);
-    cudaError_t e = cudaMalloc(&w.arena, w.arena_bytes);
+    knn_status st = knnq::world_init_resident(w, desc, x_dev, y_dev, n, s);
+    if (st != KNN_OK) {
+        release(w);
+        delete h;
+        return st;
+    }
+    void *scratch = nullptr;
+    cudaError_t e = cudaMalloc(&scratch, w.arena_bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
+        release(w);
         delete h;
         return fail(KNN_ERR_OOM, "knn_world_create: cudaMalloc(%zu) failed: %s", w.arena_bytes,
                     cudaGetErrorString(e));
     }
-    carve(w, static_cast<char *>(w.arena));
-    knnq::prepare_kernels();
-    cudaMemsetAsync(w.stamp, 0, sizeof(unsigned long long) * (size_t)n, s);
-    cudaMemsetAsync(w.err, 0, 16, s);
-    cudaMemsetAsync(w.tickinfo, 0, 16, s);
-    // look-back status words must not hold anything that could match a live epoch
-    cudaMemsetAsync(w.status, 0, sizeof(uint64_t) * w.status_words, s);
-    cudaMemsetAsync(w.scalars, 0, sizeof(int32_t) * knnq::kNumScalars, s);
-    cudaMemcpyAsync(w.px, x_dev, sizeof(float) * (size_t)n, cudaMemcpyDeviceToDevice, s);
-    cudaMemcpyAsync(w.py, y_dev, sizeof(float) * (size_t)n, cudaMemcpyDeviceToDevice, s);
-    knnq::launch_validate_positions(w.px, w.py, n, w.err + 1, s);
-    uint32_t bad = 0;
-    cudaMemcpyAsync(&bad, w.err + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
-    e = cudaStreamSynchronize(s);
-    if (e == cudaSuccess) e = cudaGetLastError();
+    knnq::world_attach_scratch(w, scratch, s);
+    e = cudaGetLastError();
     if (e != cudaSuccess) {
         release(w);
         delete h;
         return cuda_fail(e, "knn_world_create");
     }
-    if (bad) {
-        release(w);
-        delete h;
-        return fail(KNN_ERR_INVALID, "knn_world_create: non-finite initial position");
-    }
-    cudaMemsetAsync(w.err, 0, 16, s);
-    w.last_stream = s;
     *out = h;
     return KNN_OK;
 }
@@ -287,8 +335,8 @@ knn_status knn_world_set_tuning(knn_world h, const knn_tuning *t) {
     if (!h || !t) return fail(KNN_ERR_INVALID, "knn_world_set_tuning: NULL argument");
     if (t->leaf_capacity < 0 || t->leaf_capacity > knnq::kMaxLeafCapacity)
         return fail(KNN_ERR_INVALID, "leaf_capacity outside [0, 4096]");
-    if (t->grid_level < 0 || t->grid_level > knnq::kMaxGridLevel || t->grid_level > h->w.L)
-        return fail(KNN_ERR_INVALID, "grid_level outside [0, min(10, max_depth)]");
+    if (t->grid_level < 0 || t->grid_level > h->w.gmax)
+        return fail(KNN_ERR_INVALID, "grid_level outside [0, %d] for this world", h->w.gmax);
     if (t->packet_level < 0 || t->packet_level > knnq::kMaxGridLevel)
         return fail(KNN_ERR_INVALID, "packet_level outside [0, 10]");
     h->w.tuning = *t;

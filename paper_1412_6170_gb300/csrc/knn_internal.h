@@ -44,15 +44,21 @@ struct World {
     knn_world_desc desc{};
     int64_t n = 0;
     int L = 16;
+    int gmax = 10;         // deepest cell-map level this world sizes its arrays for
     float scale = 0.f;     // 2^L / side, binary32
     knn_tuning tuning{};   // user overrides (0 = auto)
     uint32_t site = 0;     // look-back launch index within the current tick
     cudaStream_t last_stream = nullptr;
     Plan last_plan{};
 
-    // one device arena
-    void *arena = nullptr;
+    // device memory: the resident part (positions, update stamps, counters)
+    // lives as long as the world; the tick scratch can be released and
+    // allocated again (a serving loop evicts idle worlds' scratch)
+    void *arena_res = nullptr;
+    size_t res_bytes = 0;
+    void *arena = nullptr;       // tick scratch (nullptr while evicted)
     size_t arena_bytes = 0;
+    bool arena_async = false;    // scratch from cudaMallocAsync (freed with cudaFreeAsync)
 
     float *px = nullptr, *py = nullptr;
     unsigned long long *stamp = nullptr;
@@ -140,6 +146,17 @@ int num_sms(int device);
 // stream capture).
 void prepare_kernels();
 void prepare_expand(int device);
+
+// Device memory layout of a world (knn_capi.cu).  base == nullptr only sizes.
+size_t carve_resident(World &w, char *base);
+size_t carve_scratch(World &w, char *base);
+// Creates the resident part of a world (positions copied and validated);
+// the scratch is left unallocated.  Sets the error message on failure.
+knn_status world_init_resident(World &w, const knn_world_desc *desc, const float *x_dev,
+                               const float *y_dev, int64_t n, cudaStream_t s);
+// Points the scratch fields into `base` (scratch_bytes) and clears what must
+// start at zero, on stream s.
+void world_attach_scratch(World &w, void *base, cudaStream_t s);
 
 // Message returned by knn_last_error() on this thread (knn_capi.cu).
 void set_last_error(const char *msg);

@@ -55,6 +55,15 @@ _i64 = ctypes.c_int64
 _i32 = ctypes.c_int32
 
 
+class knn_server_desc(ctypes.Structure):
+    _fields_ = [("n_slots", _i32), ("reserved", _i32), ("hbm_budget_bytes", _i64)]
+
+
+class knn_server_counters(ctypes.Structure):
+    _fields_ = [("worlds", _i32), ("resident_worlds", _i32), ("scratch_bytes", _i64),
+                ("admitted", _i64), ("completed", _i64), ("evictions", _i64), ("pending", _i64)]
+
+
 class knn_tick_args(ctypes.Structure):
     _fields_ = [("upd_id_dev", _vp), ("upd_x_dev", _vp), ("upd_y_dev", _vp), ("n_upd", _i64),
                 ("q_id_dev", _vp), ("q_x_dev", _vp), ("q_y_dev", _vp), ("n_q", _i64),
@@ -83,6 +92,17 @@ _SIGNATURES = {
                        ctypes.c_int),
     "knn_world_autotune": ([_vp, _vp, _vp, _vp, _i64, _i32, _vp, _vp, _i32,
                             ctypes.POINTER(knn_tuning), _vp], ctypes.c_int),
+    "knn_server_create": ([ctypes.POINTER(knn_server_desc), ctypes.POINTER(_vp)], ctypes.c_int),
+    "knn_server_add_world": ([_vp, ctypes.POINTER(knn_world_desc), _vp, _vp, _i64,
+                              ctypes.POINTER(_i32)], ctypes.c_int),
+    "knn_server_submit": ([_vp, _i32, ctypes.POINTER(knn_tick_args), ctypes.POINTER(_i64)],
+                          ctypes.c_int),
+    "knn_server_poll": ([_vp, _i64, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_double)],
+                        ctypes.c_int),
+    "knn_server_wait": ([_vp, _i64, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "knn_server_stats": ([_vp, ctypes.POINTER(knn_server_counters)], ctypes.c_int),
+    "knn_server_world_status": ([_vp, _i32, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
+    "knn_server_destroy": ([_vp], ctypes.c_int),
     "knn_query_static": ([ctypes.POINTER(knn_world_desc), _vp, _vp, _i64, _vp, _vp, _vp, _i64,
                           _i32, _vp, _vp, _vp], ctypes.c_int),
 }
@@ -231,6 +251,54 @@ def tick_args(k: int, q_id=None, upd_id=None, upd_x=None, upd_y=None, q_x=None, 
                          0 if upd_id is None else int(upd_id.shape[0]), _ptr(q_id), _ptr(q_x),
                          _ptr(q_y), 0 if q_id is None else int(q_id.shape[0]), k,
                          _ptr(out_ids), _ptr(out_d2))
+
+
+def knn_server_create(n_slots: int = 4, hbm_budget_bytes: int = 0) -> int:
+    h = _vp()
+    d = knn_server_desc(n_slots, 0, hbm_budget_bytes)
+    _check(lib().knn_server_create(ctypes.byref(d), ctypes.byref(h)))
+    return h.value
+
+
+def knn_server_add_world(s: int, desc: knn_world_desc, x_dev: int, y_dev: int, n: int) -> int:
+    idx = _i32(0)
+    _check(lib().knn_server_add_world(s, ctypes.byref(desc), x_dev, y_dev, n, ctypes.byref(idx)))
+    return idx.value
+
+
+def knn_server_submit(s: int, world_index: int, args: knn_tick_args) -> int:
+    rid = _i64(0)
+    _check(lib().knn_server_submit(s, world_index, ctypes.byref(args), ctypes.byref(rid)))
+    return rid.value
+
+
+def knn_server_poll(s: int, request_id: int) -> tuple:
+    st = _i32(0)
+    lat = ctypes.c_double(0.0)
+    _check(lib().knn_server_poll(s, request_id, ctypes.byref(st), ctypes.byref(lat)))
+    return st.value, lat.value
+
+
+def knn_server_wait(s: int, request_id: int) -> float:
+    lat = ctypes.c_double(0.0)
+    _check(lib().knn_server_wait(s, request_id, ctypes.byref(lat)))
+    return lat.value
+
+
+def knn_server_stats(s: int) -> dict:
+    c = knn_server_counters()
+    _check(lib().knn_server_stats(s, ctypes.byref(c)))
+    return {f: getattr(c, f) for f, _ in knn_server_counters._fields_}
+
+
+def knn_server_world_status(s: int, world_index: int) -> tuple:
+    bits = ctypes.c_uint32(0)
+    st = lib().knn_server_world_status(s, world_index, ctypes.byref(bits))
+    return st, bits.value
+
+
+def knn_server_destroy(s: int) -> None:
+    _check(lib().knn_server_destroy(s))
 
 
 def knn_query_static(desc: knn_world_desc, x_dev, y_dev, n: int, q_id, q_x, q_y, n_q: int,

@@ -77,7 +77,7 @@ def test_clustered_4m_k32_full_size_sampled():
 @pytest.mark.parametrize("tuning", [dict(leaf_capacity=1), dict(leaf_capacity=3, grid_level=2),
                                     dict(leaf_capacity=200, grid_level=4, packet_level=1),
                                     dict(leaf_capacity=4096, grid_level=1, packet_level=0),
-                                    dict(leaf_capacity=16, grid_level=10, packet_level=10)])
+                                    dict(leaf_capacity=16, grid_level=9, packet_level=9)])
 def test_tuning_invariance(tuning):
     w = synth.skewed_moving(n=20000, k=16, ticks=1, seed=11, query_frac=0.5)
     run_and_compare(w, tuning=tuning, what=f"tuning {tuning}")
