@@ -133,6 +133,188 @@ def cpu_baseline(workload, target_s: float = 12.0):
                       f"brute force over all {workload.n} objects, {dt:.1f} s"}
 
 
+def pct(v, q):
+    v = sorted(v)
+    return v[min(len(v) - 1, int(round(q * (len(v) - 1))))]
+
+
+def serving_vs_plain(dev, n_worlds=8, n_obj=N_OBJ, k=K, n_req=128, load=0.8, n_slots=4,
+                     seed=7):
+    """Tick requests over several resident 1M-object worlds: the serving loop
+    (continuous batching over n_slots streams) against the same request stream
+    run one tick at a time (plain).  Arrivals are Poisson at `load` times the
+    plain capacity; each request is a full tick (all objects move and query)."""
+    import numpy as np
+    import torch
+
+    from paper_1412_6170_gb300 import knnq, synth
+    ws = []
+    for i in range(n_worlds):
+        w = synth.plain_uniform_moving(n=n_obj, k=k, ticks=2, seed=seed * 100 + i)
+        ws.append({
+            "x": torch.from_numpy(w.x0).to(dev), "y": torch.from_numpy(w.y0).to(dev),
+            "ids": torch.from_numpy(w.ticks[0].upd_id).to(dev),
+            "ux": [torch.from_numpy(t.upd_x).to(dev) for t in w.ticks],
+            "uy": [torch.from_numpy(t.upd_y).to(dev) for t in w.ticks],
+            "oi": torch.empty((n_obj, k), dtype=torch.int32, device=dev),
+            "od": torch.empty((n_obj, k), dtype=torch.float32, device=dev)})
+
+    def req_args(i):
+        d = ws[i % n_worlds]
+        j = (i // n_worlds) % 2
+        return knnq.tick_args(k, d["ids"], d["ids"], d["ux"][j], d["uy"][j],
+                              out_ids=d["oi"], out_d2=d["od"])
+
+    stream = torch.cuda.current_stream()
+    plain = [knnq.World(d["x"], d["y"], k_max=k, max_queries=n_obj) for d in ws]
+    for i in range(2 * n_worlds):  # warm-up
+        a = req_args(i)
+        knnq.knn_tick(plain[i % n_worlds].handle, a.upd_id_dev, a.upd_x_dev, a.upd_y_dev,
+                      a.n_upd, a.q_id_dev, None, None, a.n_q, k, a.out_ids_dev, a.out_d2_dev,
+                      stream.cuda_stream)
+    torch.cuda.synchronize()
+    # plain service time (one tick, synchronised)
+    svc = []
+    for i in range(2 * n_worlds):
+        t0 = time.perf_counter()
+        a = req_args(i)
+        knnq.knn_tick(plain[i % n_worlds].handle, a.upd_id_dev, a.upd_x_dev, a.upd_y_dev,
+                      a.n_upd, a.q_id_dev, None, None, a.n_q, k, a.out_ids_dev, a.out_d2_dev,
+                      stream.cuda_stream)
+        torch.cuda.synchronize()
+        svc.append(time.perf_counter() - t0)
+    service = statistics.median(svc)
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(service / load, n_req)
+    arrive = np.cumsum(gaps) - gaps[0]
+
+    def spin_until(t_abs):
+        while time.perf_counter() < t_abs:
+            pass
+
+    # plain: FIFO, one tick at a time
+    lat_p = []
+    t_base = time.perf_counter() + 0.01
+    for i in range(n_req):
+        spin_until(t_base + arrive[i])
+        a = req_args(i)
+        knnq.knn_tick(plain[i % n_worlds].handle, a.upd_id_dev, a.upd_x_dev, a.upd_y_dev,
+                      a.n_upd, a.q_id_dev, None, None, a.n_q, k, a.out_ids_dev, a.out_d2_dev,
+                      stream.cuda_stream)
+        torch.cuda.synchronize()
+        lat_p.append(time.perf_counter() - (t_base + arrive[i]))
+    span_p = (time.perf_counter() - t_base)
+    for w in plain:
+        w.close()
+
+    # served: the serving loop, same arrivals
+    srv = knnq.knn_server_create(n_slots, 0)
+    idx = [knnq.knn_server_add_world(srv, knnq.knn_world_desc(0.0, 0.0, 1.0, 0, 0, k, n_obj),
+                                     d["x"].data_ptr(), d["y"].data_ptr(), n_obj) for d in ws]
+    warm = [knnq.knn_server_submit(srv, idx[i % n_worlds], req_args(i)) for i in range(n_worlds)]
+    for r in warm:
+        knnq.knn_server_wait(srv, r)
+    rids = []
+    t_base = time.perf_counter() + 0.01
+    for i in range(n_req):
+        spin_until(t_base + arrive[i])
+        rids.append(knnq.knn_server_submit(srv, idx[i % n_worlds], req_args(i)))
+    lat_s = [knnq.knn_server_wait(srv, r) / 1e3 for r in rids]
+    span_s = (time.perf_counter() - t_base)
+    # saturation: every request submitted at once
+    t0 = time.perf_counter()
+    rids = [knnq.knn_server_submit(srv, idx[i % n_worlds], req_args(i)) for i in range(n_req)]
+    for r in rids:
+        knnq.knn_server_wait(srv, r)
+    sat_s = time.perf_counter() - t0
+    knnq.knn_server_destroy(srv)
+    plain = [knnq.World(d["x"], d["y"], k_max=k, max_queries=n_obj) for d in ws]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(n_req):
+        a = req_args(i)
+        knnq.knn_tick(plain[i % n_worlds].handle, a.upd_id_dev, a.upd_x_dev, a.upd_y_dev,
+                      a.n_upd, a.q_id_dev, None, None, a.n_q, k, a.out_ids_dev, a.out_d2_dev,
+                      stream.cuda_stream)
+    torch.cuda.synchronize()
+    sat_p = time.perf_counter() - t0
+    for w in plain:
+        w.close()
+    q = n_req * n_obj
+    return {
+        "workload": f"{n_worlds} resident worlds x {n_obj} uniform objects, k={k}, "
+                    f"{n_req} tick requests (all objects move and query), Poisson arrivals "
+                    f"at {load} x plain capacity; served: {n_slots} stream slots",
+        "plain_service_ms": 1e3 * service,
+        "served": {"p50_ms": 1e3 * pct(lat_s, 0.5), "p99_ms": 1e3 * pct(lat_s, 0.99),
+                   "queries_per_s_at_load": q / span_s, "queries_per_s_saturated": q / sat_s},
+        "plain": {"p50_ms": 1e3 * pct(lat_p, 0.5), "p99_ms": 1e3 * pct(lat_p, 0.99),
+                  "queries_per_s_at_load": q / span_p, "queries_per_s_saturated": q / sat_p},
+    }
+
+
+def batched_vs_plain(dev, n_worlds=256, seed=0, iters=5):
+    """Many uneven worlds (1k-200k objects, uniform or clustered, k in {4,8,16,32}, all
+    query): one knn_batch_tick (a recorded CUDA graph) against one knn_tick per world."""
+    import torch
+
+    from paper_1412_6170_gb300 import knnq, synth
+    wl = synth.many_worlds(n_worlds=n_worlds, seed=seed, ticks=2)
+    stream = torch.cuda.current_stream()
+    data, worlds_b, worlds_p = [], [], []
+    for w in wl:
+        t = w.ticks[0]
+        d = {"ids": torch.from_numpy(t.upd_id).to(dev), "ux": torch.from_numpy(t.upd_x).to(dev),
+             "uy": torch.from_numpy(t.upd_y).to(dev), "q": torch.from_numpy(t.q_id).to(dev),
+             "oi": torch.empty((t.q_id.shape[0], w.k), dtype=torch.int32, device=dev),
+             "od": torch.empty((t.q_id.shape[0], w.k), dtype=torch.float32, device=dev)}
+        data.append(d)
+        x, y = torch.from_numpy(w.x0).to(dev), torch.from_numpy(w.y0).to(dev)
+        worlds_b.append(knnq.World(x, y, k_max=w.k, max_queries=w.n))
+        worlds_p.append(knnq.World(x, y, k_max=w.k, max_queries=w.n))
+    args = [knnq.tick_args(w.k, d["q"], d["ids"], d["ux"], d["uy"], out_ids=d["oi"],
+                           out_d2=d["od"]) for w, d in zip(wl, data)]
+    handles = [w.handle for w in worlds_b]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    knnq.knn_batch_tick(handles, args, stream.cuda_stream)  # records the graph
+    torch.cuda.synchronize()
+    record_s = time.perf_counter() - t0
+    for _ in range(2):
+        knnq.knn_batch_tick(handles, args, stream.cuda_stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(iters):
+        knnq.knn_batch_tick(handles, args, stream.cuda_stream)
+    e1.record(stream)
+    e1.synchronize()
+    batch_ms = e0.elapsed_time(e1) / iters
+
+    def plain_pass():
+        for w, a in zip(worlds_p, args):
+            knnq.knn_tick(w.handle, a.upd_id_dev, a.upd_x_dev, a.upd_y_dev, a.n_upd, a.q_id_dev,
+                          None, None, a.n_q, a.k, a.out_ids_dev, a.out_d2_dev, stream.cuda_stream)
+    plain_pass()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    t0 = time.perf_counter()
+    for _ in range(iters):
+        plain_pass()
+    e1.record(stream)
+    e1.synchronize()
+    plain_ms = e0.elapsed_time(e1) / iters
+    plain_host_ms = 1e3 * (time.perf_counter() - t0) / iters
+    q = sum(int(a.n_q) for a in args)
+    for w in worlds_b + worlds_p:
+        w.close()
+    return {"workload": f"{n_worlds} worlds, {sum(w.n for w in wl)} objects, {q} queries per "
+                        "batch tick; objects log-uniform in [1k, 200k], uniform or clustered, "
+                        "k in {4,8,16,32}",
+            "batched_ms": batch_ms, "plain_ms": plain_ms, "plain_host_ms": plain_host_ms,
+            "batched_queries_per_s": q / (batch_ms / 1e3),
+            "plain_queries_per_s": q / (plain_ms / 1e3), "graph_record_s": record_s}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -332,6 +514,9 @@ def run_gpu(args):
         "exact_spot_check": spot,
         "wall_s": wall,
     }
+    if not args.no_patterns:
+        line["serving"] = serving_vs_plain(dev)
+        line["batching"] = batched_vs_plain(dev)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
     print(json.dumps(line), flush=True)
@@ -347,6 +532,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--no-patterns", action="store_true",
+                    help="skip the serving and batching comparisons")
     args = ap.parse_args()
     if args.warmup < 1:
         args.warmup = 1

@@ -162,6 +162,7 @@ typedef struct {
 typedef struct {
     int32_t worlds, resident_worlds;  /* registered / holding scratch now */
     int64_t scratch_bytes;            /* scratch the server holds now */
+    int64_t largest_world_scratch;    /* scratch the largest registered world needs */
     int64_t admitted, completed, evictions, pending;
 } knn_server_counters;
 

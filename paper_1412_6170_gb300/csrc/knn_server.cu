@@ -288,6 +288,10 @@ knn_status knn_server_stats(knn_server s, knn_server_counters *out) {
     for (ServerWorld *w : s->worlds) resident += w->h.w.arena != nullptr;
     out->resident_worlds = resident;
     out->scratch_bytes = s->used;
+    int64_t largest = 0;
+    for (ServerWorld *w : s->worlds)
+        largest = (int64_t)w->h.w.arena_bytes > largest ? (int64_t)w->h.w.arena_bytes : largest;
+    out->largest_world_scratch = largest;
     out->admitted = s->admitted;
     out->completed = s->completed;
     out->evictions = s->evictions;

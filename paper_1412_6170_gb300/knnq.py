@@ -61,7 +61,8 @@ class knn_server_desc(ctypes.Structure):
 
 class knn_server_counters(ctypes.Structure):
     _fields_ = [("worlds", _i32), ("resident_worlds", _i32), ("scratch_bytes", _i64),
-                ("admitted", _i64), ("completed", _i64), ("evictions", _i64), ("pending", _i64)]
+                ("largest_world_scratch", _i64), ("admitted", _i64), ("completed", _i64),
+                ("evictions", _i64), ("pending", _i64)]
 
 
 class knn_tick_args(ctypes.Structure):

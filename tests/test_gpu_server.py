@@ -65,12 +65,10 @@ def test_alone_and_mixed_give_identical_rows():
     ws = synth.many_worlds(n_worlds=7, seed=11, n_lo=2000, n_hi=60000, ks=(4, 16, 32),
                            ticks=3, query_frac=(0.2, 1.0))
     order = make_requests(ws, 3)
-    alone, lat_a, _ = run_server(ws, order, n_slots=1, budget=0, torch=torch, dev=dev)
-    # budget for about two worlds' scratch: admission must evict and re-admit
-    probe = knnq.World(to_dev(ws[0].x0), to_dev(ws[0].y0), k_max=32, max_queries=ws[0].n)
-    probe.close()
-    biggest = max(w.n for w in ws)
-    budget = int(2.2 * 110 * biggest) + 8 * (1 << 20) * 3
+    alone, lat_a, st_a = run_server(ws, order, n_slots=1, budget=0, torch=torch, dev=dev)
+    # a budget of 1.5 times the largest world's scratch: admission must evict and re-admit
+    assert st_a["scratch_bytes"] > 2 * st_a["largest_world_scratch"]
+    budget = int(1.5 * st_a["largest_world_scratch"])
     mixed, lat_m, st = run_server(ws, order, n_slots=4, budget=budget, torch=torch, dev=dev)
     assert st["completed"] == len(order) and st["evictions"] > 0
     assert all(v > 0 for v in lat_a + lat_m)
