@@ -48,6 +48,43 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def expand_profile():
+    """Per-launch DRAM traffic and ALU-pipe use of k_expand from the committed ncu
+    summary, or None when the kernel source changed since that capture."""
+    import hashlib
+    import re
+    prof = os.path.join(ROOT, "profiles", "k_expand_uniform1M_k16.md")
+    src = os.path.join(ROOT, "paper_1412_6170_gb300", "csrc", "knn_expand.cu")
+    try:
+        text = open(prof).read()
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if re.search(r"source sha256[^:]*: *([0-9a-f]{16})", text).group(1) != h:
+            return None
+        traffic = int(re.search(r"traffic_bytes_per_launch: *(\d+)", text).group(1))
+        alu = float(re.search(r"sm__inst_executed_pipe_alu[^|]*\| *([0-9.]+)", text).group(1))
+        return {"traffic": traffic, "alu_pipe_pct": alu}
+    except Exception:  # noqa: BLE001
+        return None
+
+
+def max_over_ranks(values, dist=None, device=None):
+    """Element-wise maximum of per-rank timings (a barrier-synchronised MAX
+    all-reduce; the data path itself has no collective)."""
+    if dist is None:
+        return list(values)
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64,
+                     device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu().tolist()]
+
+
+def replicas_value(n_ranks, units_per_rank, max_seconds):
+    """Whole-job throughput of independent replicas: every rank's units over the
+    slowest rank's time (weak scaling)."""
+    return n_ranks * units_per_rank / max_seconds
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -443,11 +480,7 @@ def run_gpu(args):
         dist.barrier()
     launches = world.launches() - launches0
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks([sum(step_ms)], dist, dev)[0]
     st, bits = world.status()
     if st != knnq.KNN_OK:
         raise RuntimeError(f"device status {st} bits {bits} after timed steps")
@@ -473,24 +506,21 @@ def run_gpu(args):
                            vp(h_uid), None, None, N_OBJ, K, vp(h_oid), vp(h_od),
                            stream.cuda_stream)
         e2e_t.append(time.perf_counter() - t0)
-    e2e_total = sum(e2e_t)
-    if dist is not None:
-        t = torch.tensor([e2e_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = max_over_ranks([sum(e2e_t)], dist, dev)[0]
 
     world.close()
     if rank != 0:
         return
     n_gpus = world_size
-    value = n_gpus * N_OBJ * args.steps / (total_ms / 1e3)
+    value = replicas_value(n_gpus, N_OBJ * args.steps, total_ms / 1e3)
     srt = sorted(step_ms)
     p99 = srt[min(len(srt) - 1, int(round(0.99 * (len(srt) - 1))))]
     p50 = statistics.median(step_ms)
     exp_ms = stage_sums["expand"] / args.steps
     hbm, hbm_kind = peaks()
     achieved = ALGO_BYTES_PER_QUERY * N_OBJ / (exp_ms / 1e3) / 1e9
-    traffic = None
+    prof = expand_profile()
+    traffic = None if prof is None else prof["traffic"]
     line = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": n_gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -504,8 +534,12 @@ def run_gpu(args):
         "roofline": {"kernel": "k_expand", "bound": "hbm", "achieved": achieved, "peak": hbm,
                      "peak_kind": hbm_kind, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": traffic,
-                     "algorithmic_bytes_per_query": ALGO_BYTES_PER_QUERY},
-        "e2e": {"value": n_gpus * N_OBJ * e2e_steps / e2e_total, "unit": "queries/s",
+                     "algorithmic_bytes_per_query": ALGO_BYTES_PER_QUERY,
+                     "limiter": None if prof is None else
+                     f"ALU pipe {prof['alu_pipe_pct']:.0f}% of peak (ncu); DRAM traffic "
+                     "below the algorithmic bytes"},
+        "e2e": {"value": replicas_value(n_gpus, N_OBJ * e2e_steps, e2e_total),
+                "unit": "queries/s",
                 "h2d_bytes_per_step": N_OBJ * 12 + N_OBJ * 4,
                 "d2h_bytes_per_step": N_OBJ * K * 8,
                 "api": "knn_tick_host (pinned host buffers, synchronous)"},
