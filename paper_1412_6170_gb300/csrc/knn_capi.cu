@@ -114,6 +114,7 @@ size_t carve_scratch(World &w, char *base) {
     w.baabb = c.take<float4>(n);
     w.cb = c.take<int32_t>(ncell);
     w.qcnt = c.take<int32_t>(n + 1);
+    w.qoff = c.take<int32_t>(n + 2);
     w.qs_x = c.take<float>(Q);
     w.qs_y = c.take<float>(Q);
     w.qs_id = c.take<int32_t>(Q);

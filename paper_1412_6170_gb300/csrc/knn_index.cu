@@ -296,10 +296,16 @@ __global__ void __launch_bounds__(256) k_leaves(
     int th, int G, const float *__restrict__ px, const float *__restrict__ py,
     float *__restrict__ xs, float *__restrict__ ys, int32_t *__restrict__ sid,
     int32_t *__restrict__ inv, int32_t *__restrict__ bstart, uint32_t *__restrict__ bcode,
-    uint8_t *__restrict__ blevel, int32_t *scalars, uint64_t *status, uint32_t *ticket,
-    const uint32_t *__restrict__ tickinfo, uint32_t site, uint32_t *err) {
+    uint8_t *__restrict__ blevel, int32_t *__restrict__ cb, int64_t ncell, int32_t *scalars,
+    uint64_t *status, uint32_t *ticket, const uint32_t *__restrict__ tickinfo, uint32_t site,
+    uint32_t *err) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t s_tile, s_tmp[8], s_excl;
+    // long runs of cells without a leaf, filled by the whole block
+    constexpr int kMaxGaps = 64;
+    __shared__ int64_t s_gap_lo[kMaxGaps], s_gap_hi[kMaxGaps];
+    __shared__ int32_t s_gap_b[kMaxGaps];
+    __shared__ int s_ngap;
     const int tid = threadIdx.x;
     if (tid == 0) s_tile = atomicAdd(ticket, 1u);
     __syncthreads();
@@ -375,6 +381,7 @@ __global__ void __launch_bounds__(256) k_leaves(
     }
     uint32_t tile_total;
     __shared__ uint32_t s_total;
+    if (tid == 0) s_ngap = 0;
     const uint32_t off = block_excl_scan_256(cnt, s_tmp, &s_total);
     tile_total = s_total;
     if (tid < 32) {
@@ -392,14 +399,41 @@ __global__ void __launch_bounds__(256) k_leaves(
             bstart[b] = (int32_t)(t0 + e);
             bcode[b] = (uint32_t)((uint64_t)s_code[e + 1] << (2 * (L - lam)));
             blevel[b] = (uint8_t)lam;
+            // cell map (the paper's z_map at level G): the cells from just after
+            // the previous leaf's cell up to this leaf's cell start at leaf b
+            int64_t c_here = (int64_t)(s_code[e + 1] >> (2 * (lam - G)));
+            if (c_here > ncell) c_here = ncell;
+            const int64_t c_prev =
+                t0 + e == 0 ? -1 : (int64_t)(s_code[e] >> (2 * (s_lam[e] - G)));
+            int slot = -1;
+            if (c_here - c_prev > 64) {
+                slot = atomicAdd(&s_ngap, 1);
+                if (slot < kMaxGaps) {
+                    s_gap_lo[slot] = c_prev + 1;
+                    s_gap_hi[slot] = c_here;
+                    s_gap_b[slot] = (int32_t)b;
+                }
+            }
+            if (slot < 0 || slot >= kMaxGaps)
+                for (int64_t c = c_prev + 1; c <= c_here; ++c) cb[c] = (int32_t)b;
             ++b;
         }
     }
-    if (t0 + kLeafTile >= n && tid == 0) {
+    if (t0 + kLeafTile >= n) {
         const uint32_t m = excl + tile_total <= (uint64_t)n ? excl + tile_total : (uint32_t)n;
-        scalars[kScalarLeaves] = (int32_t)m;
-        bstart[m] = (int32_t)n;
+        if (tid == 0) {
+            scalars[kScalarLeaves] = (int32_t)m;
+            bstart[m] = (int32_t)n;
+        }
+        // cells after the last leaf's cell map to m (no leaf)
+        const int e = (int)(n - 1 - t0);
+        const int64_t c_last = (int64_t)(s_code[e + 1] >> (2 * (s_lam[e + 1] - G)));
+        for (int64_t c = c_last + 1 + tid; c <= ncell; c += 256) cb[c] = (int32_t)m;
     }
+    __syncthreads();
+    const int ngap = s_ngap < kMaxGaps ? s_ngap : kMaxGaps;
+    for (int gi = 0; gi < ngap; ++gi)
+        for (int64_t c = s_gap_lo[gi] + tid; c <= s_gap_hi[gi]; c += 256) cb[c] = s_gap_b[gi];
     // leaf-ordered SoA (a5)
     for (int e = tid; e < kLeafTile; e += 256) {
         const int64_t i = t0 + e;
@@ -448,44 +482,28 @@ __global__ void k_leaf_aabb(const int32_t *__restrict__ bstart, const int32_t *_
     }
 }
 
-// Uniform cell map at level G (the paper's z_map): cb[c] = first leaf whose
-// level-G cell is >= c, so the leaves of cell c are [cb[c], cb[c+1]).
-__global__ void k_cellmap(const uint32_t *__restrict__ bcode, const int32_t *__restrict__ scalars,
-                          int L, int G, int32_t *__restrict__ cb, int64_t ncell) {
-    const int32_t m = scalars[kScalarLeaves];  // <= n by construction
-    const int sh = 2 * (L - G);
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c <= ncell;
-         c += (int64_t)gridDim.x * blockDim.x) {
-        int32_t lo = 0, hi = m;
-        while (lo < hi) {
-            const int32_t mid = (lo + hi) >> 1;
-            if ((int64_t)(bcode[mid] >> sh) < c) lo = mid + 1;
-            else hi = mid;
-        }
-        cb[c] = lo;
-    }
-}
-
 void launch_leaves(World &w, const Plan &p, cudaStream_t s) {
     const int r = p.passes & 1;
     const int tiles = (int)((w.n + kLeafTile - 1) / kLeafTile);
     const size_t sm = leaves_smem(p.th);
     prepare_kernels();
+    const int64_t ncell = 1ll << (2 * p.G);
     k_leaves<<<tiles, 256, sm, s>>>(w.key[r], w.val[r], w.n, p.L, p.th, p.G, w.px, w.py, w.xs,
-                                    w.ys, w.sid, w.inv, w.bstart, w.bcode, w.blevel, w.scalars,
-                                    w.status, w.counters + kCtrLeaves, w.tickinfo, w.site++,
-                                    w.err);
+                                    w.ys, w.sid, w.inv, w.bstart, w.bcode, w.blevel, w.cb,
+                                    ncell, w.scalars, w.status, w.counters + kCtrLeaves,
+                                    w.tickinfo, w.site++, w.err);
     const int g = grid_for(w.n, 256, num_sms(w.device) * 8);
     k_leaf_aabb<<<g, 256, 0, s>>>(w.bstart, w.scalars, w.xs, w.ys, w.baabb, w.n);
-    const int64_t ncell = 1ll << (2 * p.G);
-    k_cellmap<<<grid_for(ncell + 1, 256, num_sms(w.device) * 16), 256, 0, s>>>(
-        w.bcode, w.scalars, p.L, p.G, w.cb, ncell);
-    w.launches += 3;
+    w.launches += 2;
 }
 
 // ---------------------------------------------------------------------------
 // Exclusive scan of int32 (single pass, look-back).  In place is allowed.
 
+// PACKETS: the value of entry c is the number of 32-query packets of cell c,
+// ceil((in[c+1] - in[c]) / 32) with in = the cells' first sorted query
+// (0 for the last entry); otherwise it is in[c].
+template <bool PACKETS>
 __global__ void __launch_bounds__(256) k_scan_excl(const int32_t *in, int32_t *out, int64_t len,
                                                    int32_t *total, uint64_t *status,
                                                    uint32_t *ticket,
@@ -501,7 +519,11 @@ __global__ void __launch_bounds__(256) k_scan_excl(const int32_t *in, int32_t *o
     uint32_t sum = 0;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-        v[q] = base + q < len ? in[base + q] : 0;
+        const int64_t c = base + q;
+        if (PACKETS)
+            v[q] = c + 1 < len ? (in[c + 1] - in[c] + 31) / 32 : 0;
+        else
+            v[q] = c < len ? in[c] : 0;
         sum += (uint32_t)v[q];
     }
     const uint32_t off = block_excl_scan_256(sum, s_tmp, &s_total);
@@ -520,10 +542,16 @@ __global__ void __launch_bounds__(256) k_scan_excl(const int32_t *in, int32_t *o
 }
 
 static void scan_excl(World &w, const int32_t *in, int32_t *out, int64_t len, int32_t *total,
-                      int counter, cudaStream_t s) {
+                      int counter, cudaStream_t s, bool packets = false) {
     const int tiles = (int)((len + kScanTile - 1) / kScanTile);
-    k_scan_excl<<<tiles, 256, 0, s>>>(in, out, len, total, w.status, w.counters + counter,
-                                      w.tickinfo, w.site++, w.err);
+    if (packets)
+        k_scan_excl<true><<<tiles, 256, 0, s>>>(in, out, len, total, w.status,
+                                                w.counters + counter, w.tickinfo, w.site++,
+                                                w.err);
+    else
+        k_scan_excl<false><<<tiles, 256, 0, s>>>(in, out, len, total, w.status,
+                                                 w.counters + counter, w.tickinfo, w.site++,
+                                                 w.err);
     ++w.launches;
 }
 
@@ -550,23 +578,44 @@ __global__ void k_query_count(const int32_t *__restrict__ q_id, int64_t n_q, int
     }
 }
 
-__global__ void k_query_scatter(const int32_t *__restrict__ q_id, int64_t n_q, int64_t n,
-                                const int32_t *__restrict__ inv, int32_t *qoff,
-                                const float *__restrict__ xs, const float *__restrict__ ys,
-                                const uint32_t *__restrict__ skey, float *qs_x, float *qs_y,
-                                int32_t *qs_id, int32_t *qs_orig, uint32_t *qs_key) {
+// Counting sort, second half: every valid query takes one slot of its
+// issuer's range [qoff[p], qoff[p+1]) (the count drops back to zero) and
+// records its caller index there.
+__global__ void k_query_place(const int32_t *__restrict__ q_id, int64_t n_q, int64_t n,
+                              const int32_t *__restrict__ inv, const int32_t *__restrict__ qoff,
+                              int32_t *qcnt, int32_t *qs_orig) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_q;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t s = q_id[i];
         if (s < 0 || s >= n) continue;
         const int32_t p = inv[s];
-        const int32_t j = atomicAdd(&qoff[p], 1);
+        const int32_t j = qoff[p] + atomicSub(&qcnt[p], 1) - 1;
         if (j < 0 || j >= n_q) continue;  // only after a timed-out look-back
-        qs_x[j] = xs[p];
-        qs_y[j] = ys[p];
-        qs_id[j] = s;
         qs_orig[j] = (int32_t)i;
-        qs_key[j] = skey[p];
+    }
+}
+
+// Walk the sorted objects in order and copy each one's position, id and key
+// into the slots of its queries: sequential reads, sequential writes.
+__global__ void k_query_fill(int64_t n, int64_t n_q, const int32_t *__restrict__ qoff,
+                             const float *__restrict__ xs, const float *__restrict__ ys,
+                             const int32_t *__restrict__ sid, const uint32_t *__restrict__ skey,
+                             float *qs_x, float *qs_y, int32_t *qs_id, uint32_t *qs_key) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        int32_t a = qoff[p], b = qoff[p + 1];
+        if (a >= b) continue;
+        if (a < 0) a = 0;
+        if (b > n_q) b = (int32_t)n_q;
+        const float x = xs[p], y = ys[p];
+        const int32_t id = sid[p];
+        const uint32_t key = skey[p];
+        for (int32_t j = a; j < b; ++j) {
+            qs_x[j] = x;
+            qs_y[j] = y;
+            qs_id[j] = id;
+            qs_key[j] = key;
+        }
     }
 }
 
@@ -575,11 +624,12 @@ void launch_queries_at_issuers(World &w, const Plan &p, const int32_t *q_id, int
     cudaMemsetAsync(w.qcnt, 0, sizeof(int32_t) * (size_t)(w.n + 1), s);
     const int g = grid_for(n_q, 256, num_sms(w.device) * 8);
     k_query_count<<<g, 256, 0, s>>>(q_id, n_q, w.n, w.inv, w.qcnt, k, out_ids, out_d2, w.err);
-    scan_excl(w, w.qcnt, w.qcnt, w.n, w.scalars + kScalarValidQueries, kCtrQueryScan, s);
+    scan_excl(w, w.qcnt, w.qoff, w.n + 1, w.scalars + kScalarValidQueries, kCtrQueryScan, s);
+    k_query_place<<<g, 256, 0, s>>>(q_id, n_q, w.n, w.inv, w.qoff, w.qcnt, w.qs_orig);
     const uint32_t *skey = w.key[p.passes & 1];
-    k_query_scatter<<<g, 256, 0, s>>>(q_id, n_q, w.n, w.inv, w.qcnt, w.xs, w.ys, skey, w.qs_x,
-                                      w.qs_y, w.qs_id, w.qs_orig, w.qs_key);
-    w.launches += 2;
+    k_query_fill<<<grid_for(w.n, 256, num_sms(w.device) * 8), 256, 0, s>>>(
+        w.n, n_q, w.qoff, w.xs, w.ys, w.sid, skey, w.qs_x, w.qs_y, w.qs_id, w.qs_key);
+    w.launches += 3;
 }
 
 __global__ void k_query_gather(const uint32_t *__restrict__ skey, const int32_t *__restrict__ sval,
@@ -625,29 +675,21 @@ void launch_queries_explicit(World &w, const Plan &p, const int32_t *q_id, const
 // Packets: at most 32 consecutive sorted queries inside one level-Gp cell,
 // one packet per warp of the expansion (the paper's per-cell tasks).
 
-__global__ void k_query_cells(const uint32_t *__restrict__ qs_key, const int32_t *__restrict__ scalars,
-                              int L, int Gp, int64_t ncell, int64_t nq_cap, int32_t *qcs,
-                              int32_t *npk) {
+// First sorted query of every level-Gp cell (qcs[c], c in [0, ncell]): each
+// boundary between consecutive sorted queries fills the cells it crosses.
+__global__ void k_query_cells(const uint32_t *__restrict__ qs_key,
+                              const int32_t *__restrict__ scalars, int L, int Gp, int64_t ncell,
+                              int64_t nq_cap, int32_t *qcs) {
     int32_t nv = scalars[kScalarValidQueries];
     if (nv < 0) nv = 0;
     if (nv > nq_cap) nv = (int32_t)nq_cap;
     const int sh = 2 * (L - Gp);
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c <= ncell;
-         c += (int64_t)gridDim.x * blockDim.x) {
-        int32_t lo = 0, hi = nv;
-        while (lo < hi) {
-            const int32_t mid = (lo + hi) >> 1;
-            if ((int64_t)((uint64_t)qs_key[mid] >> sh) < c) lo = mid + 1;
-            else hi = mid;
-        }
-        int32_t lo2 = lo, hi2 = nv;
-        while (lo2 < hi2) {
-            const int32_t mid = (lo2 + hi2) >> 1;
-            if ((int64_t)((uint64_t)qs_key[mid] >> sh) < c + 1) lo2 = mid + 1;
-            else hi2 = mid;
-        }
-        qcs[c] = lo;
-        npk[c] = c < ncell ? (lo2 - lo + 31) / 32 : 0;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j <= nv;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        int64_t c_here = j < nv ? (int64_t)((uint64_t)qs_key[j] >> sh) : ncell;
+        if (c_here > ncell) c_here = ncell;
+        const int64_t c_prev = j > 0 ? (int64_t)((uint64_t)qs_key[j - 1] >> sh) : -1;
+        for (int64_t c = c_prev + 1; c <= c_here; ++c) qcs[c] = (int32_t)j;
     }
 }
 
@@ -667,8 +709,10 @@ __global__ void k_packets(const int32_t *__restrict__ qcs, const int32_t *__rest
 void launch_packets(World &w, const Plan &p, int64_t n_q, cudaStream_t s) {
     const int64_t ncell = 1ll << (2 * p.Gp);
     const int g = grid_for(ncell + 1, 256, num_sms(w.device) * 16);
-    k_query_cells<<<g, 256, 0, s>>>(w.qs_key, w.scalars, p.L, p.Gp, ncell, n_q, w.qcs, w.npk);
-    scan_excl(w, w.npk, w.pk_off, ncell + 1, w.scalars + kScalarPackets, kCtrPacketScan, s);
+    k_query_cells<<<grid_for(n_q + 1, 256, num_sms(w.device) * 8), 256, 0, s>>>(
+        w.qs_key, w.scalars, p.L, p.Gp, ncell, n_q, w.qcs);
+    scan_excl(w, w.qcs, w.pk_off, ncell + 1, w.scalars + kScalarPackets, kCtrPacketScan, s,
+              true);
     k_packets<<<g, 256, 0, s>>>(w.qcs, w.pk_off, ncell, packet_capacity(w), w.pk_start,
                                 w.pk_len);
     w.launches += 2;

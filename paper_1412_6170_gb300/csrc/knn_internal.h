@@ -72,7 +72,7 @@ struct World {
     uint8_t *blevel = nullptr;
     float4 *baabb = nullptr;
     int32_t *cb = nullptr;
-    int32_t *qcnt = nullptr;
+    int32_t *qcnt = nullptr, *qoff = nullptr;
     float *qs_x = nullptr, *qs_y = nullptr;
     int32_t *qs_id = nullptr, *qs_orig = nullptr;
     uint32_t *qs_key = nullptr;

@@ -82,6 +82,7 @@ size_t cut_scratch(knnq::World &w, unsigned char *base, int64_t n_q) {
     w.baabb = c.take<float4>(n);
     w.cb = c.take<int32_t>(ncell);
     w.qcnt = c.take<int32_t>(n + 1);
+    w.qoff = c.take<int32_t>(n + 2);
     w.qs_x = c.take<float>(n_q);
     w.qs_y = c.take<float>(n_q);
     w.qs_id = c.take<int32_t>(n_q);
