@@ -112,6 +112,8 @@ size_t carve_scratch(World &w, char *base) {
     w.bcode = c.take<uint32_t>(n);
     w.blevel = c.take<uint8_t>(n);
     w.baabb = c.take<float4>(n);
+    w.brange = c.take<int2>(n);
+    w.obj_leaf = c.take<int32_t>(n);
     w.cb = c.take<int32_t>(ncell);
     w.qcnt = c.take<int32_t>(n + 1);
     w.qoff = c.take<int32_t>(n + 2);
@@ -120,6 +122,7 @@ size_t carve_scratch(World &w, char *base) {
     w.qs_id = c.take<int32_t>(Q);
     w.qs_orig = c.take<int32_t>(Q);
     w.qs_key = c.take<uint32_t>(Q);
+    w.qs_leaf = c.take<int32_t>(Q);
     w.qcs = c.take<int32_t>(ncell);
     w.npk = c.take<int32_t>(ncell);
     w.pk_off = c.take<int32_t>(ncell);

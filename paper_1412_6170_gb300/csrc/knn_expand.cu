@@ -27,13 +27,12 @@ struct ExpandArgs {
     const float *xs, *ys;
     const int32_t *sid;
     const int32_t *bstart;
-    const uint32_t *bcode;
     const uint8_t *blevel;
     const float4 *baabb;
+    const int2 *brange;
     const int32_t *cb;
     const float *qs_x, *qs_y;
-    const int32_t *qs_id, *qs_orig;
-    const uint32_t *qs_key;
+    const int32_t *qs_id, *qs_orig, *qs_leaf;
     const int32_t *pk_start, *pk_len;
     const int32_t *scalars;
     uint32_t *pk_counter;
@@ -42,6 +41,7 @@ struct ExpandArgs {
     float x0, y0, scale_g, side;
     float spec2;  // alpha^2 of the speculative first threshold (0: none)
     int L, G, k;
+    int vec_out;  // rows may be written with 16-byte stores
     int64_t n, n_q, pk_cap;
 };
 
@@ -62,6 +62,9 @@ constexpr int kWarps = 4;  // warps per block
 struct WarpSmem {
     float4 obj[32];                              // staged objects (x, y, id bits, -)
     unsigned long long buf[kBufCap][32];         // [slot][lane]
+    float4 lbb[32];                              // gathered leaf box, per lane
+    int2 lrg[32];                                // its objects [x, y)
+    int2 lc[32];                                 // leaves [x, y) of the lane's cell
 };
 
 __device__ __forceinline__ void cmpx(unsigned long long &x, unsigned long long &y) {
@@ -123,24 +126,6 @@ __device__ __forceinline__ void flush(Lane<KC> &L, WarpSmem &sm, int lane) {
     L.thr = fminf(L.thr, __uint_as_float((uint32_t)(L.lst[KC - 1] >> 32)));
 }
 
-// Leaf of the cell map closest (in Morton order) to a query key: the last leaf
-// of the key's level-G cell whose first code is <= key, or the cell's first
-// leaf.  Returns the insertion point when the cell has no leaf.
-__device__ __forceinline__ int32_t leaf_near(const ExpandArgs &g, uint32_t key) {
-    uint32_t c = key >> (2 * (g.L - g.G));
-    const uint32_t last = (1u << (2 * g.G)) - 1u;
-    c = c < last ? c : last;
-    int32_t lo = g.cb[c], hi = g.cb[c + 1];
-    if (lo == hi) return lo;
-    const int32_t first = lo;
-    while (lo < hi) {  // first leaf with code > key
-        const int32_t mid = (lo + hi) >> 1;
-        if (g.bcode[mid] <= key) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo > first ? lo - 1 : first;
-}
-
 __device__ __forceinline__ int cell_g(float v, float v0, float scale, int G) {
     const float t = __fmul_rn(__fsub_rn(v, v0), scale);
     const int lim = 1 << G;
@@ -159,14 +144,43 @@ __device__ __forceinline__ float warp_min(float v) {
     for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(kFull, v, o));
     return v;
 }
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// Squared distance from (x, y) up to a box [x0, x1] x [y0, y1]: a lower bound
+// of the squared distance to every point of the box, in the same rounding as
+// the exact distances (round-to-nearest is monotone, so a point farther out
+// never gets a smaller bound).
+__device__ __forceinline__ float box_lb(float x0, float y0, float x1, float y1, float qx0,
+                                        float qy0, float qx1, float qy1) {
+    float dx = 0.f, dy = 0.f;
+    if (qx1 < x0) dx = __fsub_rn(x0, qx1);
+    else if (qx0 > x1) dx = __fsub_rn(qx0, x1);
+    if (qy1 < y0) dy = __fsub_rn(y0, qy1);
+    else if (qy0 > y1) dy = __fsub_rn(qy0, y1);
+    return __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+}
+
+__device__ __forceinline__ int32_t key_id(unsigned long long key) {
+    const uint32_t lo = (uint32_t)key;
+    return lo == 0xFFFFFFFFu ? -1 : (int32_t)lo - 1;
+}
 
 // One packet = one pass of a single loop.  Each iteration (a) merges the
-// buffers if some lane holds kBatch candidates, (b) finds the next objects to
-// test -- first the packet's own leaves widened to >= k+1 objects (the paper's
-// first iteration and left/right walk), then, ring by ring outward from the
-// packet, every leaf of the level-G cells that can still hold a better object
-// for some lane -- and (c) tests up to kBatch objects against every lane.
-// Keeping one copy of the scan and one of the merge keeps the kernel small.
+// buffers if some lane holds kFlushAt candidates, (b) finds the next objects
+// to test -- first the packet's own leaves widened to >= k+1 objects (the
+// paper's first iteration and left/right walk), then, ring by ring outward from
+// the packet, every leaf of the level-G cells that can still hold a better
+// object for some lane -- and (c) tests up to kBatch objects against every lane.
+// The rings are gathered 32 cells at a time, one per lane: the lanes read the
+// cell map and then the leaf records of their cells side by side, a leaf
+// whose box is out of reach of the whole packet is dropped at once, and the
+// others wait in a ballot mask, tested exactly per lane against the lanes'
+// thresholds of the moment they are taken.  Keeping one copy of the scan and
+// one of the merge keeps the kernel small.
 template <int KC>
 __global__ void __launch_bounds__(kWarps * 32) k_expand(const ExpandArgs g) {
     __shared__ WarpSmem smem[kWarps];
@@ -202,9 +216,10 @@ __global__ void __launch_bounds__(kWarps * 32) k_expand(const ExpandArgs g) {
         if (__ballot_sync(kFull, active) == 0u) continue;
 
         // phase 1: the packet's own leaves, widened along the leaf order
-        int32_t b_lo = leaf_near(g, g.qs_key[q0]);
-        int32_t b_hi = leaf_near(g, g.qs_key[q0 + ql - 1]);
-        b_hi = b_hi < m ? b_hi + 1 : m;
+        int32_t b_lo = g.qs_leaf[q0];
+        int32_t b_hi = g.qs_leaf[q0 + ql - 1];
+        b_lo = b_lo < 0 ? 0 : (b_lo > m ? m : b_lo);
+        b_hi = b_hi < 0 ? 0 : (b_hi < m ? b_hi + 1 : m);
         if (b_hi < b_lo) b_hi = b_lo;
         {
             bool left = true;
@@ -224,7 +239,9 @@ __global__ void __launch_bounds__(kWarps * 32) k_expand(const ExpandArgs g) {
         float spec = kInf;
         if (g.spec2 > 0.f && !all_in_phase1 && b_hi - b_lo <= 64) {
             float area = 0.f;
-            for (int32_t b = b_lo; b < b_hi; ++b) area += ldexpf(1.f, -2 * (int)g.blevel[b]);
+            for (int32_t b = b_lo + lane; b < b_hi; b += 32)
+                area += ldexpf(1.f, -2 * (int)g.blevel[b]);
+            area = warp_sum(area);
             const float cnt1 = (float)(g.bstart[b_hi] - g.bstart[b_lo]);
             spec = g.spec2 * (float)k * area * g.side * g.side / (3.14159265f * cnt1);
         }
@@ -238,9 +255,12 @@ __global__ void __launch_bounds__(kWarps * 32) k_expand(const ExpandArgs g) {
         int32_t cur, end;                     // objects to test
         int32_t staged, staged_end;           // objects held in sm.obj
         int phase;
-        // phase-2 cursor: ring r, position t on it, leaves [bcur, bend) of a cell
+        // phase-2 cursor: ring r, next ring position t; the lanes' cells and
+        // last gathered leaves sit in sm.lc / sm.lbb / sm.lrg (shared memory
+        // keeps them out of the registers the merges need); bit i of pend: lane
+        // i's gathered leaf still waits for its exact test
         int r, t;
-        int32_t bcur, bend;
+        unsigned pend;
         float bx0 = 0.f, bx1 = 0.f, by0 = 0.f, by1 = 0.f;
         int ccx = 0, ccy = 0, cx0 = 0, cx1 = 0, cy0 = 0, cy1 = 0, rmax = 0;
         auto bound = [&]() {
@@ -267,8 +287,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_expand(const ExpandArgs g) {
         phase = 1;
         r = 0;
         t = 0;
-        bcur = 0;
-        bend = 0;
+        sm.lc[lane] = make_int2(0, 0);
+        pend = 0u;
         for (;;) {
             // (a) merge when a buffer is full, or when a list must fill up to bound the box
             const bool need_thr = phase == 1 && cur >= end && !all_in_phase1;
@@ -289,22 +309,42 @@ __global__ void __launch_bounds__(kWarps * 32) k_expand(const ExpandArgs g) {
                     bound();
                 }
                 bool found = false;
-                while (!found) {
-                    if (bcur < bend) {
-                        const int32_t b = bcur++;
-                        if (b >= b_lo && b < b_hi) continue;
-                        const float4 bb = g.baabb[b];
-                        float dx = 0.f, dy = 0.f;
-                        if (qx < bb.x) dx = __fsub_rn(bb.x, qx);
-                        else if (qx > bb.z) dx = __fsub_rn(qx, bb.z);
-                        if (qy < bb.y) dy = __fsub_rn(bb.y, qy);
-                        else if (qy > bb.w) dy = __fsub_rn(qy, bb.w);
-                        const float lb = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+                for (;;) {
+                    if (pend) {  // a gathered leaf: exact test of every lane
+                        const int i = __ffs(pend) - 1;
+                        pend &= pend - 1u;
+                        const float4 ab = sm.lbb[i];
+                        const float lb = box_lb(ab.x, ab.y, ab.z, ab.w, qx, qy, qx, qy);
                         if (__any_sync(kFull, lb <= L.thr)) {
-                            cur = g.bstart[b];
-                            end = g.bstart[b + 1];
+                            const int2 rg = sm.lrg[i];
+                            cur = rg.x;
+                            end = rg.y;
                             found = true;
+                            break;
                         }
+                        continue;
+                    }
+                    int2 lc = sm.lc[lane];
+                    if (__any_sync(kFull, lc.x < lc.y)) {
+                        // next leaf of every lane's cell; the packet's box against
+                        // the largest threshold drops what no lane can use
+                        const float R2 = warp_max(active ? L.thr : 0.f);
+                        bool keep = false;
+                        __syncwarp();  // every lane is done with the last gathered boxes
+                        if (lc.x < lc.y) {
+                            const int32_t b = lc.x++;
+                            sm.lc[lane] = lc;
+                            if (b < b_lo || b >= b_hi) {
+                                const float4 bb = g.baabb[b];
+                                const int2 rg = g.brange[b];
+                                keep = rg.x < rg.y &&
+                                       box_lb(bb.x, bb.y, bb.z, bb.w, bx0, by0, bx1, by1) <= R2;
+                                sm.lbb[lane] = bb;
+                                sm.lrg[lane] = rg;
+                            }
+                        }
+                        pend = __ballot_sync(kFull, keep);
+                        __syncwarp();
                         continue;
                     }
                     const int per = r == 0 ? 1 : 8 * r;
@@ -315,17 +355,26 @@ __global__ void __launch_bounds__(kWarps * 32) k_expand(const ExpandArgs g) {
                         if (r > rmax) break;
                         continue;
                     }
-                    int cx, cy;
-                    if (r == 0) { cx = ccx; cy = ccy; }
-                    else if (t < 2 * r + 1) { cx = ccx - r + t; cy = ccy - r; }
-                    else if (t < 4 * r + 2) { cx = ccx - r + (t - 2 * r - 1); cy = ccy + r; }
-                    else if (t < 6 * r + 1) { cx = ccx - r; cy = ccy - r + 1 + (t - 4 * r - 2); }
-                    else { cx = ccx + r; cy = ccy - r + 1 + (t - 6 * r - 1); }
-                    ++t;
-                    if (cx < cx0 || cx > cx1 || cy < cy0 || cy > cy1) continue;
-                    const uint32_t c = interleave((uint32_t)cx, (uint32_t)cy);
-                    bcur = g.cb[c];
-                    bend = g.cb[c + 1];
+                    // the next 32 positions of ring r, one per lane
+                    const int u = t + lane;
+                    lc = make_int2(0, 0);
+                    if (u < per) {
+                        int cx, cy;
+                        if (r == 0) { cx = ccx; cy = ccy; }
+                        else if (u < 2 * r + 1) { cx = ccx - r + u; cy = ccy - r; }
+                        else if (u < 4 * r + 2) { cx = ccx - r + (u - 2 * r - 1); cy = ccy + r; }
+                        else if (u < 6 * r + 1) { cx = ccx - r; cy = ccy - r + 1 + (u - 4 * r - 2); }
+                        else { cx = ccx + r; cy = ccy - r + 1 + (u - 6 * r - 1); }
+                        if (cx >= cx0 && cx <= cx1 && cy >= cy0 && cy <= cy1) {
+                            const uint32_t c = interleave((uint32_t)cx, (uint32_t)cy);
+                            lc.x = g.cb[c];
+                            lc.y = g.cb[c + 1];
+                            lc.x = lc.x > 0 ? lc.x : 0;
+                            lc.y = lc.y < m ? lc.y : m;
+                        }
+                    }
+                    sm.lc[lane] = lc;
+                    t += 32;
                 }
                 if (!found) break;
             }
@@ -376,21 +425,64 @@ __global__ void __launch_bounds__(kWarps * 32) k_expand(const ExpandArgs g) {
         break;
         }
 
-        // write the row in caller order
-        if (active) {
-            int32_t *oi = g.out_ids + (int64_t)orig * k;
-            float *od = g.out_d2 + (int64_t)orig * k;
+        // a8: write the rows in caller order
+        if constexpr (KC <= 32) {
+            // through shared memory, so that neighbouring lanes write
+            // neighbouring entries of a row: ids first, then distances
+            constexpr int S = KC + 4;  // row stride (words); rows stay 16-byte aligned
+            uint32_t *rows = reinterpret_cast<uint32_t *>(&sm.buf[0][0]);
+            int32_t *s_orig = reinterpret_cast<int32_t *>(&sm.obj[0]);
+            __syncwarp();
+            s_orig[lane] = active ? orig : -1;
+            const int vw = g.vec_out ? 4 : 1;
+            const int per_row = k / vw;
+            const int total = ql * per_row;
+            for (int pass = 0; pass < 2; ++pass) {
 #pragma unroll
-            for (int i = 0; i < KC; ++i) {
-                if (i >= KC - k) {
-                    const int rr = i - (KC - k);
-                    const unsigned long long key = L.lst[i];
-                    if (key == kPad) {
-                        oi[rr] = -1;
-                        od[rr] = kInf;
-                    } else {
-                        oi[rr] = (int32_t)((uint32_t)key) - 1;
-                        od[rr] = __uint_as_float((uint32_t)(key >> 32));
+                for (int i = 0; i < KC; i += 4) {
+                    uint4 v;
+                    if (pass == 0)
+                        v = make_uint4((uint32_t)key_id(L.lst[i]), (uint32_t)key_id(L.lst[i + 1]),
+                                       (uint32_t)key_id(L.lst[i + 2]),
+                                       (uint32_t)key_id(L.lst[i + 3]));
+                    else
+                        v = make_uint4((uint32_t)(L.lst[i] >> 32), (uint32_t)(L.lst[i + 1] >> 32),
+                                       (uint32_t)(L.lst[i + 2] >> 32),
+                                       (uint32_t)(L.lst[i + 3] >> 32));
+                    *reinterpret_cast<uint4 *>(rows + lane * S + i) = v;
+                }
+                __syncwarp();
+                uint32_t *out = pass == 0 ? reinterpret_cast<uint32_t *>(g.out_ids)
+                                          : reinterpret_cast<uint32_t *>(g.out_d2);
+                for (int base = 0; base < total; base += 32) {
+                    const int v = base + lane;
+                    if (v < total) {
+                        const int row = v / per_row;
+                        const int c = (v - row * per_row) * vw;
+                        const int32_t o = s_orig[row];
+                        if (o >= 0) {
+                            const uint32_t *src = rows + row * S + (KC - k) + c;
+                            uint32_t *dst = out + (int64_t)o * k + c;
+                            if (vw == 4)
+                                *reinterpret_cast<uint4 *>(dst) =
+                                    *reinterpret_cast<const uint4 *>(src);
+                            else
+                                *dst = *src;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        } else {
+            if (active) {
+                int32_t *oi = g.out_ids + (int64_t)orig * k;
+                float *od = g.out_d2 + (int64_t)orig * k;
+#pragma unroll
+                for (int i = 0; i < KC; ++i) {
+                    if (i >= KC - k) {
+                        const int rr = i - (KC - k);
+                        oi[rr] = key_id(L.lst[i]);
+                        od[rr] = __uint_as_float((uint32_t)(L.lst[i] >> 32));
                     }
                 }
             }
@@ -433,14 +525,14 @@ void launch_expand(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t *out
     a.ys = w.ys;
     a.sid = w.sid;
     a.bstart = w.bstart;
-    a.bcode = w.bcode;
     a.baabb = w.baabb;
+    a.brange = w.brange;
     a.cb = w.cb;
     a.qs_x = w.qs_x;
     a.qs_y = w.qs_y;
     a.qs_id = w.qs_id;
     a.qs_orig = w.qs_orig;
-    a.qs_key = w.qs_key;
+    a.qs_leaf = w.qs_leaf;
     a.pk_start = w.pk_start;
     a.pk_len = w.pk_len;
     a.scalars = w.scalars;
@@ -459,6 +551,8 @@ void launch_expand(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t *out
     a.n = w.n;
     a.n_q = n_q;
     a.pk_cap = packet_capacity(w);
+    a.vec_out = k % 4 == 0 && ((reinterpret_cast<uintptr_t>(out_ids) |
+                                reinterpret_cast<uintptr_t>(out_d2)) & 15u) == 0;
     if (k <= 4) run<4>(a, w.device, s);
     else if (k <= 8) run<8>(a, w.device, s);
     else if (k <= 16) run<16>(a, w.device, s);

@@ -296,7 +296,8 @@ __global__ void __launch_bounds__(256) k_leaves(
     int th, int G, const float *__restrict__ px, const float *__restrict__ py,
     float *__restrict__ xs, float *__restrict__ ys, int32_t *__restrict__ sid,
     int32_t *__restrict__ inv, int32_t *__restrict__ bstart, uint32_t *__restrict__ bcode,
-    uint8_t *__restrict__ blevel, int32_t *__restrict__ cb, int64_t ncell, int32_t *scalars,
+    uint8_t *__restrict__ blevel, int32_t *__restrict__ obj_leaf, int32_t *__restrict__ cb,
+    int64_t ncell, int32_t *scalars,
     uint64_t *status, uint32_t *ticket, const uint32_t *__restrict__ tickinfo, uint32_t site,
     uint32_t *err) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -393,6 +394,8 @@ __global__ void __launch_bounds__(256) k_leaves(
     uint32_t b = excl + off;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
+        const int64_t iq = t0 + tid * 4 + q;
+        if (iq < n) obj_leaf[iq] = (int32_t)((fl & (1u << q)) ? b : b - 1u);
         if ((fl & (1u << q)) && b < (uint64_t)n) {
             const int e = tid * 4 + q;
             const int lam = s_lam[e + 1];
@@ -462,14 +465,16 @@ static size_t leaves_smem(int th) {
 // bounds of member distances by the expansion).
 __global__ void k_leaf_aabb(const int32_t *__restrict__ bstart, const int32_t *__restrict__ scalars,
                             const float *__restrict__ xs, const float *__restrict__ ys,
-                            float4 *__restrict__ baabb, int64_t n) {
+                            float4 *__restrict__ baabb, int2 *__restrict__ brange, int64_t n) {
     const int32_t m = scalars[kScalarLeaves];
     for (int32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < m; b += gridDim.x * blockDim.x) {
         const int32_t s = bstart[b], e = bstart[b + 1];
         if (s < 0 || e <= s || e > n) {  // leaves are never empty
             baabb[b] = make_float4(0.f, 0.f, -1.f, -1.f);
+            brange[b] = make_int2(0, 0);
             continue;
         }
+        brange[b] = make_int2(s, e);
         float x0 = xs[s], x1 = x0, y0 = ys[s], y1 = y0;
         for (int32_t i = s + 1; i < e; ++i) {
             const float x = xs[i], y = ys[i];
@@ -489,11 +494,12 @@ void launch_leaves(World &w, const Plan &p, cudaStream_t s) {
     prepare_kernels();
     const int64_t ncell = 1ll << (2 * p.G);
     k_leaves<<<tiles, 256, sm, s>>>(w.key[r], w.val[r], w.n, p.L, p.th, p.G, w.px, w.py, w.xs,
-                                    w.ys, w.sid, w.inv, w.bstart, w.bcode, w.blevel, w.cb,
+                                    w.ys, w.sid, w.inv, w.bstart, w.bcode, w.blevel, w.obj_leaf,
+                                    w.cb,
                                     ncell, w.scalars, w.status, w.counters + kCtrLeaves,
                                     w.tickinfo, w.site++, w.err);
     const int g = grid_for(w.n, 256, num_sms(w.device) * 8);
-    k_leaf_aabb<<<g, 256, 0, s>>>(w.bstart, w.scalars, w.xs, w.ys, w.baabb, w.n);
+    k_leaf_aabb<<<g, 256, 0, s>>>(w.bstart, w.scalars, w.xs, w.ys, w.baabb, w.brange, w.n);
     w.launches += 2;
 }
 
@@ -600,7 +606,8 @@ __global__ void k_query_place(const int32_t *__restrict__ q_id, int64_t n_q, int
 __global__ void k_query_fill(int64_t n, int64_t n_q, const int32_t *__restrict__ qoff,
                              const float *__restrict__ xs, const float *__restrict__ ys,
                              const int32_t *__restrict__ sid, const uint32_t *__restrict__ skey,
-                             float *qs_x, float *qs_y, int32_t *qs_id, uint32_t *qs_key) {
+                             const int32_t *__restrict__ obj_leaf, float *qs_x, float *qs_y,
+                             int32_t *qs_id, uint32_t *qs_key, int32_t *qs_leaf) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
         int32_t a = qoff[p], b = qoff[p + 1];
@@ -610,11 +617,13 @@ __global__ void k_query_fill(int64_t n, int64_t n_q, const int32_t *__restrict__
         const float x = xs[p], y = ys[p];
         const int32_t id = sid[p];
         const uint32_t key = skey[p];
+        const int32_t leaf = obj_leaf[p];
         for (int32_t j = a; j < b; ++j) {
             qs_x[j] = x;
             qs_y[j] = y;
             qs_id[j] = id;
             qs_key[j] = key;
+            qs_leaf[j] = leaf;
         }
     }
 }
@@ -628,21 +637,45 @@ void launch_queries_at_issuers(World &w, const Plan &p, const int32_t *q_id, int
     k_query_place<<<g, 256, 0, s>>>(q_id, n_q, w.n, w.inv, w.qoff, w.qcnt, w.qs_orig);
     const uint32_t *skey = w.key[p.passes & 1];
     k_query_fill<<<grid_for(w.n, 256, num_sms(w.device) * 8), 256, 0, s>>>(
-        w.n, n_q, w.qoff, w.xs, w.ys, w.sid, skey, w.qs_x, w.qs_y, w.qs_id, w.qs_key);
+        w.n, n_q, w.qoff, w.xs, w.ys, w.sid, skey, w.obj_leaf, w.qs_x, w.qs_y, w.qs_id,
+        w.qs_key, w.qs_leaf);
     w.launches += 3;
+}
+
+// Leaf next to a level-L key in Morton order: the last leaf of the key's
+// level-G cell whose first code is <= key, else the cell's first leaf, or the
+// insertion point when the cell has no leaf.
+__device__ __forceinline__ int32_t leaf_near(const int32_t *__restrict__ cb,
+                                             const uint32_t *__restrict__ bcode, int L, int G,
+                                             uint32_t key) {
+    uint32_t c = key >> (2 * (L - G));
+    const uint32_t last = (1u << (2 * G)) - 1u;
+    c = c < last ? c : last;
+    int32_t lo = cb[c], hi = cb[c + 1];
+    if (lo == hi) return lo;
+    const int32_t first = lo;
+    while (lo < hi) {  // first leaf with code > key
+        const int32_t mid = (lo + hi) >> 1;
+        if (bcode[mid] <= key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo > first ? lo - 1 : first;
 }
 
 __global__ void k_query_gather(const uint32_t *__restrict__ skey, const int32_t *__restrict__ sval,
                                int64_t n_q, const int32_t *__restrict__ q_id,
                                const float *__restrict__ q_x, const float *__restrict__ q_y,
                                float *qs_x, float *qs_y, int32_t *qs_id, int32_t *qs_orig,
-                               uint32_t *qs_key, int32_t *scalars) {
+                               uint32_t *qs_key, int32_t *scalars, const int32_t *__restrict__ cb,
+                               const uint32_t *__restrict__ bcode, int L, int G,
+                               int32_t *qs_leaf) {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t == 0) scalars[kScalarValidQueries] = (int32_t)n_q;
     for (int64_t j = t; j < n_q; j += (int64_t)gridDim.x * blockDim.x) {
         const int32_t v = sval[j];
         qs_key[j] = skey[j];
         qs_orig[j] = v;
+        qs_leaf[j] = leaf_near(cb, bcode, L, G, skey[j]);
         if (v >= 0) {
             qs_x[j] = q_x[v];
             qs_y[j] = q_y[v];
@@ -667,7 +700,7 @@ void launch_queries_explicit(World &w, const Plan &p, const int32_t *q_id, const
     const int r = p.passes & 1;
     k_query_gather<<<grid_for(n_q, 256, num_sms(w.device) * 8), 256, 0, s>>>(
         w.key[r], w.val[r], n_q, q_id, q_x, q_y, w.qs_x, w.qs_y, w.qs_id, w.qs_orig, w.qs_key,
-        w.scalars);
+        w.scalars, w.cb, w.bcode, p.L, p.G, w.qs_leaf);
     w.launches += 2;
 }
 

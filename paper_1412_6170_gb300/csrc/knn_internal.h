@@ -71,11 +71,14 @@ struct World {
     uint32_t *bcode = nullptr;
     uint8_t *blevel = nullptr;
     float4 *baabb = nullptr;
+    int2 *brange = nullptr;      // leaf b holds sorted objects [x, y)
+    int32_t *obj_leaf = nullptr; // leaf of every sorted object
     int32_t *cb = nullptr;
     int32_t *qcnt = nullptr, *qoff = nullptr;
     float *qs_x = nullptr, *qs_y = nullptr;
     int32_t *qs_id = nullptr, *qs_orig = nullptr;
     uint32_t *qs_key = nullptr;
+    int32_t *qs_leaf = nullptr;  // a leaf at (or next to) each sorted query
     int32_t *qcs = nullptr, *npk = nullptr, *pk_off = nullptr;
     int32_t *pk_start = nullptr, *pk_len = nullptr;
     uint64_t *status = nullptr;
