@@ -146,32 +146,44 @@ __device__ __forceinline__ uint32_t lookback_warp(uint64_t *status, uint32_t til
     return excl;
 }
 
-// Sequential per-thread look-back over a strided status array (one digit of a
-// radix pass per thread): status[t * stride].
+// Per-thread look-back over a strided status array (one digit of a radix pass
+// per thread): status[t * stride].  The words of kAhead predecessors are read
+// together and then taken in order, so a run of tiles that have published only
+// their aggregates costs one memory round trip per kAhead tiles.
 __device__ __forceinline__ uint32_t lookback_thread(uint64_t *status, uint32_t tile,
                                                     uint32_t stride, uint32_t epoch,
                                                     uint32_t agg, uint32_t *err) {
+    constexpr int kAhead = 8;
     if (tile == 0) {
         st_status(&status[0], pack_status(epoch, kFlagPrefix, agg));
         return 0u;
     }
     st_status(&status[(uint64_t)tile * stride], pack_status(epoch, kFlagAgg, agg));
     uint32_t excl = 0;
-    for (int64_t t = (int64_t)tile - 1; t >= 0; --t) {
-        uint64_t s = ld_status(&status[(uint64_t)t * stride]);
-        uint32_t spins = 0;
-        while (!status_ready(s, epoch)) {
-            ++spins;
-            if (spins > kSpinLimit || ((spins & 63u) == 0u && ld_abort(err))) {
-                raise_timeout(err);
-                s = pack_status(epoch, kFlagPrefix, 0u);
-                break;
+    bool done = false;
+    for (int64_t t = (int64_t)tile - 1; t >= 0 && !done; t -= kAhead) {
+        uint64_t s[kAhead];
+#pragma unroll
+        for (int i = 0; i < kAhead; ++i)
+            s[i] = t - i >= 0 ? ld_status(&status[(uint64_t)(t - i) * stride])
+                              : pack_status(epoch, kFlagPrefix, 0u);
+#pragma unroll
+        for (int i = 0; i < kAhead; ++i) {
+            if (done) break;
+            uint32_t spins = 0;
+            while (!status_ready(s[i], epoch)) {
+                ++spins;
+                if (spins > kSpinLimit || ((spins & 63u) == 0u && ld_abort(err))) {
+                    raise_timeout(err);
+                    s[i] = pack_status(epoch, kFlagPrefix, 0u);
+                    break;
+                }
+                if (spins > 8) __nanosleep(100);
+                s[i] = ld_status(&status[(uint64_t)(t - i) * stride]);
             }
-            if (spins > 8) __nanosleep(100);
-            s = ld_status(&status[(uint64_t)t * stride]);
+            excl += status_value(s[i]);
+            if (status_flag(s[i]) == kFlagPrefix) done = true;
         }
-        excl += status_value(s);
-        if (status_flag(s) == kFlagPrefix) break;
     }
     st_status(&status[(uint64_t)tile * stride], pack_status(epoch, kFlagPrefix, excl + agg));
     return excl;

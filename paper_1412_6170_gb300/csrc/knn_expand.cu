@@ -235,7 +235,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_expand(const ExpandArgs g) {
 
         // Speculative first threshold: alpha^2 times the area that holds k objects
         // at the density of the packet's own leaves (objects / quadtree area).  A
-        // lane that finds fewer than k objects within it is redone exactly below.
+        // lane that finds fewer than k objects within it is redone below, first
+        // within four times that area, then without a threshold.
         float spec = kInf;
         if (g.spec2 > 0.f && !all_in_phase1 && b_hi - b_lo <= 64) {
             float area = 0.f;
@@ -408,14 +409,15 @@ __global__ void __launch_bounds__(kWarps * 32) k_expand(const ExpandArgs g) {
         }
         flush<KC>(L, sm, lane);
         // a lane whose speculative threshold held fewer than k objects starts over
-        // with no threshold; lanes that are done take no part in the second walk
-        if (attempt == 0 && spec < kInf) {
+        // with four times the threshold, then with none; lanes that are done take
+        // no part in the later walks
+        if (attempt < 2 && spec < kInf) {
             const bool redo = active && L.lst[KC - 1] == kPad;
             if (__any_sync(kFull, redo)) {
                 if (redo) {
 #pragma unroll
                     for (int i = 0; i < KC; ++i) L.lst[i] = i < KC - k ? 0ull : kPad;
-                    L.thr = kInf;
+                    L.thr = attempt == 0 ? 4.f * spec : kInf;
                 } else {
                     L.thr = -kInf;
                 }
@@ -542,7 +544,10 @@ void launch_expand(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t *out
     a.x0 = w.desc.x0;
     a.y0 = w.desc.y0;
     a.side = w.desc.side;
-    a.spec2 = 2.25f;
+    // alpha^2: the disc of the first threshold holds k + 3 sqrt(k) + 2 objects
+    // on average, about three standard deviations of a Poisson count above k,
+    // so a redo is rare and the first walk stays short for large k
+    a.spec2 = 1.0f + 3.0f / sqrtf((float)k) + 2.0f / (float)k;
     a.blevel = w.blevel;
     a.scale_g = ldexpf(w.scale, -(p.L - p.G));
     a.L = p.L;
