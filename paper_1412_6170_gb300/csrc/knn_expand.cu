@@ -50,10 +50,11 @@ struct ExpandArgs {
 // every real key and marks an empty slot; 0 is below every real key.
 constexpr unsigned long long kPad = 0x7f800000FFFFFFFFull;
 
-// Per-lane candidate buffer (shared memory, kBufCap slots per lane):
-// candidates whose d^2 is within the lane's current threshold are appended
-// there and merged into the sorted register list kBatch at a time, once some
-// lane holds kFlushAt of them (late merges keep the batches full).
+// Per-lane candidate buffer (shared memory, kBufCap slots per lane, a stack):
+// candidates whose d^2 is within the lane's current threshold are pushed
+// there.  Once some lane holds kFlushAt of them, every lane merges its newest
+// kBatch into its sorted register list -- one batch, not the whole buffer, so
+// that lanes that buffer slowly fill their batches before they are merged.
 constexpr int kBatch = 8;
 constexpr int kBufCap = 32;
 constexpr int kFlushAt = kBufCap - kBatch;
@@ -109,22 +110,21 @@ struct Lane {
     int count;                   // buffered candidates (slots 0 .. count-1)
 };
 
-// Merge every buffered candidate of every lane into its list, kBatch at a time.
-// The threshold becomes the list's k-th distance once the list is full (it
-// never rises above the threshold the walk started with).
+// Merge the newest kBatch buffered candidates (or all, if fewer) into the
+// list.  The threshold becomes the list's k-th distance once the list is full
+// (it never rises above the threshold the walk started with).
 template <int KC>
-__device__ __forceinline__ void flush(Lane<KC> &L, WarpSmem &sm, int lane) {
-    for (int base = 0; __any_sync(kFull, L.count > base); base += kBatch) {
-        unsigned long long b[kBatch];
+__device__ __forceinline__ void merge_top(Lane<KC> &L, WarpSmem &sm, int lane) {
+    const int base = L.count > kBatch ? L.count - kBatch : 0;
+    unsigned long long b[kBatch];
 #pragma unroll
-        for (int t = 0; t < kBatch; ++t)
-            b[t] = base + t < L.count ? sm.buf[base + t][lane] : kPad;
-        sort8(b);
-        merge_batch<KC>(L.lst, b);
-    }
-    L.count = 0;
+    for (int t = 0; t < kBatch; ++t) b[t] = base + t < L.count ? sm.buf[base + t][lane] : kPad;
+    sort8(b);
+    merge_batch<KC>(L.lst, b);
+    L.count = base;
     L.thr = fminf(L.thr, __uint_as_float((uint32_t)(L.lst[KC - 1] >> 32)));
 }
+
 
 __device__ __forceinline__ int cell_g(float v, float v0, float scale, int G) {
     const float t = __fmul_rn(__fsub_rn(v, v0), scale);
@@ -169,8 +169,8 @@ __device__ __forceinline__ int32_t key_id(unsigned long long key) {
     return lo == 0xFFFFFFFFu ? -1 : (int32_t)lo - 1;
 }
 
-// One packet = one pass of a single loop.  Each iteration (a) merges the
-// buffers if some lane holds kFlushAt candidates, (b) finds the next objects
+// One packet = one pass of a single loop.  Each iteration (a) merges a batch
+// of the buffers if some lane holds kFlushAt candidates, (b) finds the next objects
 // to test -- first the packet's own leaves widened to >= k+1 objects (the
 // paper's first iteration and left/right walk), then, ring by ring outward from
 // the packet, every leaf of the level-G cells that can still hold a better
@@ -255,7 +255,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_expand(const ExpandArgs g) {
 
         int32_t cur, end;                     // objects to test
         int32_t staged, staged_end;           // objects held in sm.obj
-        int phase;
+        int phase;                            // 1: own leaves, 2: rings, 3: draining
+        bool flushing = false;                // small lists: a full buffer drains them all
         // phase-2 cursor: ring r, next ring position t; the lanes' cells and
         // last gathered leaves sit in sm.lc / sm.lbb / sm.lrg (shared memory
         // keeps them out of the registers the merges need); bit i of pend: lane
@@ -291,15 +292,25 @@ __global__ void __launch_bounds__(kWarps * 32) k_expand(const ExpandArgs g) {
         sm.lc[lane] = make_int2(0, 0);
         pend = 0u;
         for (;;) {
-            // (a) merge when a buffer is full, or when a list must fill up to bound the box
-            const bool need_thr = phase == 1 && cur >= end && !all_in_phase1;
-            if (__any_sync(kFull, L.count >= kFlushAt ||
-                                      (need_thr && L.count > 0 && !(L.thr < kInf))))
-                flush<KC>(L, sm, lane);
+            // (a) merge a batch when a buffer is full, when a list must fill up to
+            // bound the box, or when the walk is over (the only merge site)
+            const bool drain = phase == 3 || flushing ||
+                               (phase == 1 && cur >= end && !all_in_phase1 && !(L.thr < kInf));
+            const bool full = __any_sync(kFull, L.count >= kFlushAt);
+            if (full || __any_sync(kFull, drain && L.count > 0)) {
+                flushing = KC <= 8 && (flushing || full);
+                merge_top<KC>(L, sm, lane);
+                continue;
+            }
+            flushing = false;
+            if (phase == 3) break;
             // (b) next objects
             if (cur >= end) {
                 if (phase == 1) {
-                    if (all_in_phase1) break;
+                    if (all_in_phase1) {
+                        phase = 3;
+                        continue;
+                    }
                     phase = 2;
                     bx0 = warp_min(active ? qx : kInf);
                     bx1 = warp_max(active ? qx : -kInf);
@@ -377,7 +388,10 @@ __global__ void __launch_bounds__(kWarps * 32) k_expand(const ExpandArgs g) {
                     sm.lc[lane] = lc;
                     t += 32;
                 }
-                if (!found) break;
+                if (!found) {
+                    phase = 3;
+                    continue;
+                }
             }
             // (c) test up to kBatch objects; stage 32 at a time through shared memory
             if (cur < staged || cur >= staged_end) {
@@ -407,7 +421,6 @@ __global__ void __launch_bounds__(kWarps * 32) k_expand(const ExpandArgs g) {
             }
             cur += n_here;
         }
-        flush<KC>(L, sm, lane);
         // a lane whose speculative threshold held fewer than k objects starts over
         // with four times the threshold, then with none; lanes that are done take
         // no part in the later walks
