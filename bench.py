@@ -428,12 +428,22 @@ def run_gpu(args):
 
     world = knnq.World(x0, y0, k_max=K, max_queries=N_OBJ)
     world.set_profiling(True)
+    # A simulation hands each tick's moves over in one of two device buffers
+    # (double buffering); the move is copied into place before the step's
+    # timed region, so inputs are resident in HBM when it starts.  knn_tick
+    # records one graph per buffer and replays it.
+    bx = [torch.empty_like(ux[0]) for _ in range(2)]
+    by = [torch.empty_like(uy[0]) for _ in range(2)]
+
+    def stage_inputs(i):
+        bx[i % 2].copy_(ux[i % N_TICKS])
+        by[i % 2].copy_(uy[i % N_TICKS])
 
     def tick(i):
-        world.tick(K, qid, ids_d, ux[i % N_TICKS], uy[i % N_TICKS], out_ids=out_ids,
-                   out_d2=out_d2)
+        world.tick(K, qid, ids_d, bx[i % 2], by[i % 2], out_ids=out_ids, out_d2=out_d2)
 
     for i in range(args.warmup):
+        stage_inputs(i)
         tick(i)
     torch.cuda.synchronize()
     st, bits = world.status()
@@ -465,6 +475,7 @@ def run_gpu(args):
     with Clocks(local) as clk:
         wall0 = time.perf_counter()
         for s in range(args.steps):
+            stage_inputs(args.warmup + s)
             flush.zero_()
             a, b = ev[s]
             a.record(stream)
@@ -527,7 +538,9 @@ def run_gpu(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_objects": N_OBJ, "k": K, "queries_per_tick": N_OBJ,
-                   "path": "plain (one knn_tick per tick)", "l2": "flushed between steps",
+                   "path": "plain (one knn_tick per tick; moves double-buffered on the "
+                           "device, copied in before each step's timed region)",
+                   "l2": "flushed between steps",
                    "parallelism": "replicas" if n_gpus > 1 else "single GPU"},
         "p50_tick_ms": p50, "p99_tick_ms": p99,
         "stages_ms": {k: v / args.steps for k, v in stage_sums.items()},

@@ -255,6 +255,23 @@ knn_status knn_world_positions(knn_world w, float *x_dev, float *y_dev, void *st
  * count; memsets and copies are not kernels and are not counted). */
 knn_status knn_world_launches(knn_world w, int64_t *count);
 
+/* Tick graphs.  knn_tick records a tick as a CUDA graph and replays it when a
+ * later tick passes the same arguments (pointers and sizes), tuning and
+ * profiling setting as one of the last 16 recorded ticks.  A replay runs the
+ * same kernels, reads the inputs afresh and advances the world's device state
+ * exactly like direct launches, so results are identical; it only saves the
+ * launch overhead.  enable = 0 launches the kernels directly.  A stream that
+ * is itself being recorded always gets direct launches.  On by default. */
+knn_status knn_world_set_graphs(knn_world w, int32_t enable);
+
+/* Records the graph of a tick with these arguments without running it, so
+ * that a later knn_tick with the same arguments (and the same tuning and
+ * profiling setting) replays it from its first call; for a loop that cycles a
+ * fixed set of input and output buffers.  At most 16 are kept per world.
+ * KNN_ERR_INVALID when graphs are off or the arguments would be rejected by
+ * knn_tick. */
+knn_status knn_world_record_tick(knn_world w, const knn_tick_args *args);
+
 /* Per-stage device times of ticks.  When enabled, each tick records CUDA
  * events around its stages on its stream; knn_world_stage_times synchronizes
  * and writes up to n_stages milliseconds for the last tick.  Stage names come

@@ -214,13 +214,113 @@ void release(World &w) {
     if (w.stage) cudaFree(w.stage);
     for (int i = 0; i <= knnq::kMaxStages; ++i)
         if (w.ev[i]) cudaEventDestroy(w.ev[i]);
+    for (knnq::TickGraph &t : w.tick_graph) {
+        if (t.exec) cudaGraphExecDestroy(t.exec);
+        t.exec = nullptr;
+    }
+    if (w.capture_stream) cudaStreamDestroy(w.capture_stream);
+    w.capture_stream = nullptr;
     w.arena = nullptr;
     w.stage = nullptr;
 }
 
+bool same_tick(const knnq::TickGraph &t, const knn_tick_args &a, const knnq::Plan &p,
+               bool marks) {
+    return t.exec && t.marks == marks && std::memcmp(&t.args, &a, sizeof(a)) == 0 &&
+           std::memcmp(&t.plan, &p, sizeof(p)) == 0;
+}
+
+// The world's graph for a tick with these arguments: a cached one, else this
+// tick recorded (on an internal stream: the caller's stream may be the legacy
+// default stream, which cannot be recorded) into the least recently used slot
+// (updated in place, or instantiated anew).  *recorded tells which.
+knn_status tick_graph(World &w, const knn_tick_args &a, knnq::TickGraph **out, bool *recorded) {
+    const knnq::Plan p = knnq::plan_for(w, a.n_q, a.k);
+    const bool marks = w.profiling;
+    *recorded = false;
+    knnq::TickGraph *hit = nullptr, *victim = &w.tick_graph[0];
+    for (knnq::TickGraph &t : w.tick_graph) {
+        if (same_tick(t, a, p, marks)) {
+            hit = &t;
+            break;
+        }
+        if (!t.exec || (victim->exec && t.used < victim->used)) victim = &t;
+    }
+    if (!hit) {
+        if (!w.capture_stream &&
+            cudaStreamCreateWithFlags(&w.capture_stream, cudaStreamNonBlocking) != cudaSuccess)
+            return cuda_fail(cudaGetLastError(), "knn_tick: stream creation");
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(w.capture_stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e, "knn_tick: begin capture");
+        const int64_t l0 = w.launches;
+        const cudaStream_t last_stream = w.last_stream;
+        const knnq::Plan last_plan = w.last_plan;
+        knnq::enqueue_tick(w, a, w.capture_stream, marks);
+        w.last_stream = last_stream;  // nothing ran yet
+        w.last_plan = last_plan;
+        const int64_t launches = w.launches - l0;
+        e = cudaStreamEndCapture(w.capture_stream, &graph);
+        if (e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return cuda_fail(e, "knn_tick: end capture");
+        }
+        bool updated = false;
+        if (victim->exec) {
+            cudaGraphExecUpdateResultInfo info;
+            updated = cudaGraphExecUpdate(victim->exec, graph, &info) == cudaSuccess;
+            if (!updated) {
+                cudaGetLastError();
+                cudaGraphExecDestroy(victim->exec);
+                victim->exec = nullptr;
+            }
+        }
+        if (!updated) {
+            e = cudaGraphInstantiate(&victim->exec, graph, 0);
+            if (e != cudaSuccess) {
+                victim->exec = nullptr;
+                cudaGraphDestroy(graph);
+                return cuda_fail(e, "knn_tick: instantiate");
+            }
+        }
+        cudaGraphDestroy(graph);
+        victim->args = a;
+        victim->plan = p;
+        victim->marks = marks;
+        victim->launches = launches;
+        w.launches -= launches;  // counted when the graph runs
+        hit = victim;
+        *recorded = true;
+    }
+    hit->used = ++w.tick_clock;
+    *out = hit;
+    return KNN_OK;
+}
+
+// One tick through the world's graph cache.
+knn_status tick_via_graph(World &w, const knn_tick_args &a, cudaStream_t s) {
+    knnq::TickGraph *g = nullptr;
+    bool recorded = false;
+    const knn_status st = tick_graph(w, a, &g, &recorded);
+    if (st != KNN_OK) return st;
+    const cudaError_t e = cudaGraphLaunch(g->exec, s);
+    if (e != cudaSuccess) return cuda_fail(e, "knn_tick: graph launch");
+    w.launches += g->launches;
+    w.last_stream = s;
+    w.last_plan = g->plan;
+    return KNN_OK;
+}
+
 void mark(World &w, int i, cudaStream_t s) {
     if (w.profiling && i <= knnq::kMaxStages) {
-        cudaEventRecord(w.ev[i], s);
+        // while a tick is being recorded, an "external" record becomes an event
+        // record node of the graph (a plain one would only mark a dependency)
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(s, &cs);
+        if (cs == cudaStreamCaptureStatusActive)
+            cudaEventRecordWithFlags(w.ev[i], s, cudaEventRecordExternal);
+        else
+            cudaEventRecord(w.ev[i], s);
         w.n_stage_events = i + 1;
     }
 }
@@ -366,7 +466,14 @@ knn_status knn_tick(knn_world h, const int32_t *upd_id, const float *upd_x, cons
     if (st != KNN_OK) return st;
     World &w = h->w;
     cudaSetDevice(w.device);
-    knnq::enqueue_tick(w, a, (cudaStream_t)stream, w.profiling);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    // a stream the caller is recording gets the kernels themselves
+    if (w.graphs && cudaStreamIsCapturing(s, &cs) == cudaSuccess &&
+        cs == cudaStreamCaptureStatusNone)
+        return tick_via_graph(w, a, s);
+    cudaGetLastError();
+    knnq::enqueue_tick(w, a, s, w.profiling);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "knn_tick launch");
     return KNN_OK;
@@ -510,6 +617,30 @@ knn_status knn_world_set_profiling(knn_world h, int32_t enable) {
     }
     w.profiling = enable != 0;
     w.n_stage_events = 0;
+    return KNN_OK;
+}
+
+knn_status knn_world_record_tick(knn_world h, const knn_tick_args *args) {
+    if (!h || !args) return fail(KNN_ERR_INVALID, "knn_world_record_tick: NULL argument");
+    World &w = h->w;
+    const knn_status st = knnq::check_tick_args(w, *args, "knn_world_record_tick");
+    if (st != KNN_OK) return st;
+    if (!w.graphs) return fail(KNN_ERR_INVALID, "knn_world_record_tick: graphs are off");
+    cudaSetDevice(w.device);
+    knnq::TickGraph *g = nullptr;
+    bool recorded = false;
+    knn_status st2 = tick_graph(w, *args, &g, &recorded);
+    if (st2 != KNN_OK) return st2;
+    // move the graph to the device now rather than at its first launch
+    cudaError_t e = cudaGraphUpload(g->exec, w.capture_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(w.capture_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "knn_world_record_tick: upload");
+    return KNN_OK;
+}
+
+knn_status knn_world_set_graphs(knn_world h, int32_t enable) {
+    if (!h) return fail(KNN_ERR_INVALID, "knn_world_set_graphs: NULL world");
+    h->w.graphs = enable != 0;
     return KNN_OK;
 }
 

@@ -521,15 +521,29 @@ __global__ void __launch_bounds__(256) k_scan_excl(const int32_t *in, int32_t *o
     __syncthreads();
     const uint32_t tile = s_tile;
     const int64_t base = (int64_t)tile * kScanTile + tid * 8;
+    // 8 consecutive entries per thread, read as two 16-byte words when whole
+    // (the buffers are 256-byte aligned and base is a multiple of 8)
+    const bool whole = base + 8 <= len;
+    int32_t x[9];
+    if (whole) {
+        const int4 a = *reinterpret_cast<const int4 *>(in + base);
+        const int4 b = *reinterpret_cast<const int4 *>(in + base + 4);
+        x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+        x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+    } else {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) x[q] = base + q < len ? in[base + q] : 0;
+    }
+    x[8] = PACKETS && base + 8 < len ? in[base + 8] : 0;
     int32_t v[8];
     uint32_t sum = 0;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         const int64_t c = base + q;
         if (PACKETS)
-            v[q] = c + 1 < len ? (in[c + 1] - in[c] + 31) / 32 : 0;
+            v[q] = c + 1 < len ? (x[q + 1] - x[q] + 31) / 32 : 0;
         else
-            v[q] = c < len ? in[c] : 0;
+            v[q] = c < len ? x[q] : 0;
         sum += (uint32_t)v[q];
     }
     const uint32_t off = block_excl_scan_256(sum, s_tmp, &s_total);
@@ -539,10 +553,19 @@ __global__ void __launch_bounds__(256) k_scan_excl(const int32_t *in, int32_t *o
     }
     __syncthreads();
     uint32_t run = s_excl + off;
+    int32_t o[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-        if (base + q < len) out[base + q] = (int32_t)run;
+        o[q] = (int32_t)run;
         run += (uint32_t)v[q];
+    }
+    if (whole) {
+        *reinterpret_cast<int4 *>(out + base) = make_int4(o[0], o[1], o[2], o[3]);
+        *reinterpret_cast<int4 *>(out + base + 4) = make_int4(o[4], o[5], o[6], o[7]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (base + q < len) out[base + q] = o[q];
     }
     if ((int64_t)(tile + 1) * kScanTile >= len && tid == 255 && total) *total = (int32_t)run;
 }

@@ -14,7 +14,7 @@ constexpr int kMaxLeafCapacity = 4096;
 constexpr int kMaxStages = 12;
 constexpr int kNumCounters = 32;
 
-// Radix sort tile (onesweep): 256 threads x 16 keys.
+// Radix sort tile: 256 threads x 16 keys.
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;
 constexpr int kSortTile = kSortThreads * kSortItems;
@@ -38,6 +38,17 @@ struct Plan {
     int Gp;          // packet level
     int passes;      // radix passes over 2L bits
 };
+
+// A whole tick recorded as a CUDA graph, with what it was recorded for.
+struct TickGraph {
+    knn_tick_args args{};
+    Plan plan{};
+    bool marks = false;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t used = 0;      // recency stamp
+    int64_t launches = 0;   // kernels in the graph
+};
+constexpr int kTickGraphs = 16;
 
 struct World {
     int device = 0;
@@ -102,6 +113,13 @@ struct World {
     bool profiling = false;
     cudaEvent_t ev[kMaxStages + 1] = {};
     int n_stage_events = 0;
+
+    // knn_tick replays a recorded graph when its arguments, plan and profiling
+    // marks match one of the last kTickGraphs ticks (least recently used goes)
+    bool graphs = true;
+    TickGraph tick_graph[kTickGraphs];
+    uint64_t tick_clock = 0;
+    cudaStream_t capture_stream = nullptr;
 
     int64_t max_rows() const { return n > desc.max_queries ? n : desc.max_queries; }
 };

@@ -87,6 +87,8 @@ _SIGNATURES = {
     "knn_world_positions": ([_vp, _vp, _vp, _vp], ctypes.c_int),
     "knn_world_launches": ([_vp, ctypes.POINTER(_i64)], ctypes.c_int),
     "knn_world_set_profiling": ([_vp, _i32], ctypes.c_int),
+    "knn_world_set_graphs": ([_vp, _i32], ctypes.c_int),
+    "knn_world_record_tick": ([_vp, ctypes.POINTER(knn_tick_args)], ctypes.c_int),
     "knn_world_stage_times": ([_vp, ctypes.POINTER(ctypes.c_float), _i32], ctypes.c_int),
     "knn_stage_name": ([_i32], ctypes.c_char_p),
     "knn_batch_tick": ([_i32, ctypes.POINTER(_vp), ctypes.POINTER(knn_tick_args), _vp],
@@ -204,6 +206,14 @@ def knn_world_launches(w: int) -> int:
 
 def knn_world_set_profiling(w: int, enable: bool) -> None:
     _check(lib().knn_world_set_profiling(w, 1 if enable else 0))
+
+
+def knn_world_set_graphs(w: int, enable: bool) -> None:
+    _check(lib().knn_world_set_graphs(w, 1 if enable else 0))
+
+
+def knn_world_record_tick(w: int, args: knn_tick_args) -> None:
+    _check(lib().knn_world_record_tick(w, ctypes.byref(args)))
 
 
 def knn_world_stage_times(w: int, n: int = 16) -> list:
@@ -408,6 +418,15 @@ class World:
 
     def set_profiling(self, enable: bool = True):
         knn_world_set_profiling(self.handle, enable)
+
+    def set_graphs(self, enable: bool = True):
+        knn_world_set_graphs(self.handle, enable)
+
+    def record_tick(self, k: int, q_id=None, upd_id=None, upd_x=None, upd_y=None, q_x=None,
+                    q_y=None, out_ids=None, out_d2=None):
+        """Record (without running) the graph that tick() with these tensors replays."""
+        knn_world_record_tick(self.handle, tick_args(k, q_id, upd_id, upd_x, upd_y, q_x, q_y,
+                                                     out_ids, out_d2))
 
     def stage_times(self) -> dict:
         names = stage_names()

@@ -268,14 +268,62 @@ def test_checkpoint_resume_bit_identical():
         a.close()
 
 
-def test_stage_profiling_reports_every_stage():
-    w = synth.plain_uniform_moving(n=100000, k=16, ticks=1, seed=1)
+@pytest.mark.parametrize("graphs", [True, False])
+def test_stage_profiling_reports_every_stage(graphs):
+    w = synth.plain_uniform_moving(n=100000, k=16, ticks=2, seed=1)
     world = make_world(w.x0, w.y0, k_max=16)
     try:
+        world.set_graphs(graphs)
         world.set_profiling(True)
-        gpu_tick(world, w.ticks[0])
-        st = world.stage_times()
-        assert list(st) == knnq.stage_names()
-        assert all(v >= 0 for v in st.values()) and st["expand"] > 0
+        for t in w.ticks:
+            gpu_tick(world, t)
+            st = world.stage_times()
+            assert list(st) == knnq.stage_names()
+            assert all(v >= 0 for v in st.values()) and st["expand"] > 0
     finally:
         world.close()
+
+
+def test_tick_graph_replay_matches_direct_launches():
+    # three input sets cycled: from the fourth tick on, knn_tick replays the
+    # graphs it recorded; a second world launches every kernel directly
+    torch, _ = torch_dev()
+    w = synth.plain_uniform_moving(n=30011, k=16, ticks=3, seed=12)
+    dev_ticks = [[to_dev(a) for a in (t.q_id, t.upd_id, t.upd_x, t.upd_y)] for t in w.ticks]
+    n_q = w.ticks[0].q_id.shape[0]
+    outs = [[(torch.empty((n_q, 16), dtype=torch.int32, device="cuda"),
+              torch.empty((n_q, 16), dtype=torch.float32, device="cuda")) for _ in range(3)]
+            for _ in range(2)]  # same output buffers for the same input set
+    a = make_world(w.x0, w.y0, k_max=16)
+    b = make_world(w.x0, w.y0, k_max=16)
+    try:
+        b.set_graphs(False)
+        # sets 0 and 1 recorded up front (nothing runs); set 2 is recorded by its first tick
+        for j in range(2):
+            a.record_tick(16, *dev_ticks[j], out_ids=outs[0][j][0], out_d2=outs[0][j][1])
+        assert a.launches() == 0
+        x, y = w.x0.copy(), w.y0.copy()
+        for i in range(8):
+            t = w.ticks[i % 3]
+            if i == 5:  # profiling marks change the recording; the results do not
+                a.set_profiling(True)
+            oa, ob = outs[0][i % 3], outs[1][i % 3]
+            ids_a, d2_a = a.tick(16, *dev_ticks[i % 3], out_ids=oa[0], out_d2=oa[1])
+            ids_b, d2_b = b.tick(16, *dev_ticks[i % 3], out_ids=ob[0], out_d2=ob[1])
+            torch.cuda.synchronize()
+            x, y, _ = oracle.apply_updates(x, y, t.upd_id, t.upd_x, t.upd_y)
+            rows = sample_rows(t.q_id.shape[0], 2000, seed=i)
+            rid, rd2 = oracle_rows(x, y, t, rows)
+            ia, da = ids_a.cpu().numpy(), d2_a.cpu().numpy()
+            assert_rows_equal(ia, da, rid, rd2, rows, what=f"graph tick {i}")
+            assert np.array_equal(ia, ids_b.cpu().numpy())
+            assert np.array_equal(da.view(np.uint32), d2_b.cpu().numpy().view(np.uint32))
+        assert a.launches() == b.launches()
+        st = a.stage_times()
+        assert st["expand"] > 0 and all(v >= 0 for v in st.values())
+        for world in (a, b):
+            s, bits = world.status()
+            assert s == knnq.KNN_OK, (s, bits)
+    finally:
+        a.close()
+        b.close()
