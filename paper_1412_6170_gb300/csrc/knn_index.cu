@@ -164,7 +164,8 @@ __global__ void __launch_bounds__(256) k_query_keys_hist(
 
 // ---------------------------------------------------------------------------
 // a3 -- one stable LSD radix pass over 8 bits (onesweep: ranks within the tile
-// by warp multi-split, digit offsets across tiles by decoupled look-back).
+// by warp multi-split -- the lanes holding the same digit found by one ballot
+// per digit bit -- and digit offsets across tiles by decoupled look-back).
 
 __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     const uint32_t *__restrict__ kin, const int32_t *__restrict__ vin,
@@ -204,10 +205,15 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
         const bool valid = wbase + j * 32 + lane < n;
         const unsigned vm = __ballot_sync(kFull, valid);
         const uint32_t d = (k[j] >> shift) & 255u;
-        unsigned peers = 0;
+        // lanes holding the same digit: one ballot per digit bit
+        unsigned peers = vm;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const unsigned bb = __ballot_sync(kFull, (d >> b) & 1u);
+            peers &= ((d >> b) & 1u) ? bb : ~bb;
+        }
         uint32_t before = 0;
         if (valid) {
-            peers = __match_any_sync(vm, d);
             before = s_wcnt[warp][d];
             r[j] = before + __popc(peers & lt);
         }
