@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_expand(const ExpandArgs g) {
             const int n_here = staged_end - cur < kBatch ? staged_end - cur : kBatch;
             const float thr = L.thr;
             const int o0 = cur - staged;
-            for (int u = 0; u < n_here; ++u) {
+            auto test = [&](int u) {
                 const float4 o = sm.obj[o0 + u];
                 const float dx = __fsub_rn(qx, o.x);
                 const float dy = __fsub_rn(qy, o.y);
@@ -418,6 +418,12 @@ __global__ void __launch_bounds__(kWarps * 32) k_expand(const ExpandArgs g) {
                         ((unsigned long long)__float_as_uint(d) << 32) | (uint32_t)idp1;
                     ++L.count;
                 }
+            };
+            if (n_here == kBatch) {
+#pragma unroll
+                for (int u = 0; u < kBatch; ++u) test(u);
+            } else {
+                for (int u = 0; u < n_here; ++u) test(u);
             }
             cur += n_here;
         }
