@@ -164,6 +164,18 @@ __device__ __forceinline__ float box_lb(float x0, float y0, float x1, float y1, 
     return __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
 }
 
+// Ring of the level-G cells around a centre cell: ring 0 is the centre, ring
+// r >= 1 the 8r cells at Chebyshev distance r.  Taking the rings in order and
+// each ring in a fixed order numbers the cells: ring r >= 1 holds numbers
+// 1 + 4r(r-1) .. 4r(r+1).  ring_of inverts that.
+__device__ __forceinline__ int ring_of(int u) {
+    if (u <= 0) return 0;
+    int r = (int)(0.5f * (1.0f + sqrtf((float)u)));
+    while (1 + 4 * r * (r + 1) <= u) ++r;
+    while (r > 0 && 1 + 4 * r * (r - 1) > u) --r;
+    return r;
+}
+
 __device__ __forceinline__ int32_t key_id(unsigned long long key) {
     const uint32_t lo = (uint32_t)key;
     return lo == 0xFFFFFFFFu ? -1 : (int32_t)lo - 1;
@@ -257,11 +269,11 @@ __global__ void __launch_bounds__(kWarps * 32) k_expand(const ExpandArgs g) {
         int32_t staged, staged_end;           // objects held in sm.obj
         int phase;                            // 1: own leaves, 2: rings, 3: draining
         bool flushing = false;                // small lists: a full buffer drains them all
-        // phase-2 cursor: ring r, next ring position t; the lanes' cells and
-        // last gathered leaves sit in sm.lc / sm.lbb / sm.lrg (shared memory
-        // keeps them out of the registers the merges need); bit i of pend: lane
-        // i's gathered leaf still waits for its exact test
-        int r, t;
+        // phase-2 cursor: number u0 of the next ring cell (see ring_of); the
+        // lanes' cells and last gathered leaves sit in sm.lc / sm.lbb / sm.lrg
+        // (shared memory keeps them out of the registers the merges need); bit
+        // i of pend: lane i's gathered leaf still waits for its exact test
+        int u0;
         unsigned pend;
         float bx0 = 0.f, bx1 = 0.f, by0 = 0.f, by1 = 0.f;
         int ccx = 0, ccy = 0, cx0 = 0, cx1 = 0, cy0 = 0, cy1 = 0, rmax = 0;
@@ -287,8 +299,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_expand(const ExpandArgs g) {
         staged = -1;
         staged_end = -1;
         phase = 1;
-        r = 0;
-        t = 0;
+        u0 = 0;
         sm.lc[lane] = make_int2(0, 0);
         pend = 0u;
         for (;;) {
@@ -318,7 +329,6 @@ __global__ void __launch_bounds__(kWarps * 32) k_expand(const ExpandArgs g) {
                     by1 = warp_max(active ? qy : -kInf);
                     ccx = cell_g(0.5f * (bx0 + bx1), g.x0, g.scale_g, g.G);
                     ccy = cell_g(0.5f * (by0 + by1), g.y0, g.scale_g, g.G);
-                    bound();
                 }
                 bool found = false;
                 for (;;) {
@@ -359,24 +369,22 @@ __global__ void __launch_bounds__(kWarps * 32) k_expand(const ExpandArgs g) {
                         __syncwarp();
                         continue;
                     }
-                    const int per = r == 0 ? 1 : 8 * r;
-                    if (t >= per) {  // ring finished; the k-th distances only shrink
-                        ++r;
-                        t = 0;
-                        bound();
-                        if (r > rmax) break;
-                        continue;
-                    }
-                    // the next 32 positions of ring r, one per lane
-                    const int u = t + lane;
+                    // the next 32 ring cells, one per lane, inside the box that the
+                    // current thresholds allow (the k-th distances only shrink);
+                    // done once the next cell's ring lies outside it
+                    bound();
+                    if (ring_of(u0) > rmax) break;
+                    const int u = u0 + lane;
+                    const int r = ring_of(u);
                     lc = make_int2(0, 0);
-                    if (u < per) {
+                    if (r <= rmax) {
+                        const int t = r == 0 ? 0 : u - (1 + 4 * r * (r - 1));
                         int cx, cy;
                         if (r == 0) { cx = ccx; cy = ccy; }
-                        else if (u < 2 * r + 1) { cx = ccx - r + u; cy = ccy - r; }
-                        else if (u < 4 * r + 2) { cx = ccx - r + (u - 2 * r - 1); cy = ccy + r; }
-                        else if (u < 6 * r + 1) { cx = ccx - r; cy = ccy - r + 1 + (u - 4 * r - 2); }
-                        else { cx = ccx + r; cy = ccy - r + 1 + (u - 6 * r - 1); }
+                        else if (t < 2 * r + 1) { cx = ccx - r + t; cy = ccy - r; }
+                        else if (t < 4 * r + 2) { cx = ccx - r + (t - 2 * r - 1); cy = ccy + r; }
+                        else if (t < 6 * r + 1) { cx = ccx - r; cy = ccy - r + 1 + (t - 4 * r - 2); }
+                        else { cx = ccx + r; cy = ccy - r + 1 + (t - 6 * r - 1); }
                         if (cx >= cx0 && cx <= cx1 && cy >= cy0 && cy <= cy1) {
                             const uint32_t c = interleave((uint32_t)cx, (uint32_t)cy);
                             lc.x = g.cb[c];
@@ -386,7 +394,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_expand(const ExpandArgs g) {
                         }
                     }
                     sm.lc[lane] = lc;
-                    t += 32;
+                    u0 += 32;
                 }
                 if (!found) {
                     phase = 3;
