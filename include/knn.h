@@ -74,7 +74,7 @@ typedef struct {
     float x0, y0, side;      /* side > 0 and finite */
     int32_t leaf_capacity;   /* th_quad: max objects per leaf; 0 = automatic; <= 4096 */
     int32_t max_depth;       /* l_max in [1, 16]; 0 = 16 */
-    int32_t k_max;           /* largest k a tick may ask for, in [1, 64] */
+    int32_t k_max;           /* largest k a tick may ask for, in [1, 512] */
     int64_t max_queries;     /* largest n_q a tick may pass, >= 0 */
 } knn_world_desc;
 
@@ -213,12 +213,17 @@ const char *knn_last_error(void);
  *   4^g >= 4n) (a finer map never pays off); larger values are rejected.
  * packet_level: queries are packed 32 to a warp within one cell of this
  *   level (<= grid_level).
+ * expansion: the expansion kernel.  1 = packets of up to 32 queries per warp,
+ *   each lane keeping its query's list in registers (k <= 64); 2 = one warp
+ *   per query, the list in shared memory and the row written by the whole
+ *   warp (any k; the paper's coalesced-writes variant, Section 3.3.2).  The
+ *   automatic choice is 1 for k <= 64 and 2 above.
  * Any field set to 0 keeps (or restores) the automatic choice. */
 typedef struct {
     int32_t leaf_capacity;
     int32_t grid_level;
     int32_t packet_level;
-    int32_t reserved;
+    int32_t expansion;
 } knn_tuning;
 
 knn_status knn_world_set_tuning(knn_world w, const knn_tuning *t);
@@ -292,7 +297,7 @@ const char *knn_stage_name(int32_t i);
  * rows, bit for bit), but creates no world and allocates nothing: its scratch
  * is one static device array of 8 MiB that every GPU loading this library
  * holds until the process exits.  Limits: n in [1, 65536], n_q in [0, 65536],
- * k in [1, 64], cell-map level at most 8; larger sizes return
+ * k in [1, 512], cell-map level at most 8; larger sizes return
  * KNN_ERR_INVALID.  desc gives the domain, leaf_capacity and max_depth
  * (k_max and max_queries are ignored).  Positions are only read.
  *

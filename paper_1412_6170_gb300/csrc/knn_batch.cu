@@ -91,10 +91,10 @@ extern "C" knn_status knn_batch_tick(int32_t n_worlds, const knn_world *worlds,
 
     // Shape: the plan of every world (and whether updates run) fixes the graph's nodes.
     std::vector<int> shape;
-    shape.reserve(6 * n_worlds);
+    shape.reserve(7 * n_worlds);
     for (int32_t i = 0; i < n_worlds; ++i) {
         const knnq::Plan p = knnq::plan_for(worlds[i]->w, args[i].n_q, args[i].k);
-        shape.insert(shape.end(), {p.th, p.G, p.Gp, args[i].n_upd > 0,
+        shape.insert(shape.end(), {p.th, p.G, p.Gp, (int)p.wide, args[i].n_upd > 0,
                                    args[i].q_x_dev != nullptr, args[i].n_q > 0});
     }
     bool reuse = g.exec && (int32_t)g.worlds.size() == n_worlds && g.shape == shape;

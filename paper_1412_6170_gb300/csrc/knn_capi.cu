@@ -56,6 +56,7 @@ Plan make_plan(const World &w, int64_t n_q, int k) {
     int Gp = w.tuning.packet_level > 0 ? w.tuning.packet_level
                                        : round_log4((double)(n_q > 0 ? n_q : 1) / 48.0);
     p.Gp = clampi(Gp, 0, p.G);
+    p.wide = w.tuning.expansion == 2 || (w.tuning.expansion != 1 && k > knnq::kMaxPacketK);
     return p;
 }
 
@@ -153,7 +154,7 @@ knn_status world_init_resident(World &w, const knn_world_desc *desc, const float
     if (n < 1 || n > (1ll << 30))
         return fail(KNN_ERR_INVALID, "world: n=%lld outside [1, 2^30]", (long long)n);
     if (desc->k_max < 1 || desc->k_max > kMaxK)
-        return fail(KNN_ERR_INVALID, "world: k_max=%d outside [1, 64]", desc->k_max);
+        return fail(KNN_ERR_INVALID, "world: k_max=%d outside [1, %d]", desc->k_max, kMaxK);
     if (desc->max_depth < 0 || desc->max_depth > 16)
         return fail(KNN_ERR_INVALID, "world: max_depth=%d outside [0, 16]", desc->max_depth);
     if (desc->leaf_capacity < 0 || desc->leaf_capacity > kMaxLeafCapacity)
@@ -370,9 +371,14 @@ void enqueue_tick(World &w, const knn_tick_args &a, cudaStream_t s, bool marks) 
                                     a.out_ids_dev, a.out_d2_dev, s);
     }
     if (m) mark(w, 4, s);
-    if (a.n_q > 0) launch_packets(w, p, a.n_q, s);
+    if (a.n_q > 0 && !p.wide) launch_packets(w, p, a.n_q, s);
     if (m) mark(w, 5, s);
-    if (a.n_q > 0) launch_expand(w, p, a.k, a.n_q, a.out_ids_dev, a.out_d2_dev, s);
+    if (a.n_q > 0) {
+        if (p.wide)
+            launch_expand_wide(w, p, a.k, a.n_q, a.out_ids_dev, a.out_d2_dev, s);
+        else
+            launch_expand(w, p, a.k, a.n_q, a.out_ids_dev, a.out_d2_dev, s);
+    }
     if (m) mark(w, 6, s);
     w.last_stream = s;
     w.last_plan = p;
@@ -443,6 +449,8 @@ knn_status knn_world_set_tuning(knn_world h, const knn_tuning *t) {
         return fail(KNN_ERR_INVALID, "grid_level outside [0, %d] for this world", h->w.gmax);
     if (t->packet_level < 0 || t->packet_level > knnq::kMaxGridLevel)
         return fail(KNN_ERR_INVALID, "packet_level outside [0, 10]");
+    if (t->expansion < 0 || t->expansion > 2)
+        return fail(KNN_ERR_INVALID, "expansion outside [0, 2]");
     h->w.tuning = *t;
     return KNN_OK;
 }
@@ -453,7 +461,7 @@ knn_status knn_world_get_tuning(knn_world h, int64_t n_q, int32_t k, knn_tuning 
     out->leaf_capacity = p.th;
     out->grid_level = p.G;
     out->packet_level = p.Gp;
-    out->reserved = 0;
+    out->expansion = p.wide ? 2 : 1;
     return KNN_OK;
 }
 

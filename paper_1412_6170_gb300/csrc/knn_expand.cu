@@ -45,10 +45,6 @@ struct ExpandArgs {
     int64_t n, n_q, pk_cap;
 };
 
-// key = (float bits of d^2) << 32 | (id + 1): for d >= 0 the unsigned order of
-// keys is the lexicographic (d^2, id) order.  kPad (+inf, 0xFFFFFFFF) is above
-// every real key and marks an empty slot; 0 is below every real key.
-constexpr unsigned long long kPad = 0x7f800000FFFFFFFFull;
 
 // Per-lane candidate buffer (shared memory, kBufCap slots per lane, a stack):
 // candidates whose d^2 is within the lane's current threshold are pushed
@@ -126,60 +122,10 @@ __device__ __forceinline__ void merge_top(Lane<KC> &L, WarpSmem &sm, int lane) {
 }
 
 
-__device__ __forceinline__ int cell_g(float v, float v0, float scale, int G) {
-    const float t = __fmul_rn(__fsub_rn(v, v0), scale);
-    const int lim = 1 << G;
-    if (!(t >= 0.0f)) return 0;
-    if (t >= (float)lim) return lim - 1;
-    return (int)t;
-}
 
-__device__ __forceinline__ float warp_max(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
-    return v;
-}
-__device__ __forceinline__ float warp_min(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(kFull, v, o));
-    return v;
-}
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    return v;
-}
 
-// Squared distance from (x, y) up to a box [x0, x1] x [y0, y1]: a lower bound
-// of the squared distance to every point of the box, in the same rounding as
-// the exact distances (round-to-nearest is monotone, so a point farther out
-// never gets a smaller bound).
-__device__ __forceinline__ float box_lb(float x0, float y0, float x1, float y1, float qx0,
-                                        float qy0, float qx1, float qy1) {
-    float dx = 0.f, dy = 0.f;
-    if (qx1 < x0) dx = __fsub_rn(x0, qx1);
-    else if (qx0 > x1) dx = __fsub_rn(qx0, x1);
-    if (qy1 < y0) dy = __fsub_rn(y0, qy1);
-    else if (qy0 > y1) dy = __fsub_rn(qy0, y1);
-    return __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
-}
 
-// Ring of the level-G cells around a centre cell: ring 0 is the centre, ring
-// r >= 1 the 8r cells at Chebyshev distance r.  Taking the rings in order and
-// each ring in a fixed order numbers the cells: ring r >= 1 holds numbers
-// 1 + 4r(r-1) .. 4r(r+1).  ring_of inverts that.
-__device__ __forceinline__ int ring_of(int u) {
-    if (u <= 0) return 0;
-    int r = (int)(0.5f * (1.0f + sqrtf((float)u)));
-    while (1 + 4 * r * (r + 1) <= u) ++r;
-    while (r > 0 && 1 + 4 * r * (r - 1) > u) --r;
-    return r;
-}
 
-__device__ __forceinline__ int32_t key_id(unsigned long long key) {
-    const uint32_t lo = (uint32_t)key;
-    return lo == 0xFFFFFFFFu ? -1 : (int32_t)lo - 1;
-}
 
 // One packet = one pass of a single loop.  Each iteration (a) merges a batch
 // of the buffers if some lane holds kFlushAt candidates, (b) finds the next objects
@@ -378,13 +324,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_expand(const ExpandArgs g) {
                     const int r = ring_of(u);
                     lc = make_int2(0, 0);
                     if (r <= rmax) {
-                        const int t = r == 0 ? 0 : u - (1 + 4 * r * (r - 1));
                         int cx, cy;
-                        if (r == 0) { cx = ccx; cy = ccy; }
-                        else if (t < 2 * r + 1) { cx = ccx - r + t; cy = ccy - r; }
-                        else if (t < 4 * r + 2) { cx = ccx - r + (t - 2 * r - 1); cy = ccy + r; }
-                        else if (t < 6 * r + 1) { cx = ccx - r; cy = ccy - r + 1 + (t - 4 * r - 2); }
-                        else { cx = ccx + r; cy = ccy - r + 1 + (t - 6 * r - 1); }
+                        ring_cell(u, r, ccx, ccy, cx, cy);
                         if (cx >= cx0 && cx <= cx1 && cy >= cy0 && cy <= cy1) {
                             const uint32_t c = interleave((uint32_t)cx, (uint32_t)cy);
                             lc.x = g.cb[c];

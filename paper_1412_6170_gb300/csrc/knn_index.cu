@@ -789,6 +789,7 @@ void prepare_kernels() {
                          (int)leaves_smem(kMaxLeafCapacity));
     num_sms(dev);          // fill the per-device caches now: the query APIs
     prepare_expand(dev);   // must not run while a batch is being recorded
+    prepare_expand_wide(dev);
     done[dev] = true;
 }
 

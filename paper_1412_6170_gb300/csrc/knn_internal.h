@@ -8,7 +8,8 @@
 
 namespace knnq {
 
-constexpr int kMaxK = 64;
+constexpr int kMaxK = 512;        // largest k of any tick
+constexpr int kMaxPacketK = 64;   // largest k of the packet expansion kernel
 constexpr int kMaxGridLevel = 10;
 constexpr int kMaxLeafCapacity = 4096;
 constexpr int kMaxStages = 12;
@@ -37,6 +38,7 @@ struct Plan {
     int G;           // cell-map level (min leaf level)
     int Gp;          // packet level
     int passes;      // radix passes over 2L bits
+    bool wide;       // expansion by one warp per query (else packets)
 };
 
 // A whole tick recorded as a CUDA graph, with what it was recorded for.
@@ -161,12 +163,15 @@ void launch_export_leaves(World &w, int64_t m, int32_t *level, uint32_t *z, int3
 // ---- launcher (knn_expand.cu) -----------------------------------------------
 void launch_expand(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t *out_ids,
                    float *out_d2, cudaStream_t s);
+void launch_expand_wide(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t *out_ids,
+                        float *out_d2, cudaStream_t s);
 
 int num_sms(int device);
 // One-time kernel attributes and cached device queries (called outside any
 // stream capture).
 void prepare_kernels();
 void prepare_expand(int device);
+void prepare_expand_wide(int device);
 
 // Device memory layout of a world (knn_capi.cu).  base == nullptr only sizes.
 size_t carve_resident(World &w, char *base);

@@ -132,7 +132,7 @@ extern "C" knn_status knn_query_static(const knn_world_desc *desc, const float *
         return bad(KNN_ERR_INVALID, "n outside [1, 65536] (the static scratch limit)");
     if (n_q < 0 || n_q > kStaticMaxQ)
         return bad(KNN_ERR_INVALID, "n_q outside [0, 65536] (the static scratch limit)");
-    if (k < 1 || k > knnq::kMaxK) return bad(KNN_ERR_INVALID, "k outside [1, 64]");
+    if (k < 1 || k > knnq::kMaxK) return bad(KNN_ERR_INVALID, "k outside [1, 512]");
     if (!x_dev || !y_dev) return bad(KNN_ERR_INVALID, "NULL positions");
     if ((q_x_dev == nullptr) != (q_y_dev == nullptr))
         return bad(KNN_ERR_INVALID, "q_x and q_y must both be given or both NULL");

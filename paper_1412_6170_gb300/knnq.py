@@ -47,7 +47,7 @@ class knn_world_desc(ctypes.Structure):
 
 class knn_tuning(ctypes.Structure):
     _fields_ = [("leaf_capacity", ctypes.c_int32), ("grid_level", ctypes.c_int32),
-                ("packet_level", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("packet_level", ctypes.c_int32), ("expansion", ctypes.c_int32)]
 
 
 _vp = ctypes.c_void_p
@@ -174,8 +174,9 @@ def knn_world_destroy(w: int) -> None:
     _check(lib().knn_world_destroy(w))
 
 
-def knn_world_set_tuning(w: int, leaf_capacity=0, grid_level=0, packet_level=0) -> None:
-    t = knn_tuning(leaf_capacity, grid_level, packet_level, 0)
+def knn_world_set_tuning(w: int, leaf_capacity=0, grid_level=0, packet_level=0,
+                         expansion=0) -> None:
+    t = knn_tuning(leaf_capacity, grid_level, packet_level, expansion)
     _check(lib().knn_world_set_tuning(w, ctypes.byref(t)))
 
 
@@ -183,7 +184,7 @@ def knn_world_get_tuning(w: int, n_q: int, k: int) -> dict:
     t = knn_tuning()
     _check(lib().knn_world_get_tuning(w, n_q, k, ctypes.byref(t)))
     return {"leaf_capacity": t.leaf_capacity, "grid_level": t.grid_level,
-            "packet_level": t.packet_level}
+            "packet_level": t.packet_level, "expansion": t.expansion}
 
 
 def knn_world_leaves(w: int, level, z, start, count, sorted_ids, cap: int,
@@ -252,7 +253,7 @@ def knn_world_autotune(w: int, q_id, q_x, q_y, n_q: int, k: int, out_ids, out_d2
     _check(lib().knn_world_autotune(w, q_id, q_x, q_y, n_q, k, out_ids, out_d2, trials,
                                     ctypes.byref(t), stream))
     return {"leaf_capacity": t.leaf_capacity, "grid_level": t.grid_level,
-            "packet_level": t.packet_level}
+            "packet_level": t.packet_level, "expansion": t.expansion}
 
 
 def tick_args(k: int, q_id=None, upd_id=None, upd_x=None, upd_y=None, q_x=None, q_y=None,
@@ -378,8 +379,8 @@ class World:
     def status(self):
         return knn_tick_status(self.handle)
 
-    def set_tuning(self, leaf_capacity=0, grid_level=0, packet_level=0):
-        knn_world_set_tuning(self.handle, leaf_capacity, grid_level, packet_level)
+    def set_tuning(self, leaf_capacity=0, grid_level=0, packet_level=0, expansion=0):
+        knn_world_set_tuning(self.handle, leaf_capacity, grid_level, packet_level, expansion)
 
     def get_tuning(self, n_q: int, k: int) -> dict:
         return knn_world_get_tuning(self.handle, n_q, k)

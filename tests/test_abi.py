@@ -35,7 +35,7 @@ def desc(**kw):
 
 
 @pytest.mark.parametrize("kw,n", [({"side": 0.0}, 10), ({"side": float("nan")}, 10),
-                                  ({"k_max": 0}, 10), ({"k_max": 65}, 10),
+                                  ({"k_max": 0}, 10), ({"k_max": 513}, 10),
                                   ({"max_depth": 17}, 10), ({"leaf_capacity": 5000}, 10),
                                   ({"max_queries": -1}, 10), ({}, 0), ({}, 2 ** 30 + 1)])
 def test_create_rejects_bad_description(lib, kw, n):

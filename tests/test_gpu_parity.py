@@ -60,6 +60,36 @@ def test_clustered_subset_queries_full(k):
     run_and_compare(w, what=f"60k clustered k={k}")
 
 
+# -------------------------------------------------------------------------
+# Large k: one warp per query, the list in shared memory (k > 64)
+
+
+@pytest.mark.parametrize("k", [65, 100, 256, 512])
+def test_large_k_uniform_ragged_full(k):
+    w = synth.plain_uniform_moving(n=30011, k=k, ticks=2, seed=21)
+    run_and_compare(w, k_max=512, what=f"30011 uniform k={k}")
+
+
+@pytest.mark.parametrize("k", [128, 500])
+def test_large_k_clustered_subset_sampled(k):
+    w = synth.skewed_moving(n=120000, k=k, ticks=2, seed=22)
+    run_and_compare(w, k_max=512, sample=3000, what=f"120k clustered k={k}")
+
+
+@pytest.mark.parametrize("expansion", [1, 2])
+@pytest.mark.parametrize("k", [1, 16, 64])
+def test_expansion_kernels_agree(k, expansion):
+    w = synth.skewed_moving(n=40000, k=k, ticks=2, seed=23, query_frac=0.5)
+    run_and_compare(w, tuning=dict(expansion=expansion), what=f"k={k} expansion {expansion}")
+
+
+def test_large_k_1m_uniform_sampled():
+    w = synth.plain_uniform_moving(n=1_000_000, k=512, ticks=1, seed=24)
+    w.ticks[0] = synth.Tick(w.ticks[0].upd_id, w.ticks[0].upd_x, w.ticks[0].upd_y,
+                            synth.random_subset(1_000_000, 50_000, seed=25, tick=0), 512)
+    run_and_compare(w, k_max=512, sample=1500, what="1M uniform k=512")
+
+
 def test_uniform_1m_k16_full_size_sampled():
     w = synth.plain_uniform_moving(n=1_000_000, k=16, ticks=2, seed=0)
     run_and_compare(w, k_max=16, sample=20000, what="1M uniform k=16")
@@ -77,7 +107,9 @@ def test_clustered_4m_k32_full_size_sampled():
 @pytest.mark.parametrize("tuning", [dict(leaf_capacity=1), dict(leaf_capacity=3, grid_level=2),
                                     dict(leaf_capacity=200, grid_level=4, packet_level=1),
                                     dict(leaf_capacity=4096, grid_level=1, packet_level=0),
-                                    dict(leaf_capacity=16, grid_level=9, packet_level=9)])
+                                    dict(leaf_capacity=16, grid_level=9, packet_level=9),
+                                    dict(expansion=2), dict(expansion=2, leaf_capacity=3),
+                                    dict(expansion=1, leaf_capacity=300, grid_level=3)])
 def test_tuning_invariance(tuning):
     w = synth.skewed_moving(n=20000, k=16, ticks=1, seed=11, query_frac=0.5)
     run_and_compare(w, tuning=tuning, what=f"tuning {tuning}")
@@ -126,11 +158,12 @@ def test_single_object_pads():
     compare_ticks([0.5], [0.5], [tick([0], 3)])
 
 
-@pytest.mark.parametrize("n,k", [(2, 1), (2, 5), (5, 4), (5, 5), (7, 64)])
+@pytest.mark.parametrize("n,k", [(2, 1), (2, 5), (5, 4), (5, 5), (7, 64), (7, 65), (300, 512),
+                                 (513, 512)])
 def test_fewer_objects_than_k(n, k):
     r = np.random.default_rng(n * 100 + k)
     x, y = r.random(n).astype(np.float32), r.random(n).astype(np.float32)
-    compare_ticks(x, y, [tick(np.arange(n), k)])
+    compare_ticks(x, y, [tick(np.arange(n), k)], k_max=max(64, k))
 
 
 def test_all_coincident_objects():
