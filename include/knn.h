@@ -217,7 +217,7 @@ const char *knn_last_error(void);
  *   each lane keeping its query's list in registers (k <= 64); 2 = one warp
  *   per query, the list in shared memory and the row written by the whole
  *   warp (any k; the paper's coalesced-writes variant, Section 3.3.2).  The
- *   automatic choice is 1 for k <= 64 and 2 above.
+ *   automatic choice is 1 for k <= 32 and 2 above.
  * Any field set to 0 keeps (or restores) the automatic choice. */
 typedef struct {
     int32_t leaf_capacity;
@@ -259,6 +259,24 @@ knn_status knn_world_positions(knn_world w, float *x_dev, float *y_dev, void *st
 /* Number of CUDA kernels this world's ticks have launched so far (host-side
  * count; memsets and copies are not kernels and are not counted). */
 knn_status knn_world_launches(knn_world w, int64_t *count);
+
+/* Index reuse (Section 4, the processing pipeline: the index is rebuilt only
+ * when needed).  With max_age > 0 a tick keeps the previous tick's leaves and
+ * only puts every object into a leaf of its level-G cell (a counting sort by
+ * leaf instead of the radix sort and the leaf split).  The leaves are rebuilt
+ * instead when max_age ticks have passed since the tick that built them, when
+ * their cost -- the sum over leaves of the squared object count -- grew past
+ * `factor` times its value right after that build (factor <= 0: no such
+ * test), when the plan changed, or when an object entered a level-G cell
+ * without leaves; the decision is taken on the device, tick by tick.  Results
+ * are identical either way; only the time changes.  max_age = 0 (the
+ * default) rebuilds every tick. */
+knn_status knn_world_set_index_reuse(knn_world w, int32_t max_age, float factor);
+
+/* Index reuse state after the last tick (synchronizes the world's last stream):
+ * *age = ticks since the tick that built the leaves (0: the last tick built
+ * them), *rebuilt = 1 when the last tick built them.  Either may be NULL. */
+knn_status knn_world_index_info(knn_world w, int32_t *age, int32_t *rebuilt);
 
 /* Tick graphs.  knn_tick records a tick as a CUDA graph and replays it when a
  * later tick passes the same arguments (pointers and sizes), tuning and

@@ -56,7 +56,12 @@ Plan make_plan(const World &w, int64_t n_q, int k) {
     int Gp = w.tuning.packet_level > 0 ? w.tuning.packet_level
                                        : round_log4((double)(n_q > 0 ? n_q : 1) / 48.0);
     p.Gp = clampi(Gp, 0, p.G);
-    p.wide = w.tuning.expansion == 2 || (w.tuning.expansion != 1 && k > knnq::kMaxPacketK);
+    // one warp per query pays off above k = 32 (measured on 1M uniform objects:
+    // k = 64 takes 2.8 ms that way against 3.5 ms in packets)
+    p.wide = w.tuning.expansion == 2 || (w.tuning.expansion != 1 && k > 32) ||
+             k > knnq::kMaxPacketK;
+    p.reuse_age = w.reuse_age;
+    p.reuse_f16 = w.reuse_factor > 0.f ? (int)std::lround(w.reuse_factor * 16.f) : 0;
     return p;
 }
 
@@ -96,11 +101,15 @@ size_t carve_scratch(World &w, char *base) {
     const int64_t ncell = (1ll << (2 * w.gmax)) + 2;
     const int64_t sort_tiles = (R + kSortTile - 1) / kSortTile;
     int64_t status = sort_tiles * 256;
+    // leaves: at most one per object, plus (index reuse) one per empty level-G cell
+    const int64_t lcap = n + (1ll << (2 * w.gmax)) + 1;
     const int64_t others[] = {(n + kLeafTile - 1) / kLeafTile,
                               (n + 1 + kScanTile - 1) / kScanTile,
-                              (ncell + kScanTile - 1) / kScanTile};
+                              (ncell + kScanTile - 1) / kScanTile,
+                              (lcap + 1 + kScanTile - 1) / kScanTile};
     for (int64_t o : others) status = status > o ? status : o;
     Carve c{base};
+    w.leaf_cap = lcap;
     w.key[0] = c.take<uint32_t>(R);
     w.key[1] = c.take<uint32_t>(R);
     w.val[0] = c.take<int32_t>(R);
@@ -109,11 +118,12 @@ size_t carve_scratch(World &w, char *base) {
     w.ys = c.take<float>(n);
     w.sid = c.take<int32_t>(n);
     w.inv = c.take<int32_t>(n);
-    w.bstart = c.take<int32_t>(n + 1);
-    w.bcode = c.take<uint32_t>(n);
-    w.blevel = c.take<uint8_t>(n);
-    w.baabb = c.take<float4>(n);
-    w.brange = c.take<int2>(n);
+    w.bstart = c.take<int32_t>(lcap + 1);
+    w.bcode = c.take<uint32_t>(lcap);
+    w.blevel = c.take<uint8_t>(lcap);
+    w.baabb = c.take<float4>(lcap);
+    w.brange = c.take<int2>(lcap);
+    w.lcnt = c.take<int32_t>(lcap + 1);
     w.obj_leaf = c.take<int32_t>(n);
     w.cb = c.take<int32_t>(ncell);
     w.qcnt = c.take<int32_t>(n + 1);
@@ -354,10 +364,11 @@ knn_status check_tick_args(const World &w, const knn_tick_args &a, const char *w
 void enqueue_tick(World &w, const knn_tick_args &a, cudaStream_t s, bool marks) {
     const Plan p = make_plan(w, a.n_q, a.k);
     const bool m = marks && w.profiling;
-    launch_tick_begin(w, s);
+    launch_tick_begin(w, p, s);
     if (m) mark(w, 0, s);
     launch_updates(w, a.upd_id_dev, a.upd_x_dev, a.upd_y_dev, a.n_upd, s);
     if (m) mark(w, 1, s);
+    if (p.reuse_age > 0) launch_index_reuse(w, p, s);  // on reuse ticks; else the sort runs
     launch_object_sort(w, p, s);
     if (m) mark(w, 2, s);
     launch_leaves(w, p, s);
@@ -643,6 +654,30 @@ knn_status knn_world_record_tick(knn_world h, const knn_tick_args *args) {
     cudaError_t e = cudaGraphUpload(g->exec, w.capture_stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(w.capture_stream);
     if (e != cudaSuccess) return cuda_fail(e, "knn_world_record_tick: upload");
+    return KNN_OK;
+}
+
+knn_status knn_world_set_index_reuse(knn_world h, int32_t max_age, float factor) {
+    if (!h) return fail(KNN_ERR_INVALID, "knn_world_set_index_reuse: NULL world");
+    if (max_age < 0 || !std::isfinite(factor) || factor > 1e6f)
+        return fail(KNN_ERR_INVALID, "knn_world_set_index_reuse: bad max_age or factor");
+    h->w.reuse_age = max_age;
+    h->w.reuse_factor = factor > 0.f ? factor : 0.f;
+    return KNN_OK;
+}
+
+knn_status knn_world_index_info(knn_world h, int32_t *age, int32_t *rebuilt) {
+    if (!h) return fail(KNN_ERR_INVALID, "knn_world_index_info: NULL world");
+    World &w = h->w;
+    if (!w.arena) return fail(KNN_ERR_INVALID, "knn_world_index_info: world scratch released");
+    cudaSetDevice(w.device);
+    int32_t v[knnq::kNumScalars];
+    cudaError_t e = cudaMemcpyAsync(v, w.scalars, sizeof(v), cudaMemcpyDeviceToHost,
+                                    w.last_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(w.last_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "knn_world_index_info");
+    if (age) *age = v[knnq::kScalarRebuild] ? 0 : v[knnq::kScalarIndexAge];
+    if (rebuilt) *rebuilt = v[knnq::kScalarRebuild];
     return KNN_OK;
 }
 

@@ -43,6 +43,7 @@ struct ExpandArgs {
     int L, G, k;
     int vec_out;  // rows may be written with 16-byte stores
     int64_t n, n_q, pk_cap;
+    int64_t leaf_cap;  // room for leaves (m <= leaf_cap)
 };
 
 
@@ -148,7 +149,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_expand(const ExpandArgs g) {
     int32_t P = g.scalars[kScalarPackets];
     P = P < 0 ? 0 : (P > g.pk_cap ? (int32_t)g.pk_cap : P);
     int32_t m = g.scalars[kScalarLeaves];
-    m = m < 0 ? 0 : (m > g.n ? (int32_t)g.n : m);
+    m = m < 0 ? 0 : (m > g.leaf_cap ? (int32_t)g.leaf_cap : m);
     const int k = g.k;
     const float kInf = __int_as_float(0x7f800000);
     const int lim = (1 << g.G) - 1;
@@ -522,6 +523,7 @@ void launch_expand(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t *out
     a.G = p.G;
     a.k = k;
     a.n = w.n;
+    a.leaf_cap = w.leaf_cap;
     a.n_q = n_q;
     a.pk_cap = packet_capacity(w);
     a.vec_out = k % 4 == 0 && ((reinterpret_cast<uintptr_t>(out_ids) |

@@ -40,6 +40,7 @@ struct WideArgs {
     float spec2;  // alpha^2 of the speculative first threshold (0: none)
     int G, k;
     int64_t n, n_q;
+    int64_t leaf_cap;  // room for leaves (m <= leaf_cap)
 };
 
 constexpr int kWideWarps = 4;  // warps per block
@@ -80,7 +81,7 @@ __global__ void __launch_bounds__(kWideWarps * 32) k_expand_wide(const WideArgs 
     int32_t nv = g.scalars[kScalarValidQueries];
     nv = nv < 0 ? 0 : (nv > g.n_q ? (int32_t)g.n_q : nv);
     int32_t m = g.scalars[kScalarLeaves];
-    m = m < 0 ? 0 : (m > g.n ? (int32_t)g.n : m);
+    m = m < 0 ? 0 : (m > g.leaf_cap ? (int32_t)g.leaf_cap : m);
     const int k = g.k;
     const float kInf = __int_as_float(0x7f800000);
     const int lim = (1 << g.G) - 1;
@@ -280,6 +281,7 @@ void launch_expand_wide(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t
     a.G = p.G;
     a.k = k;
     a.n = w.n;
+    a.leaf_cap = w.leaf_cap;
     a.n_q = n_q;
     if (k <= 64) run_wide<64>(a, w.device, s);
     else if (k <= 128) run_wide<128>(a, w.device, s);

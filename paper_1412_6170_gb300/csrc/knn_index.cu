@@ -37,20 +37,51 @@ void launch_validate_positions(const float *x, const float *y, int64_t n, uint32
 // batch wins.  Pass 1 stamps each object with the largest (tick, index) of a
 // valid entry; pass 2 lets only that entry write.
 
+// Index reuse (Section 4 pipeline): the index (the leaves) is rebuilt only
+// when needed -- when the last tick's cost grew past a factor of the cost
+// right after the last build, after reuse_age ticks at the most, when the
+// plan changed, or (decided later in the tick) when an object moved into a
+// level-G cell without leaves.  The cost proxy is the sum over leaves of the
+// squared object count (candidate pairs).  The decision is taken here, on
+// the device, so a recorded tick graph needs no host round trip.
 __global__ void k_tick_begin(uint32_t *tickinfo, uint32_t *counters, int n_counters,
-                             uint32_t *err) {
+                             uint32_t *err, int32_t *scalars, int reuse_age, int reuse_f16,
+                             int32_t sig) {
     const int i = threadIdx.x;
     if (i == 0) {
         tickinfo[0] += 64u;  // room for 64 look-back launches per tick
         tickinfo[1] += 1u;
         err[2] = 0u;
+        unsigned long long *cost_base =
+            reinterpret_cast<unsigned long long *>(scalars + kScalarCostBase);
+        unsigned long long *cost_now =
+            reinterpret_cast<unsigned long long *>(scalars + kScalarCostNow);
+        if (scalars[kScalarRebuild]) {  // the last tick built the leaves
+            *cost_base = *cost_now;
+            scalars[kScalarIndexAge] = 0;
+        }
+        const int age = scalars[kScalarIndexAge] + 1;
+        const bool rebuild = reuse_age <= 0 || scalars[kScalarIndexSig] != sig ||
+                             age > reuse_age ||
+                             (reuse_f16 > 0 &&
+                              *cost_now * 16ull > (unsigned long long)reuse_f16 * *cost_base);
+        scalars[kScalarRebuild] = rebuild ? 1 : 0;
+        scalars[kScalarIndexAge] = age;
+        *cost_now = 0ull;
     }
     if (i < n_counters) counters[i] = 0u;
 }
 
-void launch_tick_begin(World &w, cudaStream_t s) {
+static int32_t index_signature(const Plan &p) {
+    return (int32_t)(0x40000000u | ((uint32_t)p.L << 24) | ((uint32_t)p.G << 16) |
+                     (uint32_t)p.th);
+}
+
+void launch_tick_begin(World &w, const Plan &p, cudaStream_t s) {
     w.site = 0;
-    k_tick_begin<<<1, kNumCounters, 0, s>>>(w.tickinfo, w.counters, kNumCounters, w.err);
+    k_tick_begin<<<1, kNumCounters, 0, s>>>(w.tickinfo, w.counters, kNumCounters, w.err,
+                                            w.scalars, p.reuse_age, p.reuse_f16,
+                                            index_signature(p));
     ++w.launches;
 }
 
@@ -105,7 +136,8 @@ void launch_updates(World &w, const int32_t *id, const float *ux, const float *u
 __global__ void __launch_bounds__(256) k_keys_hist(
     const float *__restrict__ px, const float *__restrict__ py, int64_t n, float x0, float y0,
     float scale, int L, int passes, uint32_t *__restrict__ key, int32_t *__restrict__ val,
-    uint32_t *hist) {
+    uint32_t *hist, const int32_t *rebuild) {
+    if (rebuild && *rebuild == 0) return;  // this tick reuses the leaves
     __shared__ uint32_t h[4][256];
     for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) (&h[0][0])[i] = 0;
     __syncthreads();
@@ -171,7 +203,8 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     const uint32_t *__restrict__ kin, const int32_t *__restrict__ vin,
     uint32_t *__restrict__ kout, int32_t *__restrict__ vout, int64_t n, int shift,
     const uint32_t *__restrict__ hist, uint64_t *status, uint32_t *ticket,
-    const uint32_t *__restrict__ tickinfo, uint32_t site, uint32_t *err) {
+    const uint32_t *__restrict__ tickinfo, uint32_t site, uint32_t *err, const int32_t *rebuild) {
+    if (rebuild && *rebuild == 0) return;  // this tick reuses the leaves
     __shared__ uint32_t s_wcnt[8][256];
     __shared__ uint32_t s_texcl[256];
     __shared__ uint32_t s_gbase[256];
@@ -263,7 +296,8 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
 }
 
 // Sort (key[0], val[0]) of n entries; the result lands in buffer (passes & 1).
-static void radix_sort(World &w, int64_t n, int passes, int counter_base, cudaStream_t s) {
+static void radix_sort(World &w, int64_t n, int passes, int counter_base, cudaStream_t s,
+                       const int32_t *rebuild = nullptr) {
     if (n <= 0) return;
     const int tiles = (int)((n + kSortTile - 1) / kSortTile);
     for (int p = 0; p < passes; ++p) {
@@ -271,18 +305,20 @@ static void radix_sort(World &w, int64_t n, int passes, int counter_base, cudaSt
         k_onesweep<<<tiles, kSortThreads, 0, s>>>(w.key[src], w.val[src], w.key[dst],
                                                    w.val[dst], n, 8 * p, w.hist + 256 * p,
                                                    w.status, w.counters + counter_base + p,
-                                                   w.tickinfo, w.site++, w.err);
+                                                   w.tickinfo, w.site++, w.err, rebuild);
         ++w.launches;
     }
 }
 
 void launch_object_sort(World &w, const Plan &p, cudaStream_t s) {
+    // with index reuse on, the sort and the leaf split run only on rebuild ticks
+    const int32_t *rebuild = p.reuse_age > 0 ? w.scalars + kScalarRebuild : nullptr;
     cudaMemsetAsync(w.hist, 0, sizeof(uint32_t) * 4 * 256, s);
     k_keys_hist<<<grid_for(w.n, 256, num_sms(w.device) * 4), 256, 0, s>>>(
         w.px, w.py, w.n, w.desc.x0, w.desc.y0, w.scale, p.L, p.passes, w.key[0], w.val[0],
-        w.hist);
+        w.hist, rebuild);
     ++w.launches;
-    radix_sort(w, w.n, p.passes, kCtrObjSort, s);
+    radix_sort(w, w.n, p.passes, kCtrObjSort, s, rebuild);
 }
 
 // ---------------------------------------------------------------------------
@@ -305,13 +341,14 @@ __global__ void __launch_bounds__(256) k_leaves(
     uint8_t *__restrict__ blevel, int32_t *__restrict__ obj_leaf, int32_t *__restrict__ cb,
     int64_t ncell, int32_t *scalars,
     uint64_t *status, uint32_t *ticket, const uint32_t *__restrict__ tickinfo, uint32_t site,
-    uint32_t *err) {
+    uint32_t *err, bool guarded, int32_t sig, bool emit_empty, int64_t leaf_cap) {
+    if (guarded && scalars[kScalarRebuild] == 0) return;  // this tick reuses the leaves
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t s_tile, s_tmp[8], s_excl;
     // long runs of cells without a leaf, filled by the whole block
     constexpr int kMaxGaps = 64;
     __shared__ int64_t s_gap_lo[kMaxGaps], s_gap_hi[kMaxGaps];
-    __shared__ int32_t s_gap_b[kMaxGaps];
+    __shared__ int32_t s_gap_b[kMaxGaps], s_gap_pos[kMaxGaps];
     __shared__ int s_ngap;
     const int tid = threadIdx.x;
     if (tid == 0) s_tile = atomicAdd(ticket, 1u);
@@ -374,17 +411,32 @@ __global__ void __launch_bounds__(256) k_leaves(
         s_code[e + 1] = code;
     }
     __syncthreads();
-    // flags: 4 consecutive elements per thread
+    // flags: 4 consecutive elements per thread.  With emit_empty (index reuse)
+    // every level-G cell without objects also gets a leaf, empty, at level G,
+    // so that any object of a later tick finds a leaf in its cell; an element
+    // that starts a leaf then counts the empty cells just before its own.
+    auto gcell = [&](int e1) -> int64_t {  // level-G cell of local element e1 - 1
+        return (int64_t)(s_code[e1] >> (2 * (s_lam[e1] - G)));
+    };
     uint32_t fl = 0, cnt = 0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int e = tid * 4 + q;
         const int64_t i = t0 + e;
         bool f = false;
-        if (i < n)
+        uint32_t wgt = 0;
+        if (i < n) {
             f = (i == 0) || s_lam[e + 1] != s_lam[e] || s_code[e + 1] != s_code[e];
+            if (f) {
+                wgt = 1;
+                if (emit_empty) {
+                    const int64_t gap = gcell(e + 1) - (i == 0 ? -1 : gcell(e)) - 1;
+                    wgt += gap > 0 ? (uint32_t)gap : 0u;
+                }
+            }
+        }
         fl |= (f ? 1u : 0u) << q;
-        cnt += f ? 1u : 0u;
+        cnt += wgt;
     }
     uint32_t tile_total;
     __shared__ uint32_t s_total;
@@ -398,51 +450,119 @@ __global__ void __launch_bounds__(256) k_leaves(
     __syncthreads();
     const uint32_t excl = s_excl;
     uint32_t b = excl + off;
+    const uint32_t gsh = 2u * (uint32_t)(L - G);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int64_t iq = t0 + tid * 4 + q;
-        if (iq < n) obj_leaf[iq] = (int32_t)((fl & (1u << q)) ? b : b - 1u);
-        if ((fl & (1u << q)) && b < (uint64_t)n) {
-            const int e = tid * 4 + q;
-            const int lam = s_lam[e + 1];
-            bstart[b] = (int32_t)(t0 + e);
-            bcode[b] = (uint32_t)((uint64_t)s_code[e + 1] << (2 * (L - lam)));
-            blevel[b] = (uint8_t)lam;
-            // cell map (the paper's z_map at level G): the cells from just after
-            // the previous leaf's cell up to this leaf's cell start at leaf b
-            int64_t c_here = (int64_t)(s_code[e + 1] >> (2 * (lam - G)));
-            if (c_here > ncell) c_here = ncell;
-            const int64_t c_prev =
-                t0 + e == 0 ? -1 : (int64_t)(s_code[e] >> (2 * (s_lam[e] - G)));
+        if (!(fl & (1u << q))) {
+            if (iq < n) obj_leaf[iq] = (int32_t)(b - 1u);
+            continue;
+        }
+        const int e = tid * 4 + q;
+        const int lam = s_lam[e + 1];
+        // cell map (the paper's z_map at level G): cb[c] is the first leaf of cell c
+        int64_t c_here = gcell(e + 1);
+        if (c_here > ncell) c_here = ncell;
+        const int64_t c_prev = iq == 0 ? -1 : gcell(e);
+        if (emit_empty && c_here - c_prev > 1) {
+            // one empty leaf for each cell strictly between the two
+            const int64_t lo = c_prev + 1, hi = c_here - 1;
             int slot = -1;
-            if (c_here - c_prev > 64) {
+            if (hi - lo >= 64) {
                 slot = atomicAdd(&s_ngap, 1);
                 if (slot < kMaxGaps) {
-                    s_gap_lo[slot] = c_prev + 1;
-                    s_gap_hi[slot] = c_here;
+                    s_gap_lo[slot] = lo;
+                    s_gap_hi[slot] = hi;
                     s_gap_b[slot] = (int32_t)b;
+                    s_gap_pos[slot] = (int32_t)iq;
                 }
             }
-            if (slot < 0 || slot >= kMaxGaps)
-                for (int64_t c = c_prev + 1; c <= c_here; ++c) cb[c] = (int32_t)b;
-            ++b;
+            if (slot < 0 || slot >= kMaxGaps) {
+                for (int64_t c = lo; c <= hi; ++c) {
+                    const uint32_t bb = b + (uint32_t)(c - lo);
+                    if (bb < (uint64_t)leaf_cap) {
+                        bstart[bb] = (int32_t)iq;
+                        bcode[bb] = (uint32_t)c << gsh;
+                        blevel[bb] = (uint8_t)G;
+                        cb[c] = (int32_t)bb;
+                    }
+                }
+            }
+            b += (uint32_t)(hi - lo + 1);
         }
+        if (iq < n) obj_leaf[iq] = (int32_t)b;
+        if (b < (uint64_t)leaf_cap) {
+            bstart[b] = (int32_t)iq;
+            bcode[b] = (uint32_t)((uint64_t)s_code[e + 1] << (2 * (L - lam)));
+            blevel[b] = (uint8_t)lam;
+            if (emit_empty) {
+                if (c_here != c_prev) cb[c_here] = (int32_t)b;
+            } else {
+                // the cells from just after the previous leaf's cell up to
+                // this leaf's cell start at leaf b
+                int slot = -1;
+                if (c_here - c_prev > 64) {
+                    slot = atomicAdd(&s_ngap, 1);
+                    if (slot < kMaxGaps) {
+                        s_gap_lo[slot] = c_prev + 1;
+                        s_gap_hi[slot] = c_here;
+                        s_gap_b[slot] = (int32_t)b;
+                        s_gap_pos[slot] = -1;
+                    }
+                }
+                if (slot < 0 || slot >= kMaxGaps)
+                    for (int64_t c = c_prev + 1; c <= c_here; ++c) cb[c] = (int32_t)b;
+            }
+        }
+        ++b;
     }
     if (t0 + kLeafTile >= n) {
-        const uint32_t m = excl + tile_total <= (uint64_t)n ? excl + tile_total : (uint32_t)n;
+        // cells after the last object's cell: no leaf (they start at leaf m),
+        // or one empty leaf each
+        const int e = (int)(n - 1 - t0);
+        const int64_t c_last = gcell(e + 1);
+        const int64_t trail = emit_empty && c_last + 1 < ncell ? ncell - 1 - c_last : 0;
+        const uint64_t m_obj = (uint64_t)excl + tile_total;
+        uint64_t m = m_obj + (uint64_t)trail;
+        m = m <= (uint64_t)leaf_cap ? m : (uint64_t)leaf_cap;
         if (tid == 0) {
             scalars[kScalarLeaves] = (int32_t)m;
+            scalars[kScalarIndexSig] = sig;
             bstart[m] = (int32_t)n;
         }
-        // cells after the last leaf's cell map to m (no leaf)
-        const int e = (int)(n - 1 - t0);
-        const int64_t c_last = (int64_t)(s_code[e + 1] >> (2 * (s_lam[e + 1] - G)));
-        for (int64_t c = c_last + 1 + tid; c <= ncell; c += 256) cb[c] = (int32_t)m;
+        for (int64_t c = c_last + 1 + tid; c <= ncell; c += 256) {
+            if (c == ncell || !emit_empty) {
+                cb[c] = (int32_t)(c == ncell ? m : m_obj);
+            } else {
+                const uint64_t bb = m_obj + (uint64_t)(c - c_last - 1);
+                if (bb < (uint64_t)leaf_cap) {
+                    bstart[bb] = (int32_t)n;
+                    bcode[bb] = (uint32_t)c << gsh;
+                    blevel[bb] = (uint8_t)G;
+                    cb[c] = (int32_t)bb;
+                }
+            }
+        }
     }
     __syncthreads();
     const int ngap = s_ngap < kMaxGaps ? s_ngap : kMaxGaps;
-    for (int gi = 0; gi < ngap; ++gi)
-        for (int64_t c = s_gap_lo[gi] + tid; c <= s_gap_hi[gi]; c += 256) cb[c] = s_gap_b[gi];
+    for (int gi = 0; gi < ngap; ++gi) {
+        const int64_t lo = s_gap_lo[gi], hi = s_gap_hi[gi];
+        const int32_t b0 = s_gap_b[gi], pos = s_gap_pos[gi];
+        for (int64_t c = lo + tid; c <= hi; c += 256) {
+            if (pos < 0) {
+                cb[c] = b0;
+            } else {
+                const int64_t bb = b0 + (c - lo);
+                if (bb < leaf_cap) {
+                    bstart[bb] = pos;
+                    bcode[bb] = (uint32_t)c << gsh;
+                    blevel[bb] = (uint8_t)G;
+                    cb[c] = (int32_t)bb;
+                }
+            }
+        }
+    }
     // leaf-ordered SoA (a5)
     for (int e = tid; e < kLeafTile; e += 256) {
         const int64_t i = t0 + e;
@@ -469,17 +589,20 @@ static size_t leaves_smem(int th) {
 
 // Tight bounding box of every leaf's members (used as conservative lower
 // bounds of member distances by the expansion).
-__global__ void k_leaf_aabb(const int32_t *__restrict__ bstart, const int32_t *__restrict__ scalars,
+// Also sums the squared leaf counts (the cost proxy of index reuse).
+__global__ void k_leaf_aabb(const int32_t *__restrict__ bstart, int32_t *scalars,
                             const float *__restrict__ xs, const float *__restrict__ ys,
                             float4 *__restrict__ baabb, int2 *__restrict__ brange, int64_t n) {
     const int32_t m = scalars[kScalarLeaves];
+    unsigned long long cost = 0;
     for (int32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < m; b += gridDim.x * blockDim.x) {
         const int32_t s = bstart[b], e = bstart[b + 1];
-        if (s < 0 || e <= s || e > n) {  // leaves are never empty
+        if (s < 0 || e <= s || e > n) {  // empty (only a reused leaf can be)
             baabb[b] = make_float4(0.f, 0.f, -1.f, -1.f);
             brange[b] = make_int2(0, 0);
             continue;
         }
+        cost += (unsigned long long)(e - s) * (unsigned long long)(e - s);
         brange[b] = make_int2(s, e);
         float x0 = xs[s], x1 = x0, y0 = ys[s], y1 = y0;
         for (int32_t i = s + 1; i < e; ++i) {
@@ -491,6 +614,10 @@ __global__ void k_leaf_aabb(const int32_t *__restrict__ bstart, const int32_t *_
         }
         baabb[b] = make_float4(x0, y0, x1, y1);
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cost += __shfl_xor_sync(kFull, cost, o);
+    if ((threadIdx.x & 31) == 0 && cost)
+        atomicAdd(reinterpret_cast<unsigned long long *>(scalars + kScalarCostNow), cost);
 }
 
 void launch_leaves(World &w, const Plan &p, cudaStream_t s) {
@@ -503,7 +630,8 @@ void launch_leaves(World &w, const Plan &p, cudaStream_t s) {
                                     w.ys, w.sid, w.inv, w.bstart, w.bcode, w.blevel, w.obj_leaf,
                                     w.cb,
                                     ncell, w.scalars, w.status, w.counters + kCtrLeaves,
-                                    w.tickinfo, w.site++, w.err);
+                                    w.tickinfo, w.site++, w.err, p.reuse_age > 0,
+                                    index_signature(p), p.reuse_age > 0, w.leaf_cap);
     const int g = grid_for(w.n, 256, num_sms(w.device) * 8);
     k_leaf_aabb<<<g, 256, 0, s>>>(w.bstart, w.scalars, w.xs, w.ys, w.baabb, w.brange, w.n);
     w.launches += 2;
@@ -520,7 +648,9 @@ __global__ void __launch_bounds__(256) k_scan_excl(const int32_t *in, int32_t *o
                                                    int32_t *total, uint64_t *status,
                                                    uint32_t *ticket,
                                                    const uint32_t *__restrict__ tickinfo,
-                                                   uint32_t site, uint32_t *err) {
+                                                   uint32_t site, uint32_t *err,
+                                                   const int32_t *skip_if) {
+    if (skip_if && *skip_if != 0) return;  // the same for every block of the launch
     __shared__ uint32_t s_tile, s_tmp[8], s_total, s_excl;
     const int tid = threadIdx.x;
     if (tid == 0) s_tile = atomicAdd(ticket, 1u);
@@ -576,17 +706,19 @@ __global__ void __launch_bounds__(256) k_scan_excl(const int32_t *in, int32_t *o
     if ((int64_t)(tile + 1) * kScanTile >= len && tid == 255 && total) *total = (int32_t)run;
 }
 
+// skip_if: when non-null and nonzero on the device, the launch does nothing.
 static void scan_excl(World &w, const int32_t *in, int32_t *out, int64_t len, int32_t *total,
-                      int counter, cudaStream_t s, bool packets = false) {
+                      int counter, cudaStream_t s, bool packets = false,
+                      const int32_t *skip_if = nullptr) {
     const int tiles = (int)((len + kScanTile - 1) / kScanTile);
     if (packets)
         k_scan_excl<true><<<tiles, 256, 0, s>>>(in, out, len, total, w.status,
                                                 w.counters + counter, w.tickinfo, w.site++,
-                                                w.err);
+                                                w.err, skip_if);
     else
         k_scan_excl<false><<<tiles, 256, 0, s>>>(in, out, len, total, w.status,
                                                  w.counters + counter, w.tickinfo, w.site++,
-                                                 w.err);
+                                                 w.err, skip_if);
     ++w.launches;
 }
 
@@ -777,6 +909,82 @@ void launch_packets(World &w, const Plan &p, int64_t n_q, cudaStream_t s) {
               true);
     k_packets<<<g, 256, 0, s>>>(w.qcs, w.pk_off, ncell, packet_capacity(w), w.pk_start,
                                 w.pk_len);
+    w.launches += 2;
+}
+
+// ---------------------------------------------------------------------------
+// Index reuse (the paper's stage (i) skipped): on a tick that keeps the
+// leaves, every object is put in a leaf of its level-G cell (the leaf whose
+// code range holds its key, else the nearest one in Morton order; any leaf of
+// the cell keeps the walk exact, since the walk reaches leaves through their
+// cells and tests every leaf's box, recomputed each tick from its members),
+// and a counting sort by leaf replaces the radix sort and the leaf split.
+// While reuse is on, the leaf split gives every empty level-G cell an empty
+// leaf, so an object always finds one; a cell without leaf (only if the plan
+// changed underneath) makes the tick rebuild instead.
+
+__global__ void k_reuse_assign(const float *__restrict__ px, const float *__restrict__ py,
+                               int64_t n, float x0, float y0, float scale, int L, int G,
+                               const int32_t *__restrict__ cb, const uint32_t *__restrict__ bcode,
+                               int32_t *scalars, uint32_t *__restrict__ key_by_id,
+                               int32_t *__restrict__ leaf_by_id, int32_t *lcnt) {
+    if (scalars[kScalarRebuild] != 0) return;
+    const int32_t m = scalars[kScalarLeaves];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t key = morton_key(px[i], py[i], x0, y0, scale, L);
+        const uint32_t c = key >> (2 * (L - G));
+        if (cb[c] >= cb[c + 1]) {  // no leaf in this cell: rebuild this tick
+            atomicExch(scalars + kScalarRebuild, 1);
+            return;
+        }
+        int32_t b = leaf_near(cb, bcode, L, G, key);
+        b = b < 0 ? 0 : (b >= m ? m - 1 : b);
+        key_by_id[i] = key;
+        leaf_by_id[i] = b;
+        atomicAdd(lcnt + b, 1);
+    }
+}
+
+__global__ void k_reuse_place(const float *__restrict__ px, const float *__restrict__ py,
+                              int64_t n, const uint32_t *__restrict__ key_by_id,
+                              const int32_t *__restrict__ leaf_by_id,
+                              const int32_t *__restrict__ bstart, int32_t *lcnt,
+                              const int32_t *__restrict__ scalars, float *__restrict__ xs,
+                              float *__restrict__ ys, int32_t *__restrict__ sid,
+                              int32_t *__restrict__ inv, int32_t *__restrict__ obj_leaf,
+                              uint32_t *__restrict__ skey) {
+    if (scalars[kScalarRebuild] != 0) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t b = leaf_by_id[i];
+        const int32_t pos = bstart[b] + atomicSub(lcnt + b, 1) - 1;  // leaves lcnt at 0
+        if (pos < 0 || pos >= n) continue;  // only after a timed-out look-back
+        xs[pos] = px[i];
+        ys[pos] = py[i];
+        sid[pos] = (int32_t)i;
+        inv[i] = pos;
+        obj_leaf[pos] = b;
+        skey[pos] = key_by_id[i];
+    }
+}
+
+void launch_index_reuse(World &w, const Plan &p, cudaStream_t s) {
+    // the sorted keys land where the radix sort leaves them; the other key and
+    // value buffers hold each object's key and leaf meanwhile
+    const int r = p.passes & 1;
+    int32_t *lcnt = w.lcnt;
+    // leaves: the objects' ones plus at most one empty leaf per level-G cell
+    int64_t len = w.n + (1ll << (2 * p.G)) + 1;
+    len = len < w.leaf_cap + 1 ? len : w.leaf_cap + 1;
+    const int g = grid_for(w.n, 256, num_sms(w.device) * 8);
+    cudaMemsetAsync(lcnt, 0, sizeof(int32_t) * (size_t)len, s);
+    k_reuse_assign<<<g, 256, 0, s>>>(w.px, w.py, w.n, w.desc.x0, w.desc.y0, w.scale, p.L, p.G,
+                                     w.cb, w.bcode, w.scalars, w.key[r ^ 1], w.val[r ^ 1], lcnt);
+    scan_excl(w, lcnt, w.bstart, len, nullptr, kCtrReuseScan, s, false,
+              w.scalars + kScalarRebuild);
+    k_reuse_place<<<g, 256, 0, s>>>(w.px, w.py, w.n, w.key[r ^ 1], w.val[r ^ 1], w.bstart, lcnt,
+                                    w.scalars, w.xs, w.ys, w.sid, w.inv, w.obj_leaf, w.key[r]);
     w.launches += 2;
 }
 

@@ -25,12 +25,17 @@ constexpr int kLeafTile = 1024;
 constexpr int kScanTile = 2048;
 
 // Device scalars written by kernels and read by later kernels.
+// Index reuse state (scratch, so an evicted world rebuilds): the signature
+// of the plan the leaves were built for, the index's age in ticks, this
+// tick's rebuild flag, and the leaves' sum of squared counts (a cost proxy)
+// right after the build and at the last tick (64-bit, two words each).
 enum Scalar : int { kScalarLeaves = 0, kScalarValidQueries = 1, kScalarPackets = 2,
-                    kNumScalars = 8 };
+                    kScalarIndexSig = 3, kScalarIndexAge = 4, kScalarRebuild = 5,
+                    kScalarCostBase = 6, kScalarCostNow = 8, kNumScalars = 16 };
 
 // Ticket counters (one per single-pass launch site in a tick).
 enum Counter : int { kCtrObjSort = 0, kCtrQuerySort = 4, kCtrLeaves = 8, kCtrQueryScan = 9,
-                     kCtrPacketScan = 10, kCtrExpand = 11 };
+                     kCtrPacketScan = 10, kCtrExpand = 11, kCtrReuseScan = 12 };
 
 struct Plan {
     int L;           // max depth (key has 2L bits)
@@ -39,6 +44,8 @@ struct Plan {
     int Gp;          // packet level
     int passes;      // radix passes over 2L bits
     bool wide;       // expansion by one warp per query (else packets)
+    int reuse_age;   // index reuse: rebuild at least every reuse_age ticks (0: every tick)
+    int reuse_f16;   // and when the cost proxy grows past reuse_f16 / 16 of its built value
 };
 
 // A whole tick recorded as a CUDA graph, with what it was recorded for.
@@ -60,6 +67,8 @@ struct World {
     int gmax = 10;         // deepest cell-map level this world sizes its arrays for
     float scale = 0.f;     // 2^L / side, binary32
     knn_tuning tuning{};   // user overrides (0 = auto)
+    int reuse_age = 0;     // index reuse (knn_world_set_index_reuse)
+    float reuse_factor = 0.f;
     uint32_t site = 0;     // look-back launch index within the current tick
     cudaStream_t last_stream = nullptr;
     Plan last_plan{};
@@ -85,6 +94,8 @@ struct World {
     uint8_t *blevel = nullptr;
     float4 *baabb = nullptr;
     int2 *brange = nullptr;      // leaf b holds sorted objects [x, y)
+    int64_t leaf_cap = 0;        // room for leaves (objects' ones + empty level-G cells)
+    int32_t *lcnt = nullptr;     // index reuse: objects per leaf
     int32_t *obj_leaf = nullptr; // leaf of every sorted object
     int32_t *cb = nullptr;
     int32_t *qcnt = nullptr, *qoff = nullptr;
@@ -146,7 +157,8 @@ inline int64_t packet_capacity(const World &w) {
 void launch_validate_positions(const float *x, const float *y, int64_t n, uint32_t *flag,
                                cudaStream_t s);
 // Start of a tick: advance epoch base and stamp tick, clear tickets and the abort flag.
-void launch_tick_begin(World &w, cudaStream_t s);
+void launch_tick_begin(World &w, const Plan &p, cudaStream_t s);
+void launch_index_reuse(World &w, const Plan &p, cudaStream_t s);
 void launch_updates(World &w, const int32_t *id, const float *ux, const float *uy,
                     int64_t n_upd, cudaStream_t s);
 void launch_object_sort(World &w, const Plan &p, cudaStream_t s);

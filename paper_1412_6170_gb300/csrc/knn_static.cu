@@ -76,6 +76,7 @@ size_t cut_scratch(knnq::World &w, unsigned char *base, int64_t n_q) {
     w.ys = c.take<float>(n);
     w.sid = c.take<int32_t>(n);
     w.inv = c.take<int32_t>(n);
+    w.leaf_cap = n;  // no index reuse here, so no empty leaves
     w.bstart = c.take<int32_t>(n + 1);
     w.bcode = c.take<uint32_t>(n);
     w.blevel = c.take<uint8_t>(n);
@@ -175,13 +176,14 @@ extern "C" knn_status knn_query_static(const knn_world_desc *desc, const float *
     const int gmax = p.L < kStaticMaxGridLevel ? p.L : kStaticMaxGridLevel;
     p.G = clampi(round_log4(2.0 * (double)n / (double)p.th), 1, gmax);
     p.Gp = clampi(round_log4((double)(n_q > 0 ? n_q : 1) / 48.0), 0, p.G);
+    p.wide = k > 32;
 
     cudaStream_t s = (cudaStream_t)stream;
     // what must start at zero: error words and device scalars; tile tickets
     // are cleared (and the epoch advanced) by the tick-begin kernel
     cudaMemsetAsync(w.err, 0, sizeof(uint32_t) * 4, s);
     cudaMemsetAsync(w.scalars, 0, sizeof(int32_t) * knnq::kNumScalars, s);
-    knnq::launch_tick_begin(w, s);
+    knnq::launch_tick_begin(w, p, s);
     knnq::launch_object_sort(w, p, s);
     knnq::launch_leaves(w, p, s);
     if (n_q > 0) {
@@ -190,8 +192,12 @@ extern "C" knn_status knn_query_static(const knn_world_desc *desc, const float *
         else
             knnq::launch_queries_explicit(w, p, q_id_dev, q_x_dev, q_y_dev, n_q, k, out_ids_dev,
                                           out_d2_dev, s);
-        knnq::launch_packets(w, p, n_q, s);
-        knnq::launch_expand(w, p, k, n_q, out_ids_dev, out_d2_dev, s);
+        if (p.wide) {
+            knnq::launch_expand_wide(w, p, k, n_q, out_ids_dev, out_d2_dev, s);
+        } else {
+            knnq::launch_packets(w, p, n_q, s);
+            knnq::launch_expand(w, p, k, n_q, out_ids_dev, out_d2_dev, s);
+        }
     }
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return bad(KNN_ERR_CUDA, cudaGetErrorString(e));

@@ -88,6 +88,8 @@ _SIGNATURES = {
     "knn_world_launches": ([_vp, ctypes.POINTER(_i64)], ctypes.c_int),
     "knn_world_set_profiling": ([_vp, _i32], ctypes.c_int),
     "knn_world_set_graphs": ([_vp, _i32], ctypes.c_int),
+    "knn_world_set_index_reuse": ([_vp, _i32, ctypes.c_float], ctypes.c_int),
+    "knn_world_index_info": ([_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)], ctypes.c_int),
     "knn_world_record_tick": ([_vp, ctypes.POINTER(knn_tick_args)], ctypes.c_int),
     "knn_world_stage_times": ([_vp, ctypes.POINTER(ctypes.c_float), _i32], ctypes.c_int),
     "knn_stage_name": ([_i32], ctypes.c_char_p),
@@ -211,6 +213,16 @@ def knn_world_set_profiling(w: int, enable: bool) -> None:
 
 def knn_world_set_graphs(w: int, enable: bool) -> None:
     _check(lib().knn_world_set_graphs(w, 1 if enable else 0))
+
+
+def knn_world_set_index_reuse(w: int, max_age: int, factor: float = 0.0) -> None:
+    _check(lib().knn_world_set_index_reuse(w, max_age, factor))
+
+
+def knn_world_index_info(w: int) -> dict:
+    age, rebuilt = _i32(), _i32()
+    _check(lib().knn_world_index_info(w, ctypes.byref(age), ctypes.byref(rebuilt)))
+    return {"age": age.value, "rebuilt": rebuilt.value}
 
 
 def knn_world_record_tick(w: int, args: knn_tick_args) -> None:
@@ -422,6 +434,12 @@ class World:
 
     def set_graphs(self, enable: bool = True):
         knn_world_set_graphs(self.handle, enable)
+
+    def set_index_reuse(self, max_age: int, factor: float = 0.0):
+        knn_world_set_index_reuse(self.handle, max_age, factor)
+
+    def index_info(self) -> dict:
+        return knn_world_index_info(self.handle)
 
     def record_tick(self, k: int, q_id=None, upd_id=None, upd_x=None, upd_y=None, q_x=None,
                     q_y=None, out_ids=None, out_d2=None):

@@ -360,3 +360,92 @@ def test_tick_graph_replay_matches_direct_launches():
     finally:
         a.close()
         b.close()
+
+
+# -------------------------------------------------------------------------
+# Index reuse: the leaves kept across ticks give the same rows
+
+
+@pytest.mark.parametrize("max_age,factor", [(3, 0.0), (100, 1.25)])
+def test_index_reuse_uniform_matches_oracle(max_age, factor):
+    w = synth.plain_uniform_moving(n=30011, k=16, ticks=6, seed=31)
+    world = make_world(w.x0, w.y0, k_max=16, max_queries=30011)
+    try:
+        world.set_index_reuse(max_age, factor)
+        x, y = w.x0.copy(), w.y0.copy()
+        ages = []
+        for ti, t in enumerate(w.ticks):
+            x, y, _ = oracle.apply_updates(x, y, t.upd_id, t.upd_x, t.upd_y)
+            ids, d2 = gpu_tick(world, t)
+            rid, rd2 = oracle_rows(x, y, t, np.arange(t.q_id.shape[0]))
+            assert_rows_equal(ids, d2, rid, rd2, what=f"reuse tick {ti}")
+            ages.append(world.index_info()["age"])
+        assert ages[0] == 0 and max(ages) >= 1, ages  # built once, then reused
+        if factor == 0.0:
+            assert max(ages) <= max_age, ages
+        st, bits = world.status()
+        assert st == knnq.KNN_OK, (st, bits)
+    finally:
+        world.close()
+
+
+def test_index_reuse_clustered_subset_queries_and_explicit_centres():
+    w = synth.skewed_moving(n=60000, k=8, ticks=5, seed=32)
+    world = make_world(w.x0, w.y0, k_max=8, max_queries=max(t.q_id.shape[0] for t in w.ticks))
+    try:
+        world.set_index_reuse(50)
+        x, y = w.x0.copy(), w.y0.copy()
+        r = np.random.default_rng(33)
+        for ti, t in enumerate(w.ticks):
+            x, y, _ = oracle.apply_updates(x, y, t.upd_id, t.upd_x, t.upd_y)
+            if ti % 2:  # explicit centres near the issuers
+                qx = np.clip(x[t.q_id] + r.normal(0, 0.01, t.q_id.shape[0]), 0, 1).astype(np.float32)
+                qy = np.clip(y[t.q_id] + r.normal(0, 0.01, t.q_id.shape[0]), 0, 1).astype(np.float32)
+                t = synth.Tick(t.upd_id, t.upd_x, t.upd_y, t.q_id, t.k, qx, qy)
+            ids, d2 = gpu_tick(world, t)
+            rows = sample_rows(t.q_id.shape[0], 3000, seed=ti)
+            rid, rd2 = oracle_rows(x, y, t, rows)
+            assert_rows_equal(ids, d2, rid, rd2, rows, what=f"clustered reuse tick {ti}")
+        assert world.index_info()["age"] >= 1
+    finally:
+        world.close()
+
+
+def test_index_reuse_across_empty_cells_and_cost_rebuild():
+    # every object in the left half; half of them jump into the right half,
+    # whose level-G cells only have empty leaves; then every object jumps into
+    # one small square, which piles them into a few leaves: the next tick's
+    # cost test rebuilds.  Every tick stays exact.
+    n = 20000
+    r = np.random.default_rng(34)
+    x0 = (r.random(n) * 0.5).astype(np.float32)
+    y0 = r.random(n).astype(np.float32)
+    ids = np.arange(n, dtype=np.int32)
+    none = (np.zeros(0, np.int32), np.zeros(0, np.float32), np.zeros(0, np.float32))
+    world = make_world(x0, y0, k_max=8, max_queries=n)
+    try:
+        world.set_index_reuse(1000, 2.0)
+        x, y = x0.copy(), y0.copy()
+        infos = []
+        for ti in range(5):
+            if ti == 2:
+                moved = ids[: n // 2]
+                upd = (moved, (x[moved] + 0.5).astype(np.float32), y[moved].copy())
+            elif ti == 3:
+                upd = (ids, (0.3 + 0.01 * r.random(n)).astype(np.float32),
+                       (0.6 + 0.01 * r.random(n)).astype(np.float32))
+            else:
+                upd = none
+            t = synth.Tick(upd[0], upd[1], upd[2], ids, 8)
+            x, y, _ = oracle.apply_updates(x, y, t.upd_id, t.upd_x, t.upd_y)
+            got_ids, got_d2 = gpu_tick(world, t)
+            rows = sample_rows(n, 3000, seed=ti)
+            rid, rd2 = oracle_rows(x, y, t, rows)
+            assert_rows_equal(got_ids, got_d2, rid, rd2, rows, what=f"jump tick {ti}")
+            infos.append(world.index_info())
+        assert [i["age"] for i in infos[:4]] == [0, 1, 2, 3], infos
+        assert infos[4]["rebuilt"] == 1, infos
+        st, bits = world.status()
+        assert st == knnq.KNN_OK, (st, bits)
+    finally:
+        world.close()

@@ -53,3 +53,48 @@ def test_leaves_match_oracle(dist, n, th, G, L):
     assert np.array_equal(got["order"], want["order"])
     for key in ("level", "z", "start", "count"):
         assert np.array_equal(got[key].astype(np.int64), want[key].astype(np.int64)), key
+
+
+@pytest.mark.parametrize("dist,n,th,G", [("clustered", 100000, 16, 8), ("half", 30000, 8, 6)])
+def test_reuse_leaves_cover_every_cell(dist, n, th, G):
+    # with index reuse on, the leaves are the oracle's plus one empty leaf at
+    # level G for every level-G cell without objects, all in Morton order
+    L = 16
+    if dist == "clustered":
+        x, y = synth.clustered_positions(n, 3)
+    else:
+        x, y = synth.uniform_positions(n, 4)
+        x = (x * 0.5).astype(np.float32)
+    world = make_world(x, y, k_max=8)
+    try:
+        world.set_tuning(leaf_capacity=th, grid_level=G, packet_level=min(G, 4))
+        world.set_index_reuse(4)
+        t = synth.Tick(np.zeros(0, np.int32), np.zeros(0, np.float32), np.zeros(0, np.float32),
+                       np.arange(100, dtype=np.int32), 4)
+        gpu_tick(world, t)
+        got = {k: v.cpu().numpy() for k, v in world.leaves().items()}
+    finally:
+        world.close()
+    got["z"] = got["z"].view(np.uint32)
+    want = oracle.pr_quadtree(x, y, L, th, min_level=G)
+    lv, z = want["level"].astype(np.int64), want["z"].astype(np.int64)
+    start, count = want["start"].astype(np.int64), want["count"].astype(np.int64)
+    cell = z >> (2 * (lv - G))
+    empty = np.setdiff1d(np.arange(4 ** G), cell)
+    zpp = np.concatenate([z << (2 * (L - lv)), empty << (2 * (L - G))])
+    order = np.argsort(zpp, kind="stable")
+    e_level = np.concatenate([lv, np.full(empty.size, G)])[order]
+    e_z = np.concatenate([z, empty])[order]
+    e_count = np.concatenate([count, np.zeros(empty.size, np.int64)])[order]
+    # an empty leaf starts where the next non-empty one does (n after the last)
+    e_start = np.concatenate([start, np.full(empty.size, -1)])[order]
+    nxt = n
+    for i in range(e_start.size - 1, -1, -1):
+        if e_start[i] < 0:
+            e_start[i] = nxt
+        else:
+            nxt = e_start[i]
+    assert empty.size > 0
+    assert np.array_equal(got["order"], want["order"])
+    for key, val in (("level", e_level), ("z", e_z), ("start", e_start), ("count", e_count)):
+        assert np.array_equal(got[key].astype(np.int64), val), key
