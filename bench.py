@@ -290,6 +290,85 @@ def serving_vs_plain(dev, n_worlds=8, n_obj=N_OBJ, k=K, n_req=128, load=0.8, n_s
     }
 
 
+def index_reuse_vs_rebuild(dev, ticks=20, max_age=8):
+    """The headline workload with the paper's index reuse (leaves kept across ticks,
+    rebuilt at least every max_age + 1 ticks) against a rebuild every tick; same
+    moves, same rows (checked here on the last tick)."""
+    import torch
+
+    from paper_1412_6170_gb300 import knnq, synth
+    wl = synth.plain_uniform_moving(n=N_OBJ, k=K, ticks=N_TICKS, seed=0)
+    ids = torch.from_numpy(wl.ticks[0].upd_id).to(dev)
+    ux = [torch.from_numpy(t.upd_x).to(dev) for t in wl.ticks]
+    uy = [torch.from_numpy(t.upd_y).to(dev) for t in wl.ticks]
+    stream = torch.cuda.current_stream()
+    out = {}
+    rows = {}
+    for name, age in (("rebuild every tick", 0), (f"reuse, max_age {max_age}", max_age)):
+        x0, y0 = torch.from_numpy(wl.x0).to(dev), torch.from_numpy(wl.y0).to(dev)
+        world = knnq.World(x0, y0, k_max=K, max_queries=N_OBJ)
+        world.set_index_reuse(age)
+        oi = torch.empty((N_OBJ, K), dtype=torch.int32, device=dev)
+        od = torch.empty((N_OBJ, K), dtype=torch.float32, device=dev)
+        try:
+            for i in range(3):
+                world.tick(K, ids, ids, ux[i % N_TICKS], uy[i % N_TICKS], out_ids=oi, out_d2=od)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for i in range(3, 3 + ticks):
+                world.tick(K, ids, ids, ux[i % N_TICKS], uy[i % N_TICKS], out_ids=oi, out_d2=od)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / ticks
+            out[name] = {"tick_ms": ms, "queries_per_s": N_OBJ / (ms * 1e-3)}
+            rows[name] = (oi.cpu(), od.cpu())
+        finally:
+            world.close()
+    a, b = rows.values()
+    same = bool(torch.equal(a[0], b[0]) and torch.equal(a[1].view(torch.int32),
+                                                        b[1].view(torch.int32)))
+    return {"workload": f"{WORKLOAD}; {ticks} back-to-back ticks (no L2 flush)",
+            "per_mode": out, "rows_identical": same}
+
+
+def k_sweep(dev, ks=(1, 4, 16, 32, 64, 128, 256, 512), iters=3):
+    """Ticks of the 1M-uniform world (every object moves and queries) for k over the
+    paper's range [1, 512]: queries/s per k and the expansion kernel used."""
+    import torch
+
+    from paper_1412_6170_gb300 import knnq, synth
+    wl = synth.plain_uniform_moving(n=N_OBJ, k=max(ks), ticks=2, seed=3)
+    x0, y0 = torch.from_numpy(wl.x0).to(dev), torch.from_numpy(wl.y0).to(dev)
+    ids = torch.from_numpy(wl.ticks[0].upd_id).to(dev)
+    ux = [torch.from_numpy(t.upd_x).to(dev) for t in wl.ticks]
+    uy = [torch.from_numpy(t.upd_y).to(dev) for t in wl.ticks]
+    world = knnq.World(x0, y0, k_max=max(ks), max_queries=N_OBJ)
+    stream = torch.cuda.current_stream()
+    out = {}
+    try:
+        for k in ks:
+            oi = torch.empty((N_OBJ, k), dtype=torch.int32, device=dev)
+            od = torch.empty((N_OBJ, k), dtype=torch.float32, device=dev)
+            world.tick(k, ids, ids, ux[0], uy[0], out_ids=oi, out_d2=od)
+            world.tick(k, ids, ids, ux[1], uy[1], out_ids=oi, out_d2=od)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for i in range(iters):
+                world.tick(k, ids, ids, ux[i % 2], uy[i % 2], out_ids=oi, out_d2=od)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / iters
+            kernel = "warp per query" if world.get_tuning(N_OBJ, k)["expansion"] == 2 \
+                else "packets"
+            out[str(k)] = {"tick_ms": ms, "queries_per_s": N_OBJ / (ms * 1e-3),
+                           "expansion": kernel}
+            del oi, od
+    finally:
+        world.close()
+    return {"workload": "uniform 1M objects, every object moves N(0,1e-3) and queries, "
+                        f"{iters} timed ticks per k", "per_k": out}
+
+
 def batched_vs_plain(dev, n_worlds=256, seed=0, iters=5):
     """Many uneven worlds (1k-200k objects, uniform or clustered, k in {4,8,16,32}, all
     query): one knn_batch_tick (a recorded CUDA graph) against one knn_tick per world."""
@@ -564,6 +643,8 @@ def run_gpu(args):
     if not args.no_patterns:
         line["serving"] = serving_vs_plain(dev)
         line["batching"] = batched_vs_plain(dev)
+        line["k_sweep"] = k_sweep(dev)
+        line["index_reuse"] = index_reuse_vs_rebuild(dev)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
     print(json.dumps(line), flush=True)

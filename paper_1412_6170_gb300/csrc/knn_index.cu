@@ -72,9 +72,10 @@ __global__ void k_tick_begin(uint32_t *tickinfo, uint32_t *counters, int n_count
     if (i < n_counters) counters[i] = 0u;
 }
 
+// The plan an index is built for; bit 29: built for reuse (with empty leaves).
 static int32_t index_signature(const Plan &p) {
-    return (int32_t)(0x40000000u | ((uint32_t)p.L << 24) | ((uint32_t)p.G << 16) |
-                     (uint32_t)p.th);
+    return (int32_t)(0x40000000u | (p.reuse_age > 0 ? 0x20000000u : 0u) |
+                     ((uint32_t)p.L << 24) | ((uint32_t)p.G << 16) | (uint32_t)p.th);
 }
 
 void launch_tick_begin(World &w, const Plan &p, cudaStream_t s) {
@@ -649,13 +650,20 @@ __global__ void __launch_bounds__(256) k_scan_excl(const int32_t *in, int32_t *o
                                                    uint32_t *ticket,
                                                    const uint32_t *__restrict__ tickinfo,
                                                    uint32_t site, uint32_t *err,
-                                                   const int32_t *skip_if) {
+                                                   const int32_t *skip_if,
+                                                   const int32_t *len_minus_1) {
     if (skip_if && *skip_if != 0) return;  // the same for every block of the launch
+    if (len_minus_1) {  // the length is known on the device only: *len_minus_1 + 1 <= len
+        const int64_t l = (int64_t)*len_minus_1 + 1;
+        len = l < len ? (l > 0 ? l : 0) : len;
+    }
     __shared__ uint32_t s_tile, s_tmp[8], s_total, s_excl;
     const int tid = threadIdx.x;
     if (tid == 0) s_tile = atomicAdd(ticket, 1u);
     __syncthreads();
     const uint32_t tile = s_tile;
+    // tiles past the end: nothing waits on them
+    if ((int64_t)tile * kScanTile >= len && tile > 0) return;
     const int64_t base = (int64_t)tile * kScanTile + tid * 8;
     // 8 consecutive entries per thread, read as two 16-byte words when whole
     // (the buffers are 256-byte aligned and base is a multiple of 8)
@@ -707,18 +715,19 @@ __global__ void __launch_bounds__(256) k_scan_excl(const int32_t *in, int32_t *o
 }
 
 // skip_if: when non-null and nonzero on the device, the launch does nothing.
+// len_minus_1: when non-null, the device value + 1 (at most len) is the length.
 static void scan_excl(World &w, const int32_t *in, int32_t *out, int64_t len, int32_t *total,
                       int counter, cudaStream_t s, bool packets = false,
-                      const int32_t *skip_if = nullptr) {
+                      const int32_t *skip_if = nullptr, const int32_t *len_minus_1 = nullptr) {
     const int tiles = (int)((len + kScanTile - 1) / kScanTile);
     if (packets)
         k_scan_excl<true><<<tiles, 256, 0, s>>>(in, out, len, total, w.status,
                                                 w.counters + counter, w.tickinfo, w.site++,
-                                                w.err, skip_if);
+                                                w.err, skip_if, len_minus_1);
     else
         k_scan_excl<false><<<tiles, 256, 0, s>>>(in, out, len, total, w.status,
                                                  w.counters + counter, w.tickinfo, w.site++,
-                                                 w.err, skip_if);
+                                                 w.err, skip_if, len_minus_1);
     ++w.launches;
 }
 
@@ -946,32 +955,48 @@ __global__ void k_reuse_assign(const float *__restrict__ px, const float *__rest
     }
 }
 
-__global__ void k_reuse_place(const float *__restrict__ px, const float *__restrict__ py,
-                              int64_t n, const uint32_t *__restrict__ key_by_id,
-                              const int32_t *__restrict__ leaf_by_id,
-                              const int32_t *__restrict__ bstart, int32_t *lcnt,
-                              const int32_t *__restrict__ scalars, float *__restrict__ xs,
-                              float *__restrict__ ys, int32_t *__restrict__ sid,
-                              int32_t *__restrict__ inv, int32_t *__restrict__ obj_leaf,
-                              uint32_t *__restrict__ skey) {
+// Each object's place: the next free slot of its leaf (the order inside a
+// leaf does not matter); perm[place] = object.
+__global__ void k_reuse_rank(int64_t n, const int32_t *__restrict__ leaf_by_id,
+                             const int32_t *__restrict__ bstart, int32_t *lcnt,
+                             const int32_t *__restrict__ scalars, int32_t *__restrict__ perm,
+                             int32_t *__restrict__ inv) {
     if (scalars[kScalarRebuild] != 0) return;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t b = leaf_by_id[i];
-        const int32_t pos = bstart[b] + atomicSub(lcnt + b, 1) - 1;  // leaves lcnt at 0
-        if (pos < 0 || pos >= n) continue;  // only after a timed-out look-back
-        xs[pos] = px[i];
-        ys[pos] = py[i];
-        sid[pos] = (int32_t)i;
+        int32_t pos = bstart[b] + atomicSub(lcnt + b, 1) - 1;  // leaves lcnt at 0
+        pos = pos < 0 ? 0 : (pos >= n ? (int32_t)(n - 1) : pos);  // only after a timeout
+        perm[pos] = (int32_t)i;
         inv[i] = pos;
-        obj_leaf[pos] = b;
-        skey[pos] = key_by_id[i];
+    }
+}
+
+// The leaf-ordered store, gathered in place order (coalesced writes).
+__global__ void k_reuse_gather(const float *__restrict__ px, const float *__restrict__ py,
+                               int64_t n, const uint32_t *__restrict__ key_by_id,
+                               const int32_t *__restrict__ leaf_by_id,
+                               const int32_t *__restrict__ perm,
+                               const int32_t *__restrict__ scalars, float *__restrict__ xs,
+                               float *__restrict__ ys, int32_t *__restrict__ sid,
+                               int32_t *__restrict__ obj_leaf, uint32_t *__restrict__ skey) {
+    if (scalars[kScalarRebuild] != 0) return;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        int32_t i = perm[p];
+        i = i < 0 || i >= n ? 0 : i;
+        xs[p] = px[i];
+        ys[p] = py[i];
+        sid[p] = i;
+        obj_leaf[p] = leaf_by_id[i];
+        skey[p] = key_by_id[i];
     }
 }
 
 void launch_index_reuse(World &w, const Plan &p, cudaStream_t s) {
-    // the sorted keys land where the radix sort leaves them; the other key and
-    // value buffers hold each object's key and leaf meanwhile
+    // the sorted keys and the place order land where the radix sort leaves its
+    // keys and ids; the other key and value buffers hold each object's key and
+    // leaf meanwhile
     const int r = p.passes & 1;
     int32_t *lcnt = w.lcnt;
     // leaves: the objects' ones plus at most one empty leaf per level-G cell
@@ -982,10 +1007,12 @@ void launch_index_reuse(World &w, const Plan &p, cudaStream_t s) {
     k_reuse_assign<<<g, 256, 0, s>>>(w.px, w.py, w.n, w.desc.x0, w.desc.y0, w.scale, p.L, p.G,
                                      w.cb, w.bcode, w.scalars, w.key[r ^ 1], w.val[r ^ 1], lcnt);
     scan_excl(w, lcnt, w.bstart, len, nullptr, kCtrReuseScan, s, false,
-              w.scalars + kScalarRebuild);
-    k_reuse_place<<<g, 256, 0, s>>>(w.px, w.py, w.n, w.key[r ^ 1], w.val[r ^ 1], w.bstart, lcnt,
-                                    w.scalars, w.xs, w.ys, w.sid, w.inv, w.obj_leaf, w.key[r]);
-    w.launches += 2;
+              w.scalars + kScalarRebuild, w.scalars + kScalarLeaves);
+    k_reuse_rank<<<g, 256, 0, s>>>(w.n, w.val[r ^ 1], w.bstart, lcnt, w.scalars, w.val[r],
+                                   w.inv);
+    k_reuse_gather<<<g, 256, 0, s>>>(w.px, w.py, w.n, w.key[r ^ 1], w.val[r ^ 1], w.val[r],
+                                     w.scalars, w.xs, w.ys, w.sid, w.obj_leaf, w.key[r]);
+    w.launches += 3;
 }
 
 void prepare_kernels() {
