@@ -331,6 +331,57 @@ def index_reuse_vs_rebuild(dev, ticks=20, max_age=8):
             "per_mode": out, "rows_identical": same}
 
 
+def brute_vs_indexed(dev, n_sample=16384):
+    """The GPU brute-force baseline (every query against every object, as in the
+    paper's comparison) against the indexed tick: on the 10k uniform k=8 world (all
+    query) and on the headline world (1M uniform, k=16) with a sample of queries;
+    rows compared for equality."""
+    import torch
+
+    from paper_1412_6170_gb300 import knnq, synth
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name, wl, nq in (("10k uniform, k=8, all query", synth.plain_uniform_one_tick(), None),
+                         ("1M uniform, k=16", synth.plain_uniform_moving(n=N_OBJ, k=K, ticks=1,
+                                                                         seed=0), n_sample)):
+        t = wl.ticks[0]
+        n, k = wl.n, t.k
+        x0, y0 = torch.from_numpy(wl.x0).to(dev), torch.from_numpy(wl.y0).to(dev)
+        q_all = torch.from_numpy(t.q_id).to(dev)
+        uid = torch.from_numpy(t.upd_id).to(dev)
+        ux, uy = torch.from_numpy(t.upd_x).to(dev), torch.from_numpy(t.upd_y).to(dev)
+        world = knnq.World(x0, y0, k_max=k, max_queries=int(q_all.shape[0]))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        try:
+            oi = torch.empty((q_all.shape[0], k), dtype=torch.int32, device=dev)
+            od = torch.empty((q_all.shape[0], k), dtype=torch.float32, device=dev)
+            world.tick(k, q_all, uid, ux, uy, out_ids=oi, out_d2=od)  # positions after the move
+            e0.record(stream)
+            for _ in range(3):
+                world.tick(k, q_all, out_ids=oi, out_d2=od)
+            e1.record(stream)
+            e1.synchronize()
+            idx_ms = e0.elapsed_time(e1) / 3
+            px, py = world.positions()
+            q = q_all if nq is None else q_all[torch.linspace(0, q_all.shape[0] - 1, nq,
+                                                                device=dev).long()]
+            knnq.brute_force(px, py, k, q)  # warm
+            e0.record(stream)
+            bi, bd = knnq.brute_force(px, py, k, q)
+            e1.record(stream)
+            e1.synchronize()
+            br_ms = e0.elapsed_time(e1)
+            rows = q.long() if nq is not None else torch.arange(q.shape[0], device=dev)
+            same = bool(torch.equal(bi, oi[rows]) and
+                        torch.equal(bd.view(torch.int32), od[rows].view(torch.int32)))
+            out[name] = {"indexed_queries_per_s": q_all.shape[0] / (idx_ms * 1e-3),
+                         "brute_queries_per_s": q.shape[0] / (br_ms * 1e-3),
+                         "brute_queries": int(q.shape[0]), "rows_identical": same}
+        finally:
+            world.close()
+    return out
+
+
 def k_sweep(dev, ks=(1, 4, 16, 32, 64, 128, 256, 512), iters=3):
     """Ticks of the 1M-uniform world (every object moves and queries) for k over the
     paper's range [1, 512]: queries/s per k and the expansion kernel used."""
@@ -645,6 +696,7 @@ def run_gpu(args):
         line["batching"] = batched_vs_plain(dev)
         line["k_sweep"] = k_sweep(dev)
         line["index_reuse"] = index_reuse_vs_rebuild(dev)
+        line["brute_force"] = brute_vs_indexed(dev)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
     print(json.dumps(line), flush=True)

@@ -203,6 +203,22 @@ knn_status knn_world_destroy(knn_world w);
 /* Thread-local description of the last error returned on this thread. */
 const char *knn_last_error(void);
 
+/* ---- GPU brute force (the paper's brute-force comparison, Section 5) ---- */
+
+/* Every query against every object, with no index: the same rows as knn_tick
+ * (Def. 1: the k smallest (d^2, id) over objects other than the issuer,
+ * ascending, padded with (-1, +inf)), for objects given as device arrays
+ * x_dev, y_dev of n floats (ids 0..n-1).  q_x_dev/q_y_dev NULL: each query is
+ * centred at its issuer q_id_dev[i] (which must lie in [0, n)); else at the
+ * given point, q_id_dev[i] = -1 meaning no issuer to exclude.  A query with
+ * an issuer outside [-1, n), no centre or a non-finite centre gets a padded
+ * row.  k in [1, 64].  Asynchronous on `stream`; nothing is allocated.
+ * O(n * n_q) work: an in-house baseline for the index's speedup. */
+knn_status knn_brute_force(const float *x_dev, const float *y_dev, int64_t n,
+                           const int32_t *q_id_dev, const float *q_x_dev, const float *q_y_dev,
+                           int64_t n_q, int32_t k, int32_t *out_ids_dev, float *out_d2_dev,
+                           void *stream);
+
 /* ---- tuning and introspection ------------------------------------------ */
 
 /* Index and expansion parameters; none of them changes any result.

@@ -75,6 +75,45 @@ __device__ __forceinline__ int32_t key_id(unsigned long long key) {
     return lo == 0xFFFFFFFFu ? -1 : (int32_t)lo - 1;
 }
 
+// Sorted register lists of keys are merged with batches of kBatch keys by
+// sorting networks (all lanes of a warp run the same compare-exchanges).
+constexpr int kBatch = 8;
+
+__device__ __forceinline__ void cmpx(unsigned long long &x, unsigned long long &y) {
+    const bool s = y < x;
+    const unsigned long long lo = s ? y : x;
+    y = s ? x : y;
+    x = lo;
+}
+
+// Sort 8 keys ascending (19 comparators, depth 6).
+__device__ __forceinline__ void sort8(unsigned long long (&b)[kBatch]) {
+    cmpx(b[0], b[2]); cmpx(b[1], b[3]); cmpx(b[4], b[6]); cmpx(b[5], b[7]);
+    cmpx(b[0], b[4]); cmpx(b[1], b[5]); cmpx(b[2], b[6]); cmpx(b[3], b[7]);
+    cmpx(b[0], b[1]); cmpx(b[2], b[3]); cmpx(b[4], b[5]); cmpx(b[6], b[7]);
+    cmpx(b[2], b[4]); cmpx(b[3], b[5]);
+    cmpx(b[1], b[4]); cmpx(b[3], b[6]);
+    cmpx(b[1], b[2]); cmpx(b[3], b[4]); cmpx(b[5], b[6]);
+}
+
+// a (KC keys, ascending) := the KC smallest of a and b (8 keys, ascending):
+// c_i = min(a_i, b_{KC-1-i}) is bitonic and holds them; a bitonic merger sorts it.
+template <int KC>
+__device__ __forceinline__ void merge_batch(unsigned long long (&a)[KC],
+                                            const unsigned long long (&b)[kBatch]) {
+#pragma unroll
+    for (int i = (KC > kBatch ? KC - kBatch : 0); i < KC; ++i) {
+        const unsigned long long v = b[KC - 1 - i];
+        a[i] = v < a[i] ? v : a[i];
+    }
+#pragma unroll
+    for (int span = KC / 2; span >= 1; span >>= 1) {
+#pragma unroll
+        for (int i = 0; i < KC; ++i)
+            if ((i & span) == 0) cmpx(a[i], a[i + span]);
+    }
+}
+
 // Level-G cell of a coordinate, with the same monotone rounding as the keys.
 __device__ __forceinline__ int cell_g(float v, float v0, float scale, int G) {
     const float t = __fmul_rn(__fsub_rn(v, v0), scale);

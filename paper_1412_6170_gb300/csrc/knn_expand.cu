@@ -52,7 +52,6 @@ struct ExpandArgs {
 // there.  Once some lane holds kFlushAt of them, every lane merges its newest
 // kBatch into its sorted register list -- one batch, not the whole buffer, so
 // that lanes that buffer slowly fill their batches before they are merged.
-constexpr int kBatch = 8;
 constexpr int kBufCap = 32;
 constexpr int kFlushAt = kBufCap - kBatch;
 constexpr int kWarps = 4;  // warps per block
@@ -64,41 +63,6 @@ struct WarpSmem {
     int2 lrg[32];                                // its objects [x, y)
     int2 lc[32];                                 // leaves [x, y) of the lane's cell
 };
-
-__device__ __forceinline__ void cmpx(unsigned long long &x, unsigned long long &y) {
-    const bool s = y < x;
-    const unsigned long long lo = s ? y : x;
-    y = s ? x : y;
-    x = lo;
-}
-
-// Sort 8 keys ascending (19 comparators, depth 6).
-__device__ __forceinline__ void sort8(unsigned long long (&b)[kBatch]) {
-    cmpx(b[0], b[2]); cmpx(b[1], b[3]); cmpx(b[4], b[6]); cmpx(b[5], b[7]);
-    cmpx(b[0], b[4]); cmpx(b[1], b[5]); cmpx(b[2], b[6]); cmpx(b[3], b[7]);
-    cmpx(b[0], b[1]); cmpx(b[2], b[3]); cmpx(b[4], b[5]); cmpx(b[6], b[7]);
-    cmpx(b[2], b[4]); cmpx(b[3], b[5]);
-    cmpx(b[1], b[4]); cmpx(b[3], b[6]);
-    cmpx(b[1], b[2]); cmpx(b[3], b[4]); cmpx(b[5], b[6]);
-}
-
-// a (KC keys, ascending) := the KC smallest of a and b (8 keys, ascending):
-// c_i = min(a_i, b_{KC-1-i}) is bitonic and holds them; a bitonic merger sorts it.
-template <int KC>
-__device__ __forceinline__ void merge_batch(unsigned long long (&a)[KC],
-                                            const unsigned long long (&b)[kBatch]) {
-#pragma unroll
-    for (int i = (KC > kBatch ? KC - kBatch : 0); i < KC; ++i) {
-        const unsigned long long v = b[KC - 1 - i];
-        a[i] = v < a[i] ? v : a[i];
-    }
-#pragma unroll
-    for (int span = KC / 2; span >= 1; span >>= 1) {
-#pragma unroll
-        for (int i = 0; i < KC; ++i)
-            if ((i & span) == 0) cmpx(a[i], a[i + span]);
-    }
-}
 
 template <int KC>
 struct Lane {
@@ -121,12 +85,6 @@ __device__ __forceinline__ void merge_top(Lane<KC> &L, WarpSmem &sm, int lane) {
     L.count = base;
     L.thr = fminf(L.thr, __uint_as_float((uint32_t)(L.lst[KC - 1] >> 32)));
 }
-
-
-
-
-
-
 
 // One packet = one pass of a single loop.  Each iteration (a) merges a batch
 // of the buffers if some lane holds kFlushAt candidates, (b) finds the next objects

@@ -88,6 +88,7 @@ _SIGNATURES = {
     "knn_world_launches": ([_vp, ctypes.POINTER(_i64)], ctypes.c_int),
     "knn_world_set_profiling": ([_vp, _i32], ctypes.c_int),
     "knn_world_set_graphs": ([_vp, _i32], ctypes.c_int),
+    "knn_brute_force": ([_vp, _vp, _i64, _vp, _vp, _vp, _i64, _i32, _vp, _vp, _vp], ctypes.c_int),
     "knn_world_set_index_reuse": ([_vp, _i32, ctypes.c_float], ctypes.c_int),
     "knn_world_index_info": ([_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)], ctypes.c_int),
     "knn_world_record_tick": ([_vp, ctypes.POINTER(knn_tick_args)], ctypes.c_int),
@@ -213,6 +214,23 @@ def knn_world_set_profiling(w: int, enable: bool) -> None:
 
 def knn_world_set_graphs(w: int, enable: bool) -> None:
     _check(lib().knn_world_set_graphs(w, 1 if enable else 0))
+
+
+def knn_brute_force(x_dev, y_dev, n: int, q_id_dev, q_x_dev, q_y_dev, n_q: int, k: int,
+                    out_ids_dev, out_d2_dev, stream: int = 0) -> None:
+    _check(lib().knn_brute_force(x_dev, y_dev, n, q_id_dev, q_x_dev, q_y_dev, n_q, k,
+                                 out_ids_dev, out_d2_dev, stream))
+
+
+def brute_force(x, y, k: int, q_id, q_x=None, q_y=None, stream=None):
+    """knn_brute_force on torch tensors; returns (ids, d2) of shape (n_q, k)."""
+    import torch
+    n_q = int(q_id.shape[0])
+    ids = torch.empty((n_q, k), dtype=torch.int32, device=q_id.device)
+    d2 = torch.empty((n_q, k), dtype=torch.float32, device=q_id.device)
+    knn_brute_force(_ptr(x), _ptr(y), int(x.shape[0]), _ptr(q_id), _ptr(q_x), _ptr(q_y), n_q, k,
+                    _ptr(ids), _ptr(d2), _stream(stream))
+    return ids, d2
 
 
 def knn_world_set_index_reuse(w: int, max_age: int, factor: float = 0.0) -> None:
