@@ -232,8 +232,11 @@ knn_status knn_brute_force(const float *x_dev, const float *y_dev, int64_t n,
  * expansion: the expansion kernel.  1 = packets of up to 32 queries per warp,
  *   each lane keeping its query's list in registers (k <= 64); 2 = one warp
  *   per query, the list in shared memory and the row written by the whole
- *   warp (any k; the paper's coalesced-writes variant, Section 3.3.2).  The
- *   automatic choice is 1 for k <= 32 and 2 above.
+ *   warp (any k; the paper's coalesced-writes variant, Section 3.3.2); 3 =
+ *   the paper's multi-pass form (Section 4.2: first iteration on the query's
+ *   own cell, then alternating left/right Morton sub-visits, one cell per
+ *   iteration; k <= 64), an ablation with the same rows, never recorded in a
+ *   tick graph.  The automatic choice is 1 for k <= 32 and 2 above.
  * Any field set to 0 keeps (or restores) the automatic choice. */
 typedef struct {
     int32_t leaf_capacity;

@@ -58,8 +58,9 @@ Plan make_plan(const World &w, int64_t n_q, int k) {
     p.Gp = clampi(Gp, 0, p.G);
     // one warp per query pays off above k = 32 (measured on 1M uniform objects:
     // k = 64 takes 2.8 ms that way against 3.5 ms in packets)
-    p.wide = w.tuning.expansion == 2 || (w.tuning.expansion != 1 && k > 32) ||
-             k > knnq::kMaxPacketK;
+    p.iterative = w.tuning.expansion == 3 && k <= knnq::kMaxPacketK;
+    p.wide = !p.iterative && (w.tuning.expansion == 2 || (w.tuning.expansion != 1 && k > 32) ||
+                              k > knnq::kMaxPacketK);
     p.reuse_age = w.reuse_age;
     p.reuse_f16 = w.reuse_factor > 0.f ? (int)std::lround(w.reuse_factor * 16.f) : 0;
     return p;
@@ -134,6 +135,7 @@ size_t carve_scratch(World &w, char *base) {
     w.qs_orig = c.take<int32_t>(Q);
     w.qs_key = c.take<uint32_t>(Q);
     w.qs_leaf = c.take<int32_t>(Q);
+    w.nav = c.take<uint32_t>(2 * Q);
     w.qcs = c.take<int32_t>(ncell);
     w.npk = c.take<int32_t>(ncell);
     w.pk_off = c.take<int32_t>(ncell);
@@ -382,10 +384,12 @@ void enqueue_tick(World &w, const knn_tick_args &a, cudaStream_t s, bool marks) 
                                     a.out_ids_dev, a.out_d2_dev, s);
     }
     if (m) mark(w, 4, s);
-    if (a.n_q > 0 && !p.wide) launch_packets(w, p, a.n_q, s);
+    if (a.n_q > 0 && !p.wide && !p.iterative) launch_packets(w, p, a.n_q, s);
     if (m) mark(w, 5, s);
     if (a.n_q > 0) {
-        if (p.wide)
+        if (p.iterative)
+            launch_expand_iter(w, p, a.k, a.n_q, a.out_ids_dev, a.out_d2_dev, s);
+        else if (p.wide)
             launch_expand_wide(w, p, a.k, a.n_q, a.out_ids_dev, a.out_d2_dev, s);
         else
             launch_expand(w, p, a.k, a.n_q, a.out_ids_dev, a.out_d2_dev, s);
@@ -460,8 +464,8 @@ knn_status knn_world_set_tuning(knn_world h, const knn_tuning *t) {
         return fail(KNN_ERR_INVALID, "grid_level outside [0, %d] for this world", h->w.gmax);
     if (t->packet_level < 0 || t->packet_level > knnq::kMaxGridLevel)
         return fail(KNN_ERR_INVALID, "packet_level outside [0, 10]");
-    if (t->expansion < 0 || t->expansion > 2)
-        return fail(KNN_ERR_INVALID, "expansion outside [0, 2]");
+    if (t->expansion < 0 || t->expansion > 3)
+        return fail(KNN_ERR_INVALID, "expansion outside [0, 3]");
     h->w.tuning = *t;
     return KNN_OK;
 }
@@ -472,7 +476,7 @@ knn_status knn_world_get_tuning(knn_world h, int64_t n_q, int32_t k, knn_tuning 
     out->leaf_capacity = p.th;
     out->grid_level = p.G;
     out->packet_level = p.Gp;
-    out->expansion = p.wide ? 2 : 1;
+    out->expansion = p.iterative ? 3 : (p.wide ? 2 : 1);
     return KNN_OK;
 }
 
@@ -487,9 +491,10 @@ knn_status knn_tick(knn_world h, const int32_t *upd_id, const float *upd_x, cons
     cudaSetDevice(w.device);
     cudaStream_t s = (cudaStream_t)stream;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    // a stream the caller is recording gets the kernels themselves
-    if (w.graphs && cudaStreamIsCapturing(s, &cs) == cudaSuccess &&
-        cs == cudaStreamCaptureStatusNone)
+    // a stream the caller is recording gets the kernels themselves; the
+    // iterative ablation (a cooperative launch) is never recorded
+    if (w.graphs && !knnq::plan_for(w, a.n_q, a.k).iterative &&
+        cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone)
         return tick_via_graph(w, a, s);
     cudaGetLastError();
     knnq::enqueue_tick(w, a, s, w.profiling);

@@ -35,7 +35,8 @@ enum Scalar : int { kScalarLeaves = 0, kScalarValidQueries = 1, kScalarPackets =
 
 // Ticket counters (one per single-pass launch site in a tick).
 enum Counter : int { kCtrObjSort = 0, kCtrQuerySort = 4, kCtrLeaves = 8, kCtrQueryScan = 9,
-                     kCtrPacketScan = 10, kCtrExpand = 11, kCtrReuseScan = 12 };
+                     kCtrPacketScan = 10, kCtrExpand = 11, kCtrReuseScan = 12,
+                     kCtrIterLeft = 13 /* and 14: iterative expansion */ };
 
 struct Plan {
     int L;           // max depth (key has 2L bits)
@@ -44,6 +45,7 @@ struct Plan {
     int Gp;          // packet level
     int passes;      // radix passes over 2L bits
     bool wide;       // expansion by one warp per query (else packets)
+    bool iterative;  // expansion in the paper's multi-pass form (an ablation)
     int reuse_age;   // index reuse: rebuild at least every reuse_age ticks (0: every tick)
     int reuse_f16;   // and when the cost proxy grows past reuse_f16 / 16 of its built value
 };
@@ -103,6 +105,7 @@ struct World {
     int32_t *qs_id = nullptr, *qs_orig = nullptr;
     uint32_t *qs_key = nullptr;
     int32_t *qs_leaf = nullptr;  // a leaf at (or next to) each sorted query
+    uint32_t *nav = nullptr;     // iterative expansion: per sorted query, left and right position
     int32_t *qcs = nullptr, *npk = nullptr, *pk_off = nullptr;
     int32_t *pk_start = nullptr, *pk_len = nullptr;
     uint64_t *status = nullptr;
@@ -176,6 +179,8 @@ void launch_export_leaves(World &w, int64_t m, int32_t *level, uint32_t *z, int3
 void launch_expand(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t *out_ids,
                    float *out_d2, cudaStream_t s);
 void launch_expand_wide(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t *out_ids,
+                        float *out_d2, cudaStream_t s);
+void launch_expand_iter(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t *out_ids,
                         float *out_d2, cudaStream_t s);
 
 int num_sms(int device);

@@ -76,7 +76,7 @@ def test_large_k_clustered_subset_sampled(k):
     run_and_compare(w, k_max=512, sample=3000, what=f"120k clustered k={k}")
 
 
-@pytest.mark.parametrize("expansion", [1, 2])
+@pytest.mark.parametrize("expansion", [1, 2, 3])
 @pytest.mark.parametrize("k", [1, 16, 64])
 def test_expansion_kernels_agree(k, expansion):
     w = synth.skewed_moving(n=40000, k=k, ticks=2, seed=23, query_frac=0.5)
@@ -217,7 +217,8 @@ def test_invalid_queries_padded_and_reported():
     assert bits & knnq.ERR_BAD_QUERY
 
 
-def test_explicit_and_anonymous_centres_outside_domain():
+@pytest.mark.parametrize("expansion", [0, 2, 3])
+def test_explicit_and_anonymous_centres_outside_domain(expansion):
     r = np.random.default_rng(6)
     n = 20000
     x, y = r.random(n).astype(np.float32), r.random(n).astype(np.float32)
@@ -228,7 +229,8 @@ def test_explicit_and_anonymous_centres_outside_domain():
     qx = (r.random(nq) * 1.4 - 0.2).astype(np.float32)
     qy = (r.random(nq) * 1.4 - 0.2).astype(np.float32)
     qx[:50] = 7.5
-    compare_ticks(x, y, [tick(qid, 16, None, qx, qy), tick(qid[::2], 3, None, qx[::2], qy[::2])])
+    compare_ticks(x, y, [tick(qid, 16, None, qx, qy), tick(qid[::2], 3, None, qx[::2], qy[::2])],
+                  tuning=dict(expansion=expansion) if expansion else None)
 
 
 def test_repeated_query_ids_and_empty_tick():
