@@ -331,6 +331,45 @@ def index_reuse_vs_rebuild(dev, ticks=20, max_age=8):
             "per_mode": out, "rows_identical": same}
 
 
+def expansion_ablation(dev, ticks=3):
+    """The headline workload's expansion in each form: packets (the default for
+    k = 16), one warp per query, and the paper's multi-pass iterative form; tick
+    times and whether the rows agree."""
+    import torch
+
+    from paper_1412_6170_gb300 import knnq, synth
+    wl = synth.plain_uniform_moving(n=N_OBJ, k=K, ticks=2, seed=5)
+    ids = torch.from_numpy(wl.ticks[0].upd_id).to(dev)
+    ux = [torch.from_numpy(t.upd_x).to(dev) for t in wl.ticks]
+    uy = [torch.from_numpy(t.upd_y).to(dev) for t in wl.ticks]
+    stream = torch.cuda.current_stream()
+    out, rows = {}, {}
+    for name, exp in (("packets", 1), ("warp per query", 2), ("multi-pass iterative", 3)):
+        x0, y0 = torch.from_numpy(wl.x0).to(dev), torch.from_numpy(wl.y0).to(dev)
+        world = knnq.World(x0, y0, k_max=K, max_queries=N_OBJ)
+        world.set_tuning(expansion=exp)
+        world.set_profiling(True)
+        oi = torch.empty((N_OBJ, K), dtype=torch.int32, device=dev)
+        od = torch.empty((N_OBJ, K), dtype=torch.float32, device=dev)
+        try:
+            world.tick(K, ids, ids, ux[0], uy[0], out_ids=oi, out_d2=od)
+            tick_ms, exp_ms = [], []
+            for i in range(ticks):
+                world.tick(K, ids, ids, ux[1 - i % 2], uy[1 - i % 2], out_ids=oi, out_d2=od)
+                st = world.stage_times()
+                tick_ms.append(sum(st.values()))
+                exp_ms.append(st["expand"])
+            out[name] = {"tick_ms": min(tick_ms), "expand_ms": min(exp_ms)}
+            rows[name] = (oi.cpu(), od.cpu())
+        finally:
+            world.close()
+    base = rows["packets"]
+    for name, (a, b) in rows.items():
+        out[name]["rows_identical_to_packets"] = bool(
+            torch.equal(a, base[0]) and torch.equal(b.view(torch.int32), base[1].view(torch.int32)))
+    return {"workload": f"{WORKLOAD}; {ticks} ticks per form", "per_form": out}
+
+
 def brute_vs_indexed(dev, n_sample=16384):
     """The GPU brute-force baseline (every query against every object, as in the
     paper's comparison) against the indexed tick: on the 10k uniform k=8 world (all
@@ -697,6 +736,7 @@ def run_gpu(args):
         line["k_sweep"] = k_sweep(dev)
         line["index_reuse"] = index_reuse_vs_rebuild(dev)
         line["brute_force"] = brute_vs_indexed(dev)
+        line["expansion_ablation"] = expansion_ablation(dev)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
     print(json.dumps(line), flush=True)
