@@ -736,36 +736,41 @@ static void scan_excl(World &w, const int32_t *in, int32_t *out, int64_t len, in
 // ordered by the issuer's place in the sorted object order (a counting sort),
 // which is the Morton order of their centres.
 
+// Counting sort, first half: every valid query counts one more query at its
+// issuer's sorted place p and keeps p and its rank among the queries of that
+// issuer (the count before its own).
 __global__ void k_query_count(const int32_t *__restrict__ q_id, int64_t n_q, int64_t n,
                               const int32_t *__restrict__ inv, int32_t *qcnt, int k,
-                              int32_t *out_ids, float *out_d2, uint32_t *err) {
+                              int32_t *out_ids, float *out_d2, uint32_t *err,
+                              int32_t *__restrict__ qp, int32_t *__restrict__ qrank) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_q;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t s = q_id[i];
         if (s < 0 || s >= n) {
             atomicOr(err, kErrBadQuery);
+            qp[i] = -1;
             for (int r = 0; r < k; ++r) {
                 out_ids[i * k + r] = -1;
                 out_d2[i * k + r] = __int_as_float(0x7f800000);
             }
             continue;
         }
-        atomicAdd(&qcnt[inv[s]], 1);
+        const int32_t p = inv[s];
+        qp[i] = p;
+        qrank[i] = atomicAdd(&qcnt[p], 1);
     }
 }
 
-// Counting sort, second half: every valid query takes one slot of its
-// issuer's range [qoff[p], qoff[p+1]) (the count drops back to zero) and
-// records its caller index there.
-__global__ void k_query_place(const int32_t *__restrict__ q_id, int64_t n_q, int64_t n,
-                              const int32_t *__restrict__ inv, const int32_t *__restrict__ qoff,
-                              int32_t *qcnt, int32_t *qs_orig) {
+// Counting sort, second half: every valid query takes the slot of its rank in
+// its issuer's range [qoff[p], qoff[p+1]) and records its caller index there.
+__global__ void k_query_place(int64_t n_q, int64_t n, const int32_t *__restrict__ qp,
+                              const int32_t *__restrict__ qrank,
+                              const int32_t *__restrict__ qoff, int32_t *qs_orig) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_q;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t s = q_id[i];
-        if (s < 0 || s >= n) continue;
-        const int32_t p = inv[s];
-        const int32_t j = qoff[p] + atomicSub(&qcnt[p], 1) - 1;
+        const int32_t p = qp[i];
+        if (p < 0 || p >= n) continue;
+        const int32_t j = qoff[p] + qrank[i];
         if (j < 0 || j >= n_q) continue;  // only after a timed-out look-back
         qs_orig[j] = (int32_t)i;
     }
@@ -800,11 +805,16 @@ __global__ void k_query_fill(int64_t n, int64_t n_q, const int32_t *__restrict__
 
 void launch_queries_at_issuers(World &w, const Plan &p, const int32_t *q_id, int64_t n_q,
                                int32_t k, int32_t *out_ids, float *out_d2, cudaStream_t s) {
+    // each query's sorted place and rank live in the sort's second buffers,
+    // free once the leaf-ordered store is written
+    const int r = p.passes & 1;
+    int32_t *qp = reinterpret_cast<int32_t *>(w.key[r ^ 1]), *qrank = w.val[r ^ 1];
     cudaMemsetAsync(w.qcnt, 0, sizeof(int32_t) * (size_t)(w.n + 1), s);
     const int g = grid_for(n_q, 256, num_sms(w.device) * 8);
-    k_query_count<<<g, 256, 0, s>>>(q_id, n_q, w.n, w.inv, w.qcnt, k, out_ids, out_d2, w.err);
+    k_query_count<<<g, 256, 0, s>>>(q_id, n_q, w.n, w.inv, w.qcnt, k, out_ids, out_d2, w.err,
+                                    qp, qrank);
     scan_excl(w, w.qcnt, w.qoff, w.n + 1, w.scalars + kScalarValidQueries, kCtrQueryScan, s);
-    k_query_place<<<g, 256, 0, s>>>(q_id, n_q, w.n, w.inv, w.qoff, w.qcnt, w.qs_orig);
+    k_query_place<<<g, 256, 0, s>>>(n_q, w.n, qp, qrank, w.qoff, w.qs_orig);
     const uint32_t *skey = w.key[p.passes & 1];
     k_query_fill<<<grid_for(w.n, 256, num_sms(w.device) * 8), 256, 0, s>>>(
         w.n, n_q, w.qoff, w.xs, w.ys, w.sid, skey, w.obj_leaf, w.qs_x, w.qs_y, w.qs_id,
