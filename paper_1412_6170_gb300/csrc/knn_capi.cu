@@ -150,6 +150,11 @@ size_t carve_scratch(World &w, char *base) {
 }
 
 void world_attach_scratch(World &w, void *base, cudaStream_t s) {
+    // recorded tick graphs point into the old scratch
+    for (TickGraph &t : w.tick_graph) {
+        if (t.exec) cudaGraphExecDestroy(t.exec);
+        t.exec = nullptr;
+    }
     w.arena = base;
     carve_scratch(w, static_cast<char *>(base));
     cudaMemsetAsync(w.scalars, 0, sizeof(int32_t) * kNumScalars, s);
@@ -341,6 +346,20 @@ void mark(World &w, int i, cudaStream_t s) {
 }  // namespace
 
 namespace knnq {
+knn_status tick_launch(World &w, const knn_tick_args &a, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    // a stream the caller is recording gets the kernels themselves; the
+    // iterative ablation (a cooperative launch) is never recorded
+    if (w.graphs && !plan_for(w, a.n_q, a.k).iterative &&
+        cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone)
+        return tick_via_graph(w, a, s);
+    cudaGetLastError();
+    enqueue_tick(w, a, s, w.profiling);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "tick launch");
+    return KNN_OK;
+}
+
 // Lets other translation units of the library report through knn_last_error.
 void set_last_error(const char *msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
 
@@ -489,18 +508,7 @@ knn_status knn_tick(knn_world h, const int32_t *upd_id, const float *upd_x, cons
     if (st != KNN_OK) return st;
     World &w = h->w;
     cudaSetDevice(w.device);
-    cudaStream_t s = (cudaStream_t)stream;
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    // a stream the caller is recording gets the kernels themselves; the
-    // iterative ablation (a cooperative launch) is never recorded
-    if (w.graphs && !knnq::plan_for(w, a.n_q, a.k).iterative &&
-        cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone)
-        return tick_via_graph(w, a, s);
-    cudaGetLastError();
-    knnq::enqueue_tick(w, a, s, w.profiling);
-    const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "knn_tick launch");
-    return KNN_OK;
+    return knnq::tick_launch(w, a, (cudaStream_t)stream);
 }
 
 knn_status knn_tick_host(knn_world h, const int32_t *upd_id, const float *upd_x,

@@ -208,6 +208,8 @@ knn_status check_tick_args(const World &w, const knn_tick_args &a, const char *w
 // Enqueue every stage of one tick on s; `marks` records stage events when
 // the world's profiling is on.
 void enqueue_tick(World &w, const knn_tick_args &a, cudaStream_t s, bool marks);
+// One tick through the world's graph cache when graphs are on (else direct).
+knn_status tick_launch(World &w, const knn_tick_args &a, cudaStream_t s);
 // The index / expansion parameters a tick with n_q queries and this k uses.
 Plan plan_for(const World &w, int64_t n_q, int k);
 
