@@ -102,7 +102,12 @@ knn_status knn_tick(knn_world w, const int32_t *upd_id_dev, const float *upd_x_d
                     const float *q_x_dev, const float *q_y_dev, int64_t n_q, int32_t k,
                     int32_t *out_ids_dev, float *out_d2_dev, void *stream);
 
-/* Arguments of one world's tick, as for knn_tick (device pointers). */
+/* Arguments of one world's tick, as for knn_tick (device pointers), plus
+ * q_k_dev: NULL, or n_q per-query list sizes (Section 2.1: a query is
+ * q = (x, y, k)).  Query i then gets the q_k_dev[i] nearest objects in the
+ * first entries of its row (still k wide) and padding after them; 0 gives an
+ * all-padding row, a value outside [0, k] a padded row and the invalid-query
+ * bit of knn_tick_status. */
 typedef struct {
     const int32_t *upd_id_dev;
     const float *upd_x_dev, *upd_y_dev;
@@ -113,7 +118,11 @@ typedef struct {
     int32_t k;
     int32_t *out_ids_dev;
     float *out_d2_dev;
+    const int32_t *q_k_dev;
 } knn_tick_args;
+
+/* knn_tick from an argument struct (which adds per-query list sizes). */
+knn_status knn_tick_ex(knn_world w, const knn_tick_args *args, void *stream);
 
 /* The same tick with every array in host memory (pageable or pinned): the
  * inputs are copied to world-owned device staging buffers, the tick runs on

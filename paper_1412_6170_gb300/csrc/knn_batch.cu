@@ -170,7 +170,7 @@ extern "C" knn_status knn_world_autotune(knn_world h, const int32_t *q_id_dev,
     if (!h) return bad(KNN_ERR_INVALID, "knn_world_autotune: NULL world");
     World &w = h->w;
     knn_tick_args a{nullptr, nullptr, nullptr, 0, q_id_dev, q_x_dev, q_y_dev, n_q, k,
-                    out_ids_dev, out_d2_dev};
+                    out_ids_dev, out_d2_dev, nullptr};
     knn_status st = knnq::check_tick_args(w, a, "knn_world_autotune");
     if (st != KNN_OK) return st;
     if (trials < 1) trials = 1;

@@ -407,11 +407,11 @@ void enqueue_tick(World &w, const knn_tick_args &a, cudaStream_t s, bool marks) 
     if (m) mark(w, 5, s);
     if (a.n_q > 0) {
         if (p.iterative)
-            launch_expand_iter(w, p, a.k, a.n_q, a.out_ids_dev, a.out_d2_dev, s);
+            launch_expand_iter(w, p, a.k, a.n_q, a.out_ids_dev, a.out_d2_dev, a.q_k_dev, s);
         else if (p.wide)
-            launch_expand_wide(w, p, a.k, a.n_q, a.out_ids_dev, a.out_d2_dev, s);
+            launch_expand_wide(w, p, a.k, a.n_q, a.out_ids_dev, a.out_d2_dev, a.q_k_dev, s);
         else
-            launch_expand(w, p, a.k, a.n_q, a.out_ids_dev, a.out_d2_dev, s);
+            launch_expand(w, p, a.k, a.n_q, a.out_ids_dev, a.out_d2_dev, a.q_k_dev, s);
     }
     if (m) mark(w, 6, s);
     w.last_stream = s;
@@ -503,12 +503,22 @@ knn_status knn_tick(knn_world h, const int32_t *upd_id, const float *upd_x, cons
                     int64_t n_upd, const int32_t *q_id, const float *q_x, const float *q_y,
                     int64_t n_q, int32_t k, int32_t *out_ids, float *out_d2, void *stream) {
     if (!h) return fail(KNN_ERR_INVALID, "knn_tick: NULL world");
-    knn_tick_args a{upd_id, upd_x, upd_y, n_upd, q_id, q_x, q_y, n_q, k, out_ids, out_d2};
+    knn_tick_args a{upd_id, upd_x, upd_y, n_upd, q_id, q_x, q_y, n_q, k, out_ids, out_d2,
+                    nullptr};
     const knn_status st = knnq::check_tick_args(h->w, a, "knn_tick");
     if (st != KNN_OK) return st;
     World &w = h->w;
     cudaSetDevice(w.device);
     return knnq::tick_launch(w, a, (cudaStream_t)stream);
+}
+
+knn_status knn_tick_ex(knn_world h, const knn_tick_args *args, void *stream) {
+    if (!h || !args) return fail(KNN_ERR_INVALID, "knn_tick_ex: NULL argument");
+    const knn_status st = knnq::check_tick_args(h->w, *args, "knn_tick_ex");
+    if (st != KNN_OK) return st;
+    World &w = h->w;
+    cudaSetDevice(w.device);
+    return knnq::tick_launch(w, *args, (cudaStream_t)stream);
 }
 
 knn_status knn_tick_host(knn_world h, const int32_t *upd_id, const float *upd_x,

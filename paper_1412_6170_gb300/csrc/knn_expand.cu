@@ -42,6 +42,8 @@ struct ExpandArgs {
     float spec2;  // alpha^2 of the speculative first threshold (0: none)
     int L, G, k;
     int vec_out;  // rows may be written with 16-byte stores
+    const int32_t *q_k;  // per-query list sizes by caller index (NULL: all k)
+    uint32_t *err;
     int64_t n, n_q, pk_cap;
     int64_t leaf_cap;  // room for leaves (m <= leaf_cap)
 };
@@ -131,6 +133,15 @@ __global__ void __launch_bounds__(kWarps * 32) k_expand(const ExpandArgs g) {
         // id + 1 of the issuer (excluded); 0 matches no object
         const int32_t self = active ? g.qs_id[j] + 1 : 0;
         if (__ballot_sync(kFull, active) == 0u) continue;
+        // this query's list size (Section 2.1, q = (x, y, k)); 0: no neighbours
+        int kq = k;
+        if (g.q_k && active) {
+            kq = g.q_k[orig];
+            if (kq < 0 || kq > k) {
+                atomicOr(g.err, kErrBadQuery);
+                kq = 0;
+            }
+        }
 
         // phase 1: the packet's own leaves, widened along the leaf order
         int32_t b_lo = g.qs_leaf[q0];
@@ -164,10 +175,17 @@ __global__ void __launch_bounds__(kWarps * 32) k_expand(const ExpandArgs g) {
             spec = g.spec2 * (float)k * area * g.side * g.side / (3.14159265f * cnt1);
         }
 
+        // the same rule for this lane's own list size
+        float spec_q = spec;
+        if (g.q_k && spec < kInf)
+            spec_q = kq > 0 ? spec * ((1.f + 3.f / sqrtf((float)kq) + 2.f / (float)kq) *
+                                      (float)kq) / (g.spec2 * (float)k)
+                            : -kInf;
+
         Lane<KC> L;
 #pragma unroll
-        for (int i = 0; i < KC; ++i) L.lst[i] = i < KC - k ? 0ull : kPad;
-        L.thr = active ? spec : -kInf;  // inactive lanes never buffer anything
+        for (int i = 0; i < KC; ++i) L.lst[i] = i < KC - kq ? 0ull : kPad;
+        L.thr = active && kq > 0 ? spec_q : -kInf;  // other lanes never buffer anything
         L.count = 0;
 
         int32_t cur, end;                     // objects to test
@@ -339,12 +357,12 @@ __global__ void __launch_bounds__(kWarps * 32) k_expand(const ExpandArgs g) {
         // with four times the threshold, then with none; lanes that are done take
         // no part in the later walks
         if (attempt < 2 && spec < kInf) {
-            const bool redo = active && L.lst[KC - 1] == kPad;
+            const bool redo = active && kq > 0 && L.lst[KC - 1] == kPad;
             if (__any_sync(kFull, redo)) {
                 if (redo) {
 #pragma unroll
-                    for (int i = 0; i < KC; ++i) L.lst[i] = i < KC - k ? 0ull : kPad;
-                    L.thr = attempt == 0 ? 4.f * spec : kInf;
+                    for (int i = 0; i < KC; ++i) L.lst[i] = i < KC - kq ? 0ull : kPad;
+                    L.thr = attempt == 0 ? 4.f * spec_q : kInf;
                 } else {
                     L.thr = -kInf;
                 }
@@ -361,8 +379,10 @@ __global__ void __launch_bounds__(kWarps * 32) k_expand(const ExpandArgs g) {
             constexpr int S = KC + 4;  // row stride (words); rows stay 16-byte aligned
             uint32_t *rows = reinterpret_cast<uint32_t *>(&sm.buf[0][0]);
             int32_t *s_orig = reinterpret_cast<int32_t *>(&sm.obj[0]);
+            int32_t *s_kq = s_orig + 32;
             __syncwarp();
             s_orig[lane] = active ? orig : -1;
+            s_kq[lane] = kq;
             const int vw = g.vec_out ? 4 : 1;
             const int per_row = k / vw;
             const int total = ql * per_row;
@@ -390,13 +410,15 @@ __global__ void __launch_bounds__(kWarps * 32) k_expand(const ExpandArgs g) {
                         const int c = (v - row * per_row) * vw;
                         const int32_t o = s_orig[row];
                         if (o >= 0) {
-                            const uint32_t *src = rows + row * S + (KC - k) + c;
                             uint32_t *dst = out + (int64_t)o * k + c;
-                            if (vw == 4)
+                            if (vw == 4) {  // every row holds k entries
                                 *reinterpret_cast<uint4 *>(dst) =
-                                    *reinterpret_cast<const uint4 *>(src);
-                            else
-                                *dst = *src;
+                                    *reinterpret_cast<const uint4 *>(rows + row * S + (KC - k) + c);
+                            } else {
+                                const int kr = s_kq[row];  // entries past it are padding
+                                *dst = c < kr ? rows[row * S + (KC - kr) + c]
+                                              : (pass == 0 ? 0xFFFFFFFFu : 0x7f800000u);
+                            }
                         }
                     }
                 }
@@ -408,11 +430,15 @@ __global__ void __launch_bounds__(kWarps * 32) k_expand(const ExpandArgs g) {
                 float *od = g.out_d2 + (int64_t)orig * k;
 #pragma unroll
                 for (int i = 0; i < KC; ++i) {
-                    if (i >= KC - k) {
-                        const int rr = i - (KC - k);
+                    const int rr = i - (KC - kq);
+                    if (rr >= 0) {
                         oi[rr] = key_id(L.lst[i]);
                         od[rr] = __uint_as_float((uint32_t)(L.lst[i] >> 32));
                     }
+                }
+                for (int rr = kq; rr < k; ++rr) {  // padding after a shorter list
+                    oi[rr] = -1;
+                    od[rr] = kInf;
                 }
             }
         }
@@ -447,7 +473,7 @@ static void run(const ExpandArgs &a, int device, cudaStream_t s) {
 }
 
 void launch_expand(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t *out_ids,
-                   float *out_d2, cudaStream_t s) {
+                   float *out_d2, const int32_t *q_k, cudaStream_t s) {
     if (n_q <= 0) return;
     ExpandArgs a;
     a.xs = w.xs;
@@ -484,8 +510,11 @@ void launch_expand(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t *out
     a.leaf_cap = w.leaf_cap;
     a.n_q = n_q;
     a.pk_cap = packet_capacity(w);
-    a.vec_out = k % 4 == 0 && ((reinterpret_cast<uintptr_t>(out_ids) |
-                                reinterpret_cast<uintptr_t>(out_d2)) & 15u) == 0;
+    a.vec_out = q_k == nullptr && k % 4 == 0 &&
+                ((reinterpret_cast<uintptr_t>(out_ids) | reinterpret_cast<uintptr_t>(out_d2)) &
+                 15u) == 0;
+    a.q_k = q_k;
+    a.err = w.err;
     if (k <= 4) run<4>(a, w.device, s);
     else if (k <= 8) run<8>(a, w.device, s);
     else if (k <= 16) run<16>(a, w.device, s);

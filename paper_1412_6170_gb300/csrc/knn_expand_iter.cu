@@ -44,6 +44,8 @@ struct IterArgs {
     float pad;  // outward move of interior quadrant edges (a few ulps of the coordinates)
     int G, k;
     int64_t n_q;
+    const int32_t *q_k;  // per-query list sizes by caller index (NULL: all k)
+    uint32_t *err;
 };
 
 constexpr uint32_t kNavDone = 0xFFFFFFFFu;
@@ -166,18 +168,21 @@ __device__ uint32_t next_cell(uint32_t from, int dir, float qx, float qy, float 
     }
 }
 
+// The query's list, kept in its row (k wide; the first kq entries are the
+// list, the rest padding), as kq keys after KC - kq zero slots.
 template <int KC>
 __device__ __forceinline__ void load_row(unsigned long long (&lst)[KC], int32_t orig, int k,
-                                         const IterArgs &g) {
+                                         int kq, const IterArgs &g) {
     const int32_t *oi = g.out_ids + (int64_t)orig * k;
     const float *od = g.out_d2 + (int64_t)orig * k;
 #pragma unroll
     for (int i = 0; i < KC; ++i) {
-        if (i < KC - k) {
+        const int r = i - (KC - kq);
+        if (r < 0) {
             lst[i] = 0ull;
         } else {
-            const int32_t id = oi[i - (KC - k)];
-            lst[i] = ((unsigned long long)__float_as_uint(od[i - (KC - k)]) << 32) |
+            const int32_t id = oi[r];
+            lst[i] = ((unsigned long long)__float_as_uint(od[r]) << 32) |
                      (uint32_t)(id < 0 ? 0xFFFFFFFFu : (uint32_t)(id + 1));
         }
     }
@@ -185,16 +190,28 @@ __device__ __forceinline__ void load_row(unsigned long long (&lst)[KC], int32_t 
 
 template <int KC>
 __device__ __forceinline__ void store_row(const unsigned long long (&lst)[KC], int32_t orig,
-                                          int k, const IterArgs &g) {
+                                          int k, int kq, const IterArgs &g) {
     int32_t *oi = g.out_ids + (int64_t)orig * k;
     float *od = g.out_d2 + (int64_t)orig * k;
 #pragma unroll
     for (int i = 0; i < KC; ++i) {
-        if (i >= KC - k) {
-            oi[i - (KC - k)] = key_id(lst[i]);
-            od[i - (KC - k)] = __uint_as_float((uint32_t)(lst[i] >> 32));
+        const int r = i - (KC - kq);
+        if (r >= 0) {
+            oi[r] = key_id(lst[i]);
+            od[r] = __uint_as_float((uint32_t)(lst[i] >> 32));
         }
     }
+}
+
+// This query's list size (Section 2.1, q = (x, y, k)); 0: no neighbours.
+__device__ __forceinline__ int query_k(int32_t orig, const IterArgs &g) {
+    if (!g.q_k) return g.k;
+    const int kq = g.q_k[orig];
+    if (kq < 0 || kq > g.k) {
+        atomicOr(g.err, kErrBadQuery);
+        return 0;
+    }
+    return kq;
 }
 
 template <int KC>
@@ -216,13 +233,23 @@ __global__ void __launch_bounds__(128) k_expand_iter(const IterArgs g) {
             continue;
         }
         const float qx = g.qs_x[j], qy = g.qs_y[j];
+        const int kq = query_k(orig, g);
+        // padding after the list (and the whole row when kq is 0)
+        for (int r = kq; r < k; ++r) {
+            g.out_ids[(int64_t)orig * k + r] = -1;
+            g.out_d2[(int64_t)orig * k + r] = __int_as_float(0x7f800000);
+        }
+        if (kq == 0) {
+            g.nav[2 * j] = g.nav[2 * j + 1] = kNavDone;
+            continue;
+        }
         const uint32_t c = interleave((uint32_t)cell_g(qx, g.x0, g.scale_g, g.G),
                                       (uint32_t)cell_g(qy, g.y0, g.scale_g, g.G));
         unsigned long long lst[KC];
 #pragma unroll
-        for (int i = 0; i < KC; ++i) lst[i] = i < KC - k ? 0ull : kPad;
+        for (int i = 0; i < KC; ++i) lst[i] = i < KC - kq ? 0ull : kPad;
         scan_cell<KC>(c, qx, qy, g.qs_id[j] + 1, m, lst, g);
-        store_row<KC>(lst, orig, k, g);
+        store_row<KC>(lst, orig, k, kq, g);
         g.nav[2 * j] = c;
         g.nav[2 * j + 1] = c;
     }
@@ -239,14 +266,15 @@ __global__ void __launch_bounds__(128) k_expand_iter(const IterArgs g) {
             if (from == kNavDone) continue;
             const int32_t orig = g.qs_orig[j];
             const float qx = g.qs_x[j], qy = g.qs_y[j];
+            const int kq = g.q_k ? g.q_k[orig] : k;  // checked in the first iteration
             unsigned long long lst[KC];
-            load_row<KC>(lst, orig, k, g);
+            load_row<KC>(lst, orig, k, kq, g);
             const float thr = __uint_as_float((uint32_t)(lst[KC - 1] >> 32));
             const uint32_t c = next_cell(from, dir, qx, qy, thr, g);
             g.nav[2 * j + dir] = c;
             if (c == kNavDone) continue;
             scan_cell<KC>(c, qx, qy, g.qs_id[j] + 1, m, lst, g);
-            store_row<KC>(lst, orig, k, g);
+            store_row<KC>(lst, orig, k, kq, g);
             ++found;
         }
         if (found) atomicAdd(g.counters + dir, found);
@@ -272,7 +300,7 @@ static void run_iter(const IterArgs &a, int device, cudaStream_t s) {
 }
 
 void launch_expand_iter(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t *out_ids,
-                        float *out_d2, cudaStream_t s) {
+                        float *out_d2, const int32_t *q_k, cudaStream_t s) {
     if (n_q <= 0) return;
     IterArgs a;
     a.xs = w.xs;
@@ -298,6 +326,8 @@ void launch_expand_iter(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t
     a.G = p.G;
     a.k = k;
     a.n_q = n_q;
+    a.q_k = q_k;
+    a.err = w.err;
     if (k <= 4) run_iter<4>(a, w.device, s);
     else if (k <= 8) run_iter<8>(a, w.device, s);
     else if (k <= 16) run_iter<16>(a, w.device, s);

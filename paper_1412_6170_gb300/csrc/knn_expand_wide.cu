@@ -37,10 +37,12 @@ struct WideArgs {
     int32_t *out_ids;
     float *out_d2;
     float x0, y0, scale_g, side;
-    float spec2;  // alpha^2 of the speculative first threshold (0: none)
+    float spec2;  // > 0: start from the speculative threshold (alpha^2 from the query's k)
     int G, k;
     int64_t n, n_q;
     int64_t leaf_cap;  // room for leaves (m <= leaf_cap)
+    const int32_t *q_k;  // per-query list sizes by caller index (NULL: all k)
+    uint32_t *err;
 };
 
 constexpr int kWideWarps = 4;  // warps per block
@@ -96,6 +98,22 @@ __global__ void __launch_bounds__(kWideWarps * 32) k_expand_wide(const WideArgs 
         if (orig < 0) continue;
         const float qx = g.qs_x[j], qy = g.qs_y[j];
         const int32_t self = g.qs_id[j] + 1;  // id + 1 of the issuer; 0 matches nothing
+        // this query's list size (Section 2.1, q = (x, y, k)); 0: no neighbours
+        int kq = k;
+        if (g.q_k) {
+            kq = g.q_k[orig];
+            if (kq < 0 || kq > k) {
+                if (lane == 0) atomicOr(g.err, kErrBadQuery);
+                kq = 0;
+            }
+        }
+        if (kq == 0) {
+            for (int r = lane; r < k; r += 32) {
+                g.out_ids[(int64_t)orig * k + r] = -1;
+                g.out_d2[(int64_t)orig * k + r] = kInf;
+            }
+            continue;
+        }
 
         // the query's own leaves, widened along the leaf order to >= k + 1 objects
         int32_t b_lo = g.qs_leaf[j];
@@ -105,7 +123,7 @@ __global__ void __launch_bounds__(kWideWarps * 32) k_expand_wide(const WideArgs 
             bool left = true;
             for (;;) {
                 const int32_t cnt = g.bstart[b_hi] - g.bstart[b_lo];
-                if (cnt >= k + 1 || (b_lo == 0 && b_hi == m)) break;
+                if (cnt >= kq + 1 || (b_lo == 0 && b_hi == m)) break;
                 if ((left && b_lo > 0) || b_hi == m) --b_lo;
                 else ++b_hi;
                 left = !left;
@@ -118,7 +136,8 @@ __global__ void __launch_bounds__(kWideWarps * 32) k_expand_wide(const WideArgs 
                 area += ldexpf(1.f, -2 * (int)g.blevel[b]);
             area = warp_sum(area);
             const float cnt1 = (float)(g.bstart[b_hi] - g.bstart[b_lo]);
-            spec = g.spec2 * (float)k * area * g.side * g.side / (3.14159265f * cnt1);
+            const float a2 = 1.f + 3.f / sqrtf((float)kq) + 2.f / (float)kq;
+            spec = a2 * (float)kq * area * g.side * g.side / (3.14159265f * cnt1);
         }
         const int ccx = cell_g(qx, g.x0, g.scale_g, g.G);
         const int ccy = cell_g(qy, g.y0, g.scale_g, g.G);
@@ -193,8 +212,8 @@ __global__ void __launch_bounds__(kWideWarps * 32) k_expand_wide(const WideArgs 
                             if (count + __popc(pm) > B) {
                                 // full: keep the k smallest; the k-th bounds the rest
                                 warp_sort_keys(buf, count, B, lane);
-                                if (count > k) count = k;
-                                thr = fminf(thr, __uint_as_float((uint32_t)(buf[k - 1] >> 32)));
+                                if (count > kq) count = kq;
+                                thr = fminf(thr, __uint_as_float((uint32_t)(buf[kq - 1] >> 32)));
                                 pass = pass && d <= thr;
                                 pm = __ballot_sync(kFull, pass);
                             }
@@ -208,7 +227,7 @@ __global__ void __launch_bounds__(kWideWarps * 32) k_expand_wide(const WideArgs 
                 }
             }
             // every object within thr is in the buffer (or was cut for k smaller ones)
-            if (count >= k || !(thr < kInf) || attempt >= 2) break;
+            if (count >= kq || !(thr < kInf) || attempt >= 2) break;
         }
 
         // a8: the row, in caller order, written by the whole warp
@@ -216,7 +235,7 @@ __global__ void __launch_bounds__(kWideWarps * 32) k_expand_wide(const WideArgs 
         int32_t *oi = g.out_ids + (int64_t)orig * k;
         float *od = g.out_d2 + (int64_t)orig * k;
         for (int r = lane; r < k; r += 32) {
-            const unsigned long long key = r < count ? buf[r] : kPad;
+            const unsigned long long key = r < count && r < kq ? buf[r] : kPad;
             oi[r] = key_id(key);
             od[r] = __uint_as_float((uint32_t)(key >> 32));
         }
@@ -252,7 +271,7 @@ static void run_wide(const WideArgs &a, int device, cudaStream_t s) {
 }
 
 void launch_expand_wide(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t *out_ids,
-                        float *out_d2, cudaStream_t s) {
+                        float *out_d2, const int32_t *q_k, cudaStream_t s) {
     if (n_q <= 0) return;
     WideArgs a;
     a.xs = w.xs;
@@ -277,11 +296,13 @@ void launch_expand_wide(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t
     a.side = w.desc.side;
     a.scale_g = ldexpf(w.scale, -(p.L - p.G));
     // the same first-threshold rule as the packet kernel
-    a.spec2 = 1.0f + 3.0f / sqrtf((float)k) + 2.0f / (float)k;
+    a.spec2 = 1.0f;
     a.G = p.G;
     a.k = k;
     a.n = w.n;
     a.leaf_cap = w.leaf_cap;
+    a.q_k = q_k;
+    a.err = w.err;
     a.n_q = n_q;
     if (k <= 64) run_wide<64>(a, w.device, s);
     else if (k <= 128) run_wide<128>(a, w.device, s);

@@ -177,11 +177,11 @@ void launch_export_leaves(World &w, int64_t m, int32_t *level, uint32_t *z, int3
 
 // ---- launcher (knn_expand.cu) -----------------------------------------------
 void launch_expand(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t *out_ids,
-                   float *out_d2, cudaStream_t s);
+                   float *out_d2, const int32_t *q_k, cudaStream_t s);
 void launch_expand_wide(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t *out_ids,
-                        float *out_d2, cudaStream_t s);
+                        float *out_d2, const int32_t *q_k, cudaStream_t s);
 void launch_expand_iter(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t *out_ids,
-                        float *out_d2, cudaStream_t s);
+                        float *out_d2, const int32_t *q_k, cudaStream_t s);
 
 int num_sms(int device);
 // One-time kernel attributes and cached device queries (called outside any

@@ -193,10 +193,10 @@ extern "C" knn_status knn_query_static(const knn_world_desc *desc, const float *
             knnq::launch_queries_explicit(w, p, q_id_dev, q_x_dev, q_y_dev, n_q, k, out_ids_dev,
                                           out_d2_dev, s);
         if (p.wide) {
-            knnq::launch_expand_wide(w, p, k, n_q, out_ids_dev, out_d2_dev, s);
+            knnq::launch_expand_wide(w, p, k, n_q, out_ids_dev, out_d2_dev, nullptr, s);
         } else {
             knnq::launch_packets(w, p, n_q, s);
-            knnq::launch_expand(w, p, k, n_q, out_ids_dev, out_d2_dev, s);
+            knnq::launch_expand(w, p, k, n_q, out_ids_dev, out_d2_dev, nullptr, s);
         }
     }
     const cudaError_t e = cudaGetLastError();

@@ -68,11 +68,12 @@ class knn_server_counters(ctypes.Structure):
 class knn_tick_args(ctypes.Structure):
     _fields_ = [("upd_id_dev", _vp), ("upd_x_dev", _vp), ("upd_y_dev", _vp), ("n_upd", _i64),
                 ("q_id_dev", _vp), ("q_x_dev", _vp), ("q_y_dev", _vp), ("n_q", _i64),
-                ("k", _i32), ("out_ids_dev", _vp), ("out_d2_dev", _vp)]
+                ("k", _i32), ("out_ids_dev", _vp), ("out_d2_dev", _vp), ("q_k_dev", _vp)]
 
 _SIGNATURES = {
     "knn_world_create": ([ctypes.POINTER(knn_world_desc), _vp, _vp, _i64, _vp,
                           ctypes.POINTER(_vp)], ctypes.c_int),
+    "knn_tick_ex": ([_vp, ctypes.POINTER(knn_tick_args), _vp], ctypes.c_int),
     "knn_tick": ([_vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _i64, _i32, _vp, _vp, _vp],
                  ctypes.c_int),
     "knn_tick_host": ([_vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _i64, _i32, _vp, _vp, _vp],
@@ -287,12 +288,16 @@ def knn_world_autotune(w: int, q_id, q_x, q_y, n_q: int, k: int, out_ids, out_d2
 
 
 def tick_args(k: int, q_id=None, upd_id=None, upd_x=None, upd_y=None, q_x=None, q_y=None,
-              out_ids=None, out_d2=None) -> knn_tick_args:
-    """knn_tick_args from torch tensors (or None)."""
+              out_ids=None, out_d2=None, q_k=None) -> knn_tick_args:
+    """knn_tick_args from torch tensors (or None); q_k: per-query list sizes."""
     return knn_tick_args(_ptr(upd_id), _ptr(upd_x), _ptr(upd_y),
                          0 if upd_id is None else int(upd_id.shape[0]), _ptr(q_id), _ptr(q_x),
                          _ptr(q_y), 0 if q_id is None else int(q_id.shape[0]), k,
-                         _ptr(out_ids), _ptr(out_d2))
+                         _ptr(out_ids), _ptr(out_d2), _ptr(q_k))
+
+
+def knn_tick_ex(w: int, args: knn_tick_args, stream: int = 0) -> None:
+    _check(lib().knn_tick_ex(w, ctypes.byref(args), stream))
 
 
 def knn_server_create(n_slots: int = 4, hbm_budget_bytes: int = 0) -> int:
@@ -395,15 +400,22 @@ class World:
             pass
 
     def tick(self, k: int, q_id=None, upd_id=None, upd_x=None, upd_y=None, q_x=None, q_y=None,
-             out_ids=None, out_d2=None, stream=None):
+             out_ids=None, out_d2=None, stream=None, q_k=None):
+        """One tick; q_k (optional int32 tensor of n_q list sizes in [0, k]) asks
+        query i for its q_k[i] nearest objects (the rest of its row is padding)."""
         import torch
         n_upd = 0 if upd_id is None else int(upd_id.shape[0])
         n_q = 0 if q_id is None else int(q_id.shape[0])
         if n_q and out_ids is None:
             out_ids = torch.empty((n_q, k), dtype=torch.int32, device=self.device)
             out_d2 = torch.empty((n_q, k), dtype=torch.float32, device=self.device)
-        knn_tick(self.handle, _ptr(upd_id), _ptr(upd_x), _ptr(upd_y), n_upd, _ptr(q_id),
-                 _ptr(q_x), _ptr(q_y), n_q, k, _ptr(out_ids), _ptr(out_d2), _stream(stream))
+        if q_k is None:
+            knn_tick(self.handle, _ptr(upd_id), _ptr(upd_x), _ptr(upd_y), n_upd, _ptr(q_id),
+                     _ptr(q_x), _ptr(q_y), n_q, k, _ptr(out_ids), _ptr(out_d2),
+                     _stream(stream))
+        else:
+            knn_tick_ex(self.handle, tick_args(k, q_id, upd_id, upd_x, upd_y, q_x, q_y, out_ids,
+                                               out_d2, q_k), _stream(stream))
         return out_ids, out_d2
 
     def status(self):

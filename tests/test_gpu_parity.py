@@ -451,3 +451,59 @@ def test_index_reuse_across_empty_cells_and_cost_rebuild():
         assert st == knnq.KNN_OK, (st, bits)
     finally:
         world.close()
+
+
+# -------------------------------------------------------------------------
+# Per-query list sizes (q = (x, y, k))
+
+
+@pytest.mark.parametrize("k,expansion", [(16, 0), (16, 2), (16, 3), (33, 0), (100, 0), (5, 1)])
+def test_per_query_k_rows_are_prefixes(k, expansion):
+    torch, _ = torch_dev()
+    w = synth.skewed_moving(n=30000, k=k, ticks=2, seed=41, query_frac=0.6)
+    world = make_world(w.x0, w.y0, k_max=128, max_queries=max(t.q_id.shape[0] for t in w.ticks))
+    r = np.random.default_rng(42)
+    try:
+        if expansion:
+            world.set_tuning(expansion=expansion)
+        x, y = w.x0.copy(), w.y0.copy()
+        for ti, t in enumerate(w.ticks):
+            x, y, _ = oracle.apply_updates(x, y, t.upd_id, t.upd_x, t.upd_y)
+            qk = r.integers(0, k + 1, t.q_id.shape[0]).astype(np.int32)
+            ids, d2 = world.tick(k, to_dev(t.q_id), to_dev(t.upd_id), to_dev(t.upd_x),
+                                 to_dev(t.upd_y), q_k=to_dev(qk))
+            torch.cuda.synchronize()
+            ids, d2 = ids.cpu().numpy(), d2.cpu().numpy()
+            rows = sample_rows(t.q_id.shape[0], 3000, seed=ti)
+            rid, rd2 = oracle_rows(x, y, t, rows, k=k)
+            cols = np.arange(k)[None, :]
+            keep = cols < qk[rows][:, None]  # the first q_k entries; padding after them
+            rid = np.where(keep, rid, -1).astype(np.int32)
+            rd2 = np.where(keep, rd2, np.float32(np.inf)).astype(np.float32)
+            assert_rows_equal(ids, d2, rid, rd2, rows, what=f"per-query k tick {ti}")
+        st, bits = world.status()
+        assert st == knnq.KNN_OK, (st, bits)
+    finally:
+        world.close()
+
+
+def test_per_query_k_out_of_range_pads_and_reports():
+    torch, _ = torch_dev()
+    r = np.random.default_rng(43)
+    n = 5000
+    x, y = r.random(n).astype(np.float32), r.random(n).astype(np.float32)
+    world = make_world(x, y, k_max=8, max_queries=4)
+    try:
+        q = np.array([1, 2, 3, 4], np.int32)
+        qk = np.array([3, -1, 9, 8], np.int32)
+        ids, d2 = world.tick(8, to_dev(q), q_k=to_dev(qk))
+        torch.cuda.synchronize()
+        ids, d2 = ids.cpu().numpy(), d2.cpu().numpy()
+        rid, rd2, _ = oracle.knn(x, y, q, 8)
+        assert np.array_equal(ids[0, :3], rid[0, :3]) and np.all(ids[0, 3:] == -1)
+        assert np.array_equal(ids[3], rid[3])
+        assert np.all(ids[1:3] == -1) and np.all(np.isinf(d2[1:3]))
+        st, bits = world.status()
+        assert st != knnq.KNN_OK and bits & 4, (st, bits)
+    finally:
+        world.close()
