@@ -334,6 +334,7 @@ void launch_object_sort(World &w, const Plan &p, cudaStream_t s) {
 // the level-by-level splitting of Section 4.1.1 produces, computed in one pass.
 // Leaves start where (lambda, code) changes; a look-back scan numbers them.
 
+template <bool EMIT_EMPTY>
 __global__ void __launch_bounds__(256) k_leaves(
     const uint32_t *__restrict__ skeys, const int32_t *__restrict__ svals, int64_t n, int L,
     int th, int G, const float *__restrict__ px, const float *__restrict__ py,
@@ -342,7 +343,8 @@ __global__ void __launch_bounds__(256) k_leaves(
     uint8_t *__restrict__ blevel, int32_t *__restrict__ obj_leaf, int32_t *__restrict__ cb,
     int64_t ncell, int32_t *scalars,
     uint64_t *status, uint32_t *ticket, const uint32_t *__restrict__ tickinfo, uint32_t site,
-    uint32_t *err, bool guarded, int32_t sig, bool emit_empty, int64_t leaf_cap) {
+    uint32_t *err, bool guarded, int32_t sig, int64_t leaf_cap) {
+    constexpr bool emit_empty = EMIT_EMPTY;
     if (guarded && scalars[kScalarRebuild] == 0) return;  // this tick reuses the leaves
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t s_tile, s_tmp[8], s_excl;
@@ -627,12 +629,13 @@ void launch_leaves(World &w, const Plan &p, cudaStream_t s) {
     const size_t sm = leaves_smem(p.th);
     prepare_kernels();
     const int64_t ncell = 1ll << (2 * p.G);
-    k_leaves<<<tiles, 256, sm, s>>>(w.key[r], w.val[r], w.n, p.L, p.th, p.G, w.px, w.py, w.xs,
-                                    w.ys, w.sid, w.inv, w.bstart, w.bcode, w.blevel, w.obj_leaf,
-                                    w.cb,
-                                    ncell, w.scalars, w.status, w.counters + kCtrLeaves,
-                                    w.tickinfo, w.site++, w.err, p.reuse_age > 0,
-                                    index_signature(p), p.reuse_age > 0, w.leaf_cap);
+    // with index reuse on, empty level-G cells get empty leaves
+    auto leaves = p.reuse_age > 0 ? k_leaves<true> : k_leaves<false>;
+    leaves<<<tiles, 256, sm, s>>>(w.key[r], w.val[r], w.n, p.L, p.th, p.G, w.px, w.py, w.xs, w.ys,
+                                  w.sid, w.inv, w.bstart, w.bcode, w.blevel, w.obj_leaf, w.cb,
+                                  ncell, w.scalars, w.status, w.counters + kCtrLeaves, w.tickinfo,
+                                  w.site++, w.err, p.reuse_age > 0, index_signature(p),
+                                  w.leaf_cap);
     const int g = grid_for(w.n, 256, num_sms(w.device) * 8);
     k_leaf_aabb<<<g, 256, 0, s>>>(w.bstart, w.scalars, w.xs, w.ys, w.baabb, w.brange, w.n);
     w.launches += 2;
@@ -1030,7 +1033,9 @@ void prepare_kernels() {
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64 || done[dev]) return;
-    cudaFuncSetAttribute(k_leaves, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_leaves<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)leaves_smem(kMaxLeafCapacity));
+    cudaFuncSetAttribute(k_leaves<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)leaves_smem(kMaxLeafCapacity));
     num_sms(dev);          // fill the per-device caches now: the query APIs
     prepare_expand(dev);   // must not run while a batch is being recorded
