@@ -674,20 +674,29 @@ def run_gpu(args):
     h_od = torch.empty((N_OBJ, K), dtype=torch.float32).pin_memory()
     vp = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
     e2e_steps = max(3, min(args.steps, 10))
-    for i in range(2):  # warm-up (first call allocates the staging buffers)
-        knnq.knn_tick_host(world.handle, vp(h_uid), vp(h_ux[i]), vp(h_uy[i]), N_OBJ,
-                           vp(h_uid), None, None, N_OBJ, K, vp(h_oid), vp(h_od),
-                           stream.cuda_stream)
-    torch.cuda.synchronize()
-    e2e_t = []
-    for s in range(e2e_steps):
-        t0 = time.perf_counter()
-        knnq.knn_tick_host(world.handle, vp(h_uid), vp(h_ux[s % 2]), vp(h_uy[s % 2]), N_OBJ,
-                           vp(h_uid), None, None, N_OBJ, K, vp(h_oid), vp(h_od),
-                           stream.cuda_stream)
-        e2e_t.append(time.perf_counter() - t0)
-    e2e_total = max_over_ranks([sum(e2e_t)], dist, dev)[0]
 
+    def e2e_run(mode):
+        # mode: how knn_tick_host uses the pinned arrays (bit 0 rows written in
+        # place by the kernels, bit 1 inputs read in place; 0 stages both)
+        world.set_host_io(write_rows=bool(mode & 1), read_inputs=bool(mode & 2))
+        for i in range(2):  # warm-up (the first staged call allocates its buffers)
+            knnq.knn_tick_host(world.handle, vp(h_uid), vp(h_ux[i]), vp(h_uy[i]), N_OBJ,
+                               vp(h_uid), None, None, N_OBJ, K, vp(h_oid), vp(h_od),
+                               stream.cuda_stream)
+        torch.cuda.synchronize()
+        t = []
+        for s in range(e2e_steps):
+            t0 = time.perf_counter()
+            knnq.knn_tick_host(world.handle, vp(h_uid), vp(h_ux[s % 2]), vp(h_uy[s % 2]), N_OBJ,
+                               vp(h_uid), None, None, N_OBJ, K, vp(h_oid), vp(h_od),
+                               stream.cuda_stream)
+            t.append(time.perf_counter() - t0)
+        return max_over_ranks([sum(t)], dist, dev)[0]
+
+    e2e_modes = {name: e2e_run(m) for name, m in
+                 (("staged", 0), ("inputs_in_place", 2), ("all_in_place", 3),
+                  ("rows_in_place", 1))}
+    e2e_total = e2e_modes["rows_in_place"]  # the library's default
     world.close()
     if rank != 0:
         return
@@ -724,7 +733,10 @@ def run_gpu(args):
                 "unit": "queries/s",
                 "h2d_bytes_per_step": N_OBJ * 12 + N_OBJ * 4,
                 "d2h_bytes_per_step": N_OBJ * K * 8,
-                "api": "knn_tick_host (pinned host buffers, synchronous)"},
+                "api": "knn_tick_host (pinned host buffers, synchronous; rows written "
+                       "in place over the CPU-GPU link, inputs copied in)",
+                "by_mode": {m: replicas_value(n_gpus, N_OBJ * e2e_steps, t)
+                            for m, t in e2e_modes.items()}},
         "gpu_launches": launches,
         "clocks": clk.summary(),
         "exact_spot_check": spot,

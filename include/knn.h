@@ -125,15 +125,26 @@ typedef struct {
 knn_status knn_tick_ex(knn_world w, const knn_tick_args *args, void *stream);
 
 /* The same tick with every array in host memory (pageable or pinned): the
- * inputs are copied to world-owned device staging buffers, the tick runs on
- * `stream`, the results are copied back, and the call returns after the
- * stream has finished.  The first call that needs larger staging buffers
- * allocates them (so that call is not allocation-free). */
+ * tick runs on `stream` and the call returns after the stream has finished.
+ * Pageable arrays go through world-owned device staging buffers (inputs
+ * copied in before the tick, rows copied out after it); the first call that
+ * needs larger staging buffers allocates them (so that call is not
+ * allocation-free).  Output arrays in pinned host memory (cudaHostAlloc,
+ * cudaHostRegister) are written in place by the expansion kernel over the
+ * CPU-GPU link, so the transfer overlaps the search; see
+ * knn_world_set_host_io.  The rows are identical either way. */
 knn_status knn_tick_host(knn_world w, const int32_t *upd_id_host, const float *upd_x_host,
                          const float *upd_y_host, int64_t n_upd, const int32_t *q_id_host,
                          const float *q_x_host, const float *q_y_host, int64_t n_q,
                          int32_t k, int32_t *out_ids_host, float *out_d2_host,
                          void *stream);
+
+/* How knn_tick_host treats pinned host arrays: bit 0 (on by default) lets the
+ * kernels write the rows straight into pinned output arrays; bit 1 (off by
+ * default) lets them read pinned input arrays in place instead of copying
+ * them to the device first.  Arrays that are not pinned are always staged.
+ * mode outside [0, 3]: KNN_ERR_INVALID. */
+knn_status knn_world_set_host_io(knn_world w, int32_t mode);
 
 /* Batch processing over many worlds (Section 2.3 per world): one tick of every
  * world in `worlds` (distinct handles on the current device), with args[i]

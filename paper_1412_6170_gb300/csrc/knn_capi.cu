@@ -521,6 +521,22 @@ knn_status knn_tick_ex(knn_world h, const knn_tick_args *args, void *stream) {
     return knnq::tick_launch(w, *args, (cudaStream_t)stream);
 }
 
+// The device-side address of a host array that the runtime has pinned
+// (cudaHostAlloc, cudaHostRegister), or NULL (pageable memory, or a device
+// array).  Kernels can read and write pinned host memory through it over the
+// CPU-GPU link, so the rows can go straight to the caller's buffer while the
+// expansion runs instead of being copied after it.
+static void *pinned_alias(const void *p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+    return a.devicePointer;
+}
+
 knn_status knn_tick_host(knn_world h, const int32_t *upd_id, const float *upd_x,
                          const float *upd_y, int64_t n_upd, const int32_t *q_id,
                          const float *q_x, const float *q_y, int64_t n_q, int32_t k,
@@ -529,16 +545,53 @@ knn_status knn_tick_host(knn_world h, const int32_t *upd_id, const float *upd_x,
     World &w = h->w;
     if (n_upd < 0 || n_q < 0 || k < 1 || k > w.desc.k_max)
         return fail(KNN_ERR_INVALID, "knn_tick_host: bad sizes");
+    if (n_upd > 0 && (!upd_id || !upd_x || !upd_y))
+        return fail(KNN_ERR_INVALID, "knn_tick_host: NULL update array with n_upd > 0");
     const bool explicit_q = q_x != nullptr;
-    const size_t b_upd = align_up(sizeof(int32_t) * (size_t)n_upd) +
-                         2 * align_up(sizeof(float) * (size_t)n_upd);
-    const size_t b_q = align_up(sizeof(int32_t) * (size_t)n_q) +
-                       (explicit_q ? 2 * align_up(sizeof(float) * (size_t)n_q) : 0);
-    const size_t b_out = align_up(sizeof(int32_t) * (size_t)n_q * k) +
-                         align_up(sizeof(float) * (size_t)n_q * k);
-    const size_t need = b_upd + b_q + b_out;
+    if (n_q > 0 && (!q_id || !out_ids || !out_d2 || (explicit_q && !q_y)))
+        return fail(KNN_ERR_INVALID, "knn_tick_host: NULL query or output array");
     cudaSetDevice(w.device);
     cudaStream_t s = (cudaStream_t)stream;
+
+    // pinned arrays are used in place (outputs: bit 0 of host_io; inputs: bit 1)
+    int32_t *a_oid = nullptr;
+    float *a_od = nullptr;
+    if ((w.host_io & 1) && n_q > 0) {
+        a_oid = static_cast<int32_t *>(pinned_alias(out_ids));
+        a_od = static_cast<float *>(pinned_alias(out_d2));
+        if (!a_oid || !a_od) a_oid = nullptr, a_od = nullptr;
+    }
+    const int32_t *a_uid = nullptr, *a_qid = nullptr;
+    const float *a_ux = nullptr, *a_uy = nullptr, *a_qx = nullptr, *a_qy = nullptr;
+    if (w.host_io & 2) {
+        if (n_upd > 0) {
+            a_uid = static_cast<const int32_t *>(pinned_alias(upd_id));
+            a_ux = static_cast<const float *>(pinned_alias(upd_x));
+            a_uy = static_cast<const float *>(pinned_alias(upd_y));
+            if (!a_uid || !a_ux || !a_uy) a_uid = nullptr, a_ux = a_uy = nullptr;
+        }
+        if (n_q > 0) {
+            a_qid = static_cast<const int32_t *>(pinned_alias(q_id));
+            if (explicit_q) {
+                a_qx = static_cast<const float *>(pinned_alias(q_x));
+                a_qy = static_cast<const float *>(pinned_alias(q_y));
+                if (!a_qx || !a_qy) a_qid = nullptr, a_qx = a_qy = nullptr;
+            }
+        }
+    }
+    const bool stage_upd = n_upd > 0 && !a_uid, stage_q = n_q > 0 && !a_qid;
+    const bool stage_out = n_q > 0 && !a_oid;
+
+    const size_t b_upd = stage_upd ? align_up(sizeof(int32_t) * (size_t)n_upd) +
+                                         2 * align_up(sizeof(float) * (size_t)n_upd)
+                                   : 0;
+    const size_t b_q = stage_q ? align_up(sizeof(int32_t) * (size_t)n_q) +
+                                     (explicit_q ? 2 * align_up(sizeof(float) * (size_t)n_q) : 0)
+                               : 0;
+    const size_t b_out = stage_out ? align_up(sizeof(int32_t) * (size_t)n_q * k) +
+                                         align_up(sizeof(float) * (size_t)n_q * k)
+                                   : 0;
+    const size_t need = b_upd + b_q + b_out;
     if (need > w.stage_bytes) {
         cudaStreamSynchronize(s);
         if (w.stage) cudaFree(w.stage);
@@ -552,40 +605,48 @@ knn_status knn_tick_host(knn_world h, const int32_t *upd_id, const float *upd_x,
         w.stage_bytes = need;
     }
     Carve c{static_cast<char *>(w.stage)};
-    int32_t *d_uid = c.take<int32_t>((size_t)n_upd);
-    float *d_ux = c.take<float>((size_t)n_upd);
-    float *d_uy = c.take<float>((size_t)n_upd);
-    int32_t *d_qid = c.take<int32_t>((size_t)n_q);
-    float *d_qx = explicit_q ? c.take<float>((size_t)n_q) : nullptr;
-    float *d_qy = explicit_q ? c.take<float>((size_t)n_q) : nullptr;
-    int32_t *d_oid = c.take<int32_t>((size_t)n_q * k);
-    float *d_od = c.take<float>((size_t)n_q * k);
-    if (n_upd > 0) {
-        if (!upd_id || !upd_x || !upd_y)
-            return fail(KNN_ERR_INVALID, "knn_tick_host: NULL update array with n_upd > 0");
+    if (stage_upd) {
+        int32_t *d_uid = c.take<int32_t>((size_t)n_upd);
+        float *d_ux = c.take<float>((size_t)n_upd);
+        float *d_uy = c.take<float>((size_t)n_upd);
         cudaMemcpyAsync(d_uid, upd_id, sizeof(int32_t) * n_upd, cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(d_ux, upd_x, sizeof(float) * n_upd, cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(d_uy, upd_y, sizeof(float) * n_upd, cudaMemcpyHostToDevice, s);
+        a_uid = d_uid, a_ux = d_ux, a_uy = d_uy;
     }
-    if (n_q > 0) {
-        if (!q_id || !out_ids || !out_d2 || (explicit_q && !q_y))
-            return fail(KNN_ERR_INVALID, "knn_tick_host: NULL query or output array");
+    if (stage_q) {
+        int32_t *d_qid = c.take<int32_t>((size_t)n_q);
         cudaMemcpyAsync(d_qid, q_id, sizeof(int32_t) * n_q, cudaMemcpyHostToDevice, s);
+        a_qid = d_qid;
         if (explicit_q) {
+            float *d_qx = c.take<float>((size_t)n_q);
+            float *d_qy = c.take<float>((size_t)n_q);
             cudaMemcpyAsync(d_qx, q_x, sizeof(float) * n_q, cudaMemcpyHostToDevice, s);
             cudaMemcpyAsync(d_qy, q_y, sizeof(float) * n_q, cudaMemcpyHostToDevice, s);
+            a_qx = d_qx, a_qy = d_qy;
         }
     }
-    knn_status st = knn_tick(h, n_upd ? d_uid : nullptr, n_upd ? d_ux : nullptr,
-                             n_upd ? d_uy : nullptr, n_upd, n_q ? d_qid : nullptr, d_qx, d_qy,
-                             n_q, k, n_q ? d_oid : nullptr, n_q ? d_od : nullptr, stream);
+    int32_t *d_oid = a_oid;
+    float *d_od = a_od;
+    if (stage_out) {
+        d_oid = c.take<int32_t>((size_t)n_q * k);
+        d_od = c.take<float>((size_t)n_q * k);
+    }
+    knn_status st = knn_tick(h, a_uid, a_ux, a_uy, n_upd, a_qid, a_qx, a_qy, n_q, k, d_oid, d_od,
+                             stream);
     if (st != KNN_OK) return st;
-    if (n_q > 0) {
+    if (stage_out) {
         cudaMemcpyAsync(out_ids, d_oid, sizeof(int32_t) * n_q * k, cudaMemcpyDeviceToHost, s);
         cudaMemcpyAsync(out_d2, d_od, sizeof(float) * n_q * k, cudaMemcpyDeviceToHost, s);
     }
     const cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "knn_tick_host");
+    return KNN_OK;
+}
+
+knn_status knn_world_set_host_io(knn_world h, int32_t mode) {
+    if (!h || mode < 0 || mode > 3) return fail(KNN_ERR_INVALID, "knn_world_set_host_io: bad argument");
+    h->w.host_io = mode;
     return KNN_OK;
 }
 

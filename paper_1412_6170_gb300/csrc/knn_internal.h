@@ -133,6 +133,7 @@ struct World {
     // knn_tick replays a recorded graph when its arguments, plan and profiling
     // marks match one of the last kTickGraphs ticks (least recently used goes)
     bool graphs = true;
+    int host_io = 1;  // knn_tick_host: bit 0 writes rows, bit 1 reads inputs in pinned host memory
     TickGraph tick_graph[kTickGraphs];
     uint64_t tick_clock = 0;
     cudaStream_t capture_stream = nullptr;

@@ -89,6 +89,7 @@ _SIGNATURES = {
     "knn_world_launches": ([_vp, ctypes.POINTER(_i64)], ctypes.c_int),
     "knn_world_set_profiling": ([_vp, _i32], ctypes.c_int),
     "knn_world_set_graphs": ([_vp, _i32], ctypes.c_int),
+    "knn_world_set_host_io": ([_vp, _i32], ctypes.c_int),
     "knn_brute_force": ([_vp, _vp, _i64, _vp, _vp, _vp, _i64, _i32, _vp, _vp, _vp], ctypes.c_int),
     "knn_world_set_index_reuse": ([_vp, _i32, ctypes.c_float], ctypes.c_int),
     "knn_world_index_info": ([_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)], ctypes.c_int),
@@ -215,6 +216,10 @@ def knn_world_set_profiling(w: int, enable: bool) -> None:
 
 def knn_world_set_graphs(w: int, enable: bool) -> None:
     _check(lib().knn_world_set_graphs(w, 1 if enable else 0))
+
+
+def knn_world_set_host_io(w: int, mode: int) -> None:
+    _check(lib().knn_world_set_host_io(w, mode))
 
 
 def knn_brute_force(x_dev, y_dev, n: int, q_id_dev, q_x_dev, q_y_dev, n_q: int, k: int,
@@ -464,6 +469,10 @@ class World:
 
     def set_graphs(self, enable: bool = True):
         knn_world_set_graphs(self.handle, enable)
+
+    def set_host_io(self, write_rows: bool = True, read_inputs: bool = False):
+        """How tick_host uses pinned host arrays in place (see knn_world_set_host_io)."""
+        knn_world_set_host_io(self.handle, (1 if write_rows else 0) | (2 if read_inputs else 0))
 
     def set_index_reuse(self, max_age: int, factor: float = 0.0):
         knn_world_set_index_reuse(self.handle, max_age, factor)

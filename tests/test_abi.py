@@ -60,3 +60,5 @@ def test_null_world_calls_are_rejected(lib):
     with pytest.raises(knnq.KnnError) as e:
         knnq.knn_world_set_tuning(None, 1, 1, 1)
     assert e.value.status == knnq.KNN_ERR_INVALID
+    assert lib.knn_world_set_host_io(None, 1) == knnq.KNN_ERR_INVALID
+    assert lib.knn_world_set_graphs(None, 1) == knnq.KNN_ERR_INVALID

@@ -283,6 +283,45 @@ def test_host_buffer_tick_matches_device_tick():
         b.close()
 
 
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
+@pytest.mark.parametrize("k,explicit", [(16, False), (5, True)])
+def test_pinned_host_tick_matches_device_tick(mode, k, explicit):
+    # pinned arrays written (bit 0) and read (bit 1) in place by the kernels,
+    # over several ticks, give the rows of the device-array tick
+    w = synth.plain_uniform_moving(n=60000, k=k, ticks=3, seed=5)
+    a = make_world(w.x0, w.y0, k_max=k)
+    b = make_world(w.x0, w.y0, k_max=k)
+    b.set_host_io(write_rows=bool(mode & 1), read_inputs=bool(mode & 2))
+    torch, dev = torch_dev()
+    try:
+        for i, t in enumerate(w.ticks):
+            nq = t.q_id.shape[0]
+            if explicit:
+                qx = (w.x0[t.q_id] + np.float32(0.001 * (i + 1))).astype(np.float32)
+                qy = w.y0[t.q_id].copy()
+                pin = [torch.from_numpy(v).pin_memory()
+                       for v in (t.upd_id, t.upd_x, t.upd_y, t.q_id, qx, qy)]
+                ids, d2 = a.tick(k, *(v.to(dev) for v in (pin[3], pin[0], pin[1], pin[2])),
+                                 q_x=pin[4].to(dev), q_y=pin[5].to(dev))
+            else:
+                pin = [torch.from_numpy(v).pin_memory()
+                       for v in (t.upd_id, t.upd_x, t.upd_y, t.q_id)]
+                ids, d2 = a.tick(k, *(v.to(dev) for v in (pin[3], pin[0], pin[1], pin[2])))
+            torch.cuda.synchronize()
+            hid = torch.full((nq, k), 7, dtype=torch.int32).pin_memory()
+            hd2 = torch.full((nq, k), 7.0, dtype=torch.float32).pin_memory()
+            knnq.knn_tick_host(b.handle, pin[0].data_ptr(), pin[1].data_ptr(), pin[2].data_ptr(),
+                               t.upd_id.shape[0], pin[3].data_ptr(),
+                               pin[4].data_ptr() if explicit else None,
+                               pin[5].data_ptr() if explicit else None, nq, k,
+                               hid.data_ptr(), hd2.data_ptr(), 0)
+            assert np.array_equal(ids.cpu().numpy(), hid.numpy())
+            assert np.array_equal(d2.cpu().numpy().view(np.uint32), hd2.numpy().view(np.uint32))
+    finally:
+        a.close()
+        b.close()
+
+
 def test_checkpoint_resume_bit_identical():
     w = synth.plain_uniform_moving(n=40000, k=8, ticks=6, seed=4)
     a = make_world(w.x0, w.y0, k_max=8)
