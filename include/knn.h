@@ -139,6 +139,29 @@ knn_status knn_tick_host(knn_world w, const int32_t *upd_id_host, const float *u
                          int32_t k, int32_t *out_ids_host, float *out_d2_host,
                          void *stream);
 
+/* Pipelined host-buffer ticks: knn_tick_host_submit enqueues the tick that
+ * knn_tick_host runs, with the same arguments, and returns without waiting.
+ * The inputs are copied on a world-owned copy stream into one of two device
+ * staging slots (used in turn), the tick runs on `stream` once they are in,
+ * and the rows are copied back on a second copy stream once it is done; with
+ * the arrays in pinned memory the copies of one tick overlap the search of
+ * the next.  *ticket receives the tick's number.  Until knn_tick_host_wait
+ * for that ticket returns, the caller must neither change its input arrays
+ * nor read its output arrays; two ticks in flight need two sets of output
+ * arrays.  Ticks of one world run in submission order.  Errors as knn_tick
+ * (checked before anything is enqueued); a submission that needs larger
+ * staging buffers waits for its slot's previous tick and allocates them. */
+knn_status knn_tick_host_submit(knn_world w, const int32_t *upd_id_host,
+                                const float *upd_x_host, const float *upd_y_host,
+                                int64_t n_upd, const int32_t *q_id_host, const float *q_x_host,
+                                const float *q_y_host, int64_t n_q, int32_t k,
+                                int32_t *out_ids_host, float *out_d2_host, void *stream,
+                                int64_t *ticket);
+
+/* Blocks until the tick `ticket` (and possibly later ones) has finished and
+ * its rows are in the output arrays.  A ticket never submitted: KNN_ERR_INVALID. */
+knn_status knn_tick_host_wait(knn_world w, int64_t ticket);
+
 /* How knn_tick_host treats pinned host arrays: bit 0 (on by default) lets the
  * kernels write the rows straight into pinned output arrays; bit 1 (off by
  * default) lets them read pinned input arrays in place instead of copying

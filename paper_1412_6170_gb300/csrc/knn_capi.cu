@@ -238,6 +238,16 @@ void release(World &w) {
     }
     if (w.capture_stream) cudaStreamDestroy(w.capture_stream);
     w.capture_stream = nullptr;
+    for (World::HostSlot &hs : w.hslot) {
+        if (hs.done) cudaEventSynchronize(hs.done);
+        if (hs.buf) cudaFree(hs.buf);
+        for (cudaEvent_t e : {hs.in, hs.ran, hs.done})
+            if (e) cudaEventDestroy(e);
+        hs = World::HostSlot{};
+    }
+    if (w.h2d) cudaStreamDestroy(w.h2d);
+    if (w.d2h) cudaStreamDestroy(w.d2h);
+    w.h2d = w.d2h = nullptr;
     w.arena = nullptr;
     w.stage = nullptr;
 }
@@ -641,6 +651,120 @@ knn_status knn_tick_host(knn_world h, const int32_t *upd_id, const float *upd_x,
     }
     const cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "knn_tick_host");
+    return KNN_OK;
+}
+
+knn_status knn_tick_host_submit(knn_world h, const int32_t *upd_id, const float *upd_x,
+                                const float *upd_y, int64_t n_upd, const int32_t *q_id,
+                                const float *q_x, const float *q_y, int64_t n_q, int32_t k,
+                                int32_t *out_ids, float *out_d2, void *stream,
+                                int64_t *ticket) {
+    if (!h || !ticket) return fail(KNN_ERR_INVALID, "knn_tick_host_submit: NULL argument");
+    World &w = h->w;
+    const bool explicit_q = q_x != nullptr;
+    if (n_upd > 0 && (!upd_id || !upd_x || !upd_y))
+        return fail(KNN_ERR_INVALID, "knn_tick_host_submit: NULL update array with n_upd > 0");
+    if (n_q > 0 && (!q_id || !out_ids || !out_d2 || (explicit_q && !q_y)))
+        return fail(KNN_ERR_INVALID, "knn_tick_host_submit: NULL query or output array");
+    if (explicit_q != (q_y != nullptr))
+        return fail(KNN_ERR_INVALID, "knn_tick_host_submit: q_x and q_y must both be given");
+    {
+        // the checks of knn_tick, before anything is enqueued
+        knn_tick_args a{};
+        a.upd_id_dev = upd_id, a.upd_x_dev = upd_x, a.upd_y_dev = upd_y, a.n_upd = n_upd;
+        a.q_id_dev = q_id, a.q_x_dev = q_x, a.q_y_dev = q_y, a.n_q = n_q, a.k = k;
+        a.out_ids_dev = out_ids, a.out_d2_dev = out_d2;
+        const knn_status st = knnq::check_tick_args(w, a, "knn_tick_host_submit");
+        if (st != KNN_OK) return st;
+    }
+    cudaSetDevice(w.device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!w.h2d) {
+        if (cudaStreamCreateWithFlags(&w.h2d, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&w.d2h, cudaStreamNonBlocking) != cudaSuccess)
+            return cuda_fail(cudaGetLastError(), "knn_tick_host_submit: copy streams");
+        for (World::HostSlot &hs : w.hslot)
+            for (cudaEvent_t *e : {&hs.in, &hs.ran, &hs.done})
+                if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess)
+                    return cuda_fail(cudaGetLastError(), "knn_tick_host_submit: events");
+    }
+    World::HostSlot &hs = w.hslot[w.tickets & 1];
+    const size_t b_upd = align_up(sizeof(int32_t) * (size_t)n_upd) +
+                         2 * align_up(sizeof(float) * (size_t)n_upd);
+    const size_t b_q = align_up(sizeof(int32_t) * (size_t)n_q) +
+                       (explicit_q ? 2 * align_up(sizeof(float) * (size_t)n_q) : 0);
+    const size_t b_out = align_up(sizeof(int32_t) * (size_t)n_q * k) +
+                         align_up(sizeof(float) * (size_t)n_q * k);
+    const size_t need = b_upd + b_q + b_out;
+    if (need > hs.bytes) {
+        cudaEventSynchronize(hs.done);  // the slot's last ticket is finished
+        if (hs.buf) cudaFree(hs.buf);
+        hs.buf = nullptr;
+        hs.bytes = 0;
+        if (cudaMalloc(&hs.buf, need) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(KNN_ERR_OOM, "knn_tick_host_submit: staging allocation of %zu bytes failed",
+                        need);
+        }
+        hs.bytes = need;
+    }
+    Carve c{static_cast<char *>(hs.buf)};
+    int32_t *d_uid = c.take<int32_t>((size_t)n_upd);
+    float *d_ux = c.take<float>((size_t)n_upd);
+    float *d_uy = c.take<float>((size_t)n_upd);
+    int32_t *d_qid = c.take<int32_t>((size_t)n_q);
+    float *d_qx = explicit_q ? c.take<float>((size_t)n_q) : nullptr;
+    float *d_qy = explicit_q ? c.take<float>((size_t)n_q) : nullptr;
+    int32_t *d_oid = c.take<int32_t>((size_t)n_q * k);
+    float *d_od = c.take<float>((size_t)n_q * k);
+
+    // inputs: once the slot's previous rows have left (its buffers are free)
+    cudaStreamWaitEvent(w.h2d, hs.done, 0);
+    if (n_upd > 0) {
+        cudaMemcpyAsync(d_uid, upd_id, sizeof(int32_t) * n_upd, cudaMemcpyHostToDevice, w.h2d);
+        cudaMemcpyAsync(d_ux, upd_x, sizeof(float) * n_upd, cudaMemcpyHostToDevice, w.h2d);
+        cudaMemcpyAsync(d_uy, upd_y, sizeof(float) * n_upd, cudaMemcpyHostToDevice, w.h2d);
+    }
+    if (n_q > 0) {
+        cudaMemcpyAsync(d_qid, q_id, sizeof(int32_t) * n_q, cudaMemcpyHostToDevice, w.h2d);
+        if (explicit_q) {
+            cudaMemcpyAsync(d_qx, q_x, sizeof(float) * n_q, cudaMemcpyHostToDevice, w.h2d);
+            cudaMemcpyAsync(d_qy, q_y, sizeof(float) * n_q, cudaMemcpyHostToDevice, w.h2d);
+        }
+    }
+    cudaEventRecord(hs.in, w.h2d);
+    // the tick, on the caller's stream, after its inputs
+    cudaStreamWaitEvent(s, hs.in, 0);
+    const knn_status st = knn_tick(h, n_upd ? d_uid : nullptr, n_upd ? d_ux : nullptr,
+                                   n_upd ? d_uy : nullptr, n_upd, n_q ? d_qid : nullptr, d_qx,
+                                   d_qy, n_q, k, n_q ? d_oid : nullptr, n_q ? d_od : nullptr,
+                                   stream);
+    if (st != KNN_OK) return st;
+    cudaEventRecord(hs.ran, s);
+    // rows: after the tick
+    cudaStreamWaitEvent(w.d2h, hs.ran, 0);
+    if (n_q > 0) {
+        cudaMemcpyAsync(out_ids, d_oid, sizeof(int32_t) * n_q * k, cudaMemcpyDeviceToHost, w.d2h);
+        cudaMemcpyAsync(out_d2, d_od, sizeof(float) * n_q * k, cudaMemcpyDeviceToHost, w.d2h);
+    }
+    cudaEventRecord(hs.done, w.d2h);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "knn_tick_host_submit");
+    *ticket = w.tickets++;
+    return KNN_OK;
+}
+
+knn_status knn_tick_host_wait(knn_world h, int64_t ticket) {
+    if (!h) return fail(KNN_ERR_INVALID, "knn_tick_host_wait: NULL world");
+    World &w = h->w;
+    if (ticket < 0 || ticket >= w.tickets)
+        return fail(KNN_ERR_INVALID, "knn_tick_host_wait: ticket %lld was not submitted",
+                    (long long)ticket);
+    cudaSetDevice(w.device);
+    // the slot's last rows-out event belongs to this ticket or a later one of
+    // the same slot; the copy stream runs them in order
+    const cudaError_t e = cudaEventSynchronize(w.hslot[ticket & 1].done);
+    if (e != cudaSuccess) return cuda_fail(e, "knn_tick_host_wait");
     return KNN_OK;
 }
 

@@ -122,6 +122,17 @@ struct World {
     void *stage = nullptr;
     size_t stage_bytes = 0;
 
+    // pipelined host-buffer ticks (knn_tick_host_submit): two staging slots
+    // used in turn, one copy stream per direction, per-slot events (inputs in,
+    // tick run, rows out)
+    struct HostSlot {
+        void *buf = nullptr;
+        size_t bytes = 0;
+        cudaEvent_t in = nullptr, ran = nullptr, done = nullptr;
+    } hslot[2];
+    cudaStream_t h2d = nullptr, d2h = nullptr;
+    int64_t tickets = 0;
+
     // kernels launched by this world's ticks so far
     int64_t launches = 0;
 

@@ -90,6 +90,9 @@ _SIGNATURES = {
     "knn_world_set_profiling": ([_vp, _i32], ctypes.c_int),
     "knn_world_set_graphs": ([_vp, _i32], ctypes.c_int),
     "knn_world_set_host_io": ([_vp, _i32], ctypes.c_int),
+    "knn_tick_host_submit": ([_vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _i64, _i32, _vp, _vp,
+                              _vp, ctypes.POINTER(_i64)], ctypes.c_int),
+    "knn_tick_host_wait": ([_vp, _i64], ctypes.c_int),
     "knn_brute_force": ([_vp, _vp, _i64, _vp, _vp, _vp, _i64, _i32, _vp, _vp, _vp], ctypes.c_int),
     "knn_world_set_index_reuse": ([_vp, _i32, ctypes.c_float], ctypes.c_int),
     "knn_world_index_info": ([_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)], ctypes.c_int),
@@ -167,6 +170,18 @@ def knn_tick_host(w: int, upd_id, upd_x, upd_y, n_upd: int, q_id, q_x, q_y, n_q:
                   out_ids, out_d2, stream: int = 0) -> None:
     _check(lib().knn_tick_host(w, upd_id, upd_x, upd_y, n_upd, q_id, q_x, q_y, n_q, k,
                                out_ids, out_d2, stream))
+
+
+def knn_tick_host_submit(w: int, upd_id, upd_x, upd_y, n_upd: int, q_id, q_x, q_y, n_q: int,
+                         k: int, out_ids, out_d2, stream: int = 0) -> int:
+    t = _i64(0)
+    _check(lib().knn_tick_host_submit(w, upd_id, upd_x, upd_y, n_upd, q_id, q_x, q_y, n_q, k,
+                                      out_ids, out_d2, stream, ctypes.byref(t)))
+    return t.value
+
+
+def knn_tick_host_wait(w: int, ticket: int) -> None:
+    _check(lib().knn_tick_host_wait(w, ticket))
 
 
 def knn_tick_status(w: int) -> tuple:

@@ -62,3 +62,7 @@ def test_null_world_calls_are_rejected(lib):
     assert e.value.status == knnq.KNN_ERR_INVALID
     assert lib.knn_world_set_host_io(None, 1) == knnq.KNN_ERR_INVALID
     assert lib.knn_world_set_graphs(None, 1) == knnq.KNN_ERR_INVALID
+    assert lib.knn_tick_host_wait(None, 0) == knnq.KNN_ERR_INVALID
+    t = ctypes.c_int64(0)
+    assert lib.knn_tick_host_submit(None, None, None, None, 0, None, None, None, 0, 1, None, None,
+                                    None, ctypes.byref(t)) == knnq.KNN_ERR_INVALID

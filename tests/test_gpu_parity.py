@@ -322,6 +322,57 @@ def test_pinned_host_tick_matches_device_tick(mode, k, explicit):
         b.close()
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+def test_pipelined_host_ticks_match_device_ticks(pinned):
+    # two ticks in flight (two sets of output arrays), waited for one tick late
+    import ctypes
+    k = 16
+    w = synth.plain_uniform_moving(n=70000, k=k, ticks=5, seed=6)
+    a = make_world(w.x0, w.y0, k_max=k)
+    b = make_world(w.x0, w.y0, k_max=k)
+    torch, dev = torch_dev()
+    try:
+        want = [gpu_tick(a, t) for t in w.ticks]
+        nq = w.ticks[0].q_id.shape[0]
+        if pinned:
+            ins = [[torch.from_numpy(v).pin_memory() for v in (t.upd_id, t.upd_x, t.upd_y, t.q_id)]
+                   for t in w.ticks]
+            outs = [(torch.empty((nq, k), dtype=torch.int32).pin_memory(),
+                     torch.empty((nq, k), dtype=torch.float32).pin_memory()) for _ in range(2)]
+            ptr = lambda v: v.data_ptr()  # noqa: E731
+            view = lambda v: v.numpy()  # noqa: E731
+        else:
+            ins = [[np.ascontiguousarray(v) for v in (t.upd_id, t.upd_x, t.upd_y, t.q_id)]
+                   for t in w.ticks]
+            outs = [(np.empty((nq, k), np.int32), np.empty((nq, k), np.float32))
+                    for _ in range(2)]
+            ptr = lambda v: v.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+            view = lambda v: v  # noqa: E731
+        s = torch.cuda.Stream()
+        tickets = []
+        for i, t in enumerate(w.ticks):
+            u, ux, uy, q = ins[i]
+            oi, od = outs[i % 2]
+            tickets.append(knnq.knn_tick_host_submit(
+                b.handle, ptr(u), ptr(ux), ptr(uy), t.upd_id.shape[0], ptr(q), None, None, nq,
+                k, ptr(oi), ptr(od), s.cuda_stream))
+            if i >= 1:
+                knnq.knn_tick_host_wait(b.handle, tickets[i - 1])
+                pi, pd = outs[(i - 1) % 2]
+                assert np.array_equal(view(pi), want[i - 1][0]), i - 1
+                assert np.array_equal(view(pd).view(np.uint32), want[i - 1][1].view(np.uint32))
+        knnq.knn_tick_host_wait(b.handle, tickets[-1])
+        li, ld = outs[(len(w.ticks) - 1) % 2]
+        assert np.array_equal(view(li), want[-1][0])
+        assert np.array_equal(view(ld).view(np.uint32), want[-1][1].view(np.uint32))
+        with pytest.raises(knnq.KnnError):
+            knnq.knn_tick_host_wait(b.handle, tickets[-1] + 1)
+        assert b.status()[0] == knnq.KNN_OK
+    finally:
+        a.close()
+        b.close()
+
+
 def test_checkpoint_resume_bit_identical():
     w = synth.plain_uniform_moving(n=40000, k=8, ticks=6, seed=4)
     a = make_world(w.x0, w.y0, k_max=8)
