@@ -53,8 +53,11 @@ Plan make_plan(const World &w, int64_t n_q, int k) {
     int G = w.tuning.grid_level > 0 ? w.tuning.grid_level
                                     : round_log4(2.0 * (double)w.n / (double)p.th);
     p.G = clampi(G, 1, gmax);
-    int Gp = w.tuning.packet_level > 0 ? w.tuning.packet_level
-                                       : round_log4((double)(n_q > 0 ? n_q : 1) / 48.0);
+    // about max(48, 12 k) queries per packet cell (measured on 1M uniform
+    // objects, all querying: k <= 8 best at ~61 per cell, k = 32 at ~244)
+    int Gp = w.tuning.packet_level > 0
+                 ? w.tuning.packet_level
+                 : round_log4((double)(n_q > 0 ? n_q : 1) / (k > 4 ? 12.0 * k : 48.0));
     p.Gp = clampi(Gp, 0, p.G);
     // one warp per query pays off above k = 32 (measured on 1M uniform objects:
     // k = 64 takes 2.8 ms that way against 3.5 ms in packets)
