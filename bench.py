@@ -721,6 +721,23 @@ def run_gpu(args):
     e2e_pipelined(e2e_steps)
     e2e_total = max_over_ranks([time.perf_counter() - t0], dist, dev)[0]
     e2e_modes = {"pipelined": e2e_total, **e2e_modes}
+    # the rows that reached host memory in the last pipelined step, against
+    # the oracle (every object moves every tick, so that tick's inputs alone
+    # fix its rows)
+    e2e_spot = None
+    if rank == 0 and not args.no_check:
+        import oracle
+        last = (e2e_steps - 1) % 2
+        t = wl.ticks[last]
+        rows = np.linspace(0, N_OBJ - 1, 512).astype(np.int64)
+        x, y, _ = oracle.apply_updates(wl.x0, wl.y0, t.upd_id, t.upd_x, t.upd_y)
+        rid, rd2, _ = oracle.knn(x, y, t.q_id[rows], K)
+        gid = h_oid2[last].numpy()[rows]
+        gd2 = h_od2[last].numpy()[rows]
+        e2e_spot = bool(np.array_equal(gid, rid) and np.array_equal(gd2.view(np.uint32),
+                                                                    rd2.view(np.uint32)))
+        if not e2e_spot:
+            raise RuntimeError("host-buffer rows differ from the oracle on the spot check")
     world.close()
     if rank != 0:
         return
@@ -762,7 +779,8 @@ def run_gpu(args):
                        "out inside the timed region, overlapping the next step's search); "
                        "by_mode adds the synchronous knn_tick_host",
                 "by_mode": {m: replicas_value(n_gpus, N_OBJ * e2e_steps, t)
-                            for m, t in e2e_modes.items()}},
+                            for m, t in e2e_modes.items()},
+                "exact_spot_check": e2e_spot},
         "gpu_launches": launches,
         "clocks": clk.summary(),
         "exact_spot_check": spot,

@@ -49,18 +49,31 @@ struct ExpandArgs {
 };
 
 
-// Per-lane candidate buffer (shared memory, kBufCap slots per lane, a stack):
+// Per-lane candidate buffer (shared memory, a stack of slots per lane):
 // candidates whose d^2 is within the lane's current threshold are pushed
-// there.  Once some lane holds kFlushAt of them, every lane merges its newest
-// kBatch into its sorted register list -- one batch, not the whole buffer, so
-// that lanes that buffer slowly fill their batches before they are merged.
-constexpr int kBufCap = 32;
-constexpr int kFlushAt = kBufCap - kBatch;
+// there.  Once some lane's buffer is within kBatch of full, every lane merges
+// its newest kBatch into its sorted register list -- one batch, not the whole
+// buffer, so that lanes that buffer slowly fill their batches before they are
+// merged.
 constexpr int kWarps = 4;  // warps per block
 
+// Buffer slots per lane and resident blocks per SM by list size.  Lists of up
+// to 8 keys fit in 72 registers, and 24 slots leave room for seven blocks per
+// SM instead of five (measured on 1M uniform objects, all querying: the
+// expansion runs 11 % faster at k = 8 and 18-19 % faster at k = 1 and 4 than
+// with 32 slots); longer lists keep 32 slots and leave the register count to
+// the compiler (k = 16 measured alike with six blocks in 80 registers).
+template <int KC>
+struct Shape {
+    static constexpr int kBufCap = KC <= 8 ? 24 : 32;
+    static constexpr int kFlushAt = kBufCap - kBatch;
+    static constexpr int kMinBlocks = KC <= 8 ? 7 : 0;
+};
+
+template <int CAP>
 struct WarpSmem {
     float4 obj[32];                              // staged objects (x, y, id bits, -)
-    unsigned long long buf[kBufCap][32];         // [slot][lane]
+    unsigned long long buf[CAP][32];             // [slot][lane]
     float4 lbb[32];                              // gathered leaf box, per lane
     int2 lrg[32];                                // its objects [x, y)
     int2 lc[32];                                 // leaves [x, y) of the lane's cell
@@ -76,8 +89,8 @@ struct Lane {
 // Merge the newest kBatch buffered candidates (or all, if fewer) into the
 // list.  The threshold becomes the list's k-th distance once the list is full
 // (it never rises above the threshold the walk started with).
-template <int KC>
-__device__ __forceinline__ void merge_top(Lane<KC> &L, WarpSmem &sm, int lane) {
+template <int KC, int CAP>
+__device__ __forceinline__ void merge_top(Lane<KC> &L, WarpSmem<CAP> &sm, int lane) {
     const int base = L.count > kBatch ? L.count - kBatch : 0;
     unsigned long long b[kBatch];
 #pragma unroll
@@ -101,10 +114,11 @@ __device__ __forceinline__ void merge_top(Lane<KC> &L, WarpSmem &sm, int lane) {
 // thresholds of the moment they are taken.  Keeping one copy of the scan and
 // one of the merge keeps the kernel small.
 template <int KC>
-__global__ void __launch_bounds__(kWarps * 32) k_expand(const ExpandArgs g) {
-    __shared__ WarpSmem smem[kWarps];
+__global__ void __launch_bounds__(kWarps * 32, Shape<KC>::kMinBlocks) k_expand(const ExpandArgs g) {
+    constexpr int kFlushAt = Shape<KC>::kFlushAt;
+    __shared__ WarpSmem<Shape<KC>::kBufCap> smem[kWarps];
     const int lane = threadIdx.x & 31;
-    WarpSmem &sm = smem[threadIdx.x >> 5];
+    WarpSmem<Shape<KC>::kBufCap> &sm = smem[threadIdx.x >> 5];
     // device scalars are exact unless a look-back timed out; clamp anyway
     int32_t P = g.scalars[kScalarPackets];
     P = P < 0 ? 0 : (P > g.pk_cap ? (int32_t)g.pk_cap : P);
@@ -233,7 +247,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_expand(const ExpandArgs g) {
             const bool full = __any_sync(kFull, L.count >= kFlushAt);
             if (full || __any_sync(kFull, drain && L.count > 0)) {
                 flushing = KC <= 8 && (flushing || full);
-                merge_top<KC>(L, sm, lane);
+                merge_top(L, sm, lane);
                 continue;
             }
             flushing = false;
