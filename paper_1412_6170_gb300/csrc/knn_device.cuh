@@ -262,18 +262,24 @@ __device__ __forceinline__ uint32_t lookback_warp(uint64_t *status, uint32_t til
 }
 
 // Per-thread look-back over a strided status array (one digit of a radix pass
-// per thread): status[t * stride].  The words of kAhead predecessors are read
-// together and then taken in order, so a run of tiles that have published only
-// their aggregates costs one memory round trip per kAhead tiles.
-__device__ __forceinline__ uint32_t lookback_thread(uint64_t *status, uint32_t tile,
-                                                    uint32_t stride, uint32_t epoch,
-                                                    uint32_t agg, uint32_t *err) {
+// per thread): status[t * stride].  Split in two so that a tile can publish its
+// aggregate as soon as it is known and do other work before it waits:
+// lookback_publish stores the aggregate (the inclusive prefix for tile 0);
+// lookback_resolve reads the words of kAhead predecessors together and takes
+// them in order -- a run of tiles that have published only their aggregates
+// costs one memory round trip per kAhead tiles -- then publishes this tile's
+// inclusive prefix and returns its exclusive prefix.
+__device__ __forceinline__ void lookback_publish(uint64_t *status, uint32_t tile,
+                                                 uint32_t stride, uint32_t epoch, uint32_t agg) {
+    st_status(&status[(uint64_t)tile * stride],
+              pack_status(epoch, tile == 0 ? kFlagPrefix : kFlagAgg, agg));
+}
+
+__device__ __forceinline__ uint32_t lookback_resolve(uint64_t *status, uint32_t tile,
+                                                     uint32_t stride, uint32_t epoch,
+                                                     uint32_t agg, uint32_t *err) {
     constexpr int kAhead = 8;
-    if (tile == 0) {
-        st_status(&status[0], pack_status(epoch, kFlagPrefix, agg));
-        return 0u;
-    }
-    st_status(&status[(uint64_t)tile * stride], pack_status(epoch, kFlagAgg, agg));
+    if (tile == 0) return 0u;
     uint32_t excl = 0;
     bool done = false;
     for (int64_t t = (int64_t)tile - 1; t >= 0 && !done; t -= kAhead) {

@@ -269,8 +269,9 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     const uint32_t texcl = block_excl_scan_256(tcnt, s_tmp, nullptr);
     const uint32_t gdig = block_excl_scan_256(hist[d], s_tmp, nullptr);
     s_texcl[d] = texcl;
-    const uint32_t back = lookback_thread(status + d, tile, 256u, epoch, tcnt, err);
-    s_gbase[d] = gdig + back;
+    // the tile's digit counts go out first; the local sort runs while the
+    // predecessors' counts arrive, then the look-back takes them
+    lookback_publish(status + d, tile, 256u, epoch, tcnt);
     __syncthreads();
 
 #pragma unroll
@@ -282,6 +283,8 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
             s_vals[lpos] = v[j];
         }
     }
+    const uint32_t back = lookback_resolve(status + d, tile, 256u, epoch, tcnt, err);
+    s_gbase[d] = gdig + back;
     __syncthreads();
     const int64_t rem = n - base;
     const int tn = rem < kSortTile ? (int)rem : kSortTile;
