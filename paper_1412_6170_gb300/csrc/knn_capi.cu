@@ -140,8 +140,6 @@ size_t carve_scratch(World &w, char *base) {
     w.qs_leaf = c.take<int32_t>(Q);
     w.nav = c.take<uint32_t>(2 * Q);
     w.qcs = c.take<int32_t>(ncell);
-    w.npk = c.take<int32_t>(ncell);
-    w.pk_off = c.take<int32_t>(ncell);
     w.pk_start = c.take<int32_t>(Q + Q / 32 + 2);
     w.pk_len = c.take<int32_t>(Q + Q / 32 + 2);
     w.status = c.take<uint64_t>(status);

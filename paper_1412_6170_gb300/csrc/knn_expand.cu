@@ -120,8 +120,12 @@ __global__ void __launch_bounds__(kWarps * 32, Shape<KC>::kMinBlocks) k_expand(c
     const int lane = threadIdx.x & 31;
     WarpSmem<Shape<KC>::kBufCap> &sm = smem[threadIdx.x >> 5];
     // device scalars are exact unless a look-back timed out; clamp anyway
-    int32_t P = g.scalars[kScalarPackets];
-    P = P < 0 ? 0 : (P > g.pk_cap ? (int32_t)g.pk_cap : P);
+    // full packets at the front of the list, partial ones at its back
+    int32_t F = g.scalars[kScalarPackets];
+    F = F < 0 ? 0 : (F > g.pk_cap ? (int32_t)g.pk_cap : F);
+    int32_t Pp = g.scalars[kScalarPartialPackets];
+    Pp = Pp < 0 ? 0 : (Pp > g.pk_cap - F ? (int32_t)(g.pk_cap - F) : Pp);
+    const int32_t P = F + Pp;
     int32_t m = g.scalars[kScalarLeaves];
     m = m < 0 ? 0 : (m > g.leaf_cap ? (int32_t)g.leaf_cap : m);
     const int k = g.k;
@@ -133,8 +137,9 @@ __global__ void __launch_bounds__(kWarps * 32, Shape<KC>::kMinBlocks) k_expand(c
         if (lane == 0) p = (int32_t)atomicAdd(g.pk_counter, 1u);
         p = __shfl_sync(kFull, p, 0);
         if (p >= P) break;
-        const int32_t q0 = g.pk_start[p];
-        int32_t ql = g.pk_len[p];
+        const int64_t pi = p < F ? (int64_t)p : g.pk_cap - 1 - (int64_t)(p - F);
+        const int32_t q0 = g.pk_start[pi];
+        int32_t ql = g.pk_len[pi];
         if (q0 < 0 || ql < 1 || q0 >= g.n_q) continue;
         if (ql > 32) ql = 32;
         if (q0 + ql > g.n_q) ql = (int32_t)(g.n_q - q0);

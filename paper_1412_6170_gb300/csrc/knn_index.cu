@@ -896,12 +896,15 @@ void launch_queries_explicit(World &w, const Plan &p, const int32_t *q_id, const
 
 // First sorted query of every level-Gp cell (qcs[c], c in [0, ncell]): each
 // boundary between consecutive sorted queries fills the cells it crosses.
-__global__ void k_query_cells(const uint32_t *__restrict__ qs_key,
-                              const int32_t *__restrict__ scalars, int L, int Gp, int64_t ncell,
-                              int64_t nq_cap, int32_t *qcs) {
+__global__ void k_query_cells(const uint32_t *__restrict__ qs_key, int32_t *scalars, int L,
+                              int Gp, int64_t ncell, int64_t nq_cap, int32_t *qcs) {
     int32_t nv = scalars[kScalarValidQueries];
     if (nv < 0) nv = 0;
     if (nv > nq_cap) nv = (int32_t)nq_cap;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        scalars[kScalarPackets] = 0;
+        scalars[kScalarPartialPackets] = 0;
+    }
     const int sh = 2 * (L - Gp);
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j <= nv;
          j += (int64_t)gridDim.x * blockDim.x) {
@@ -912,27 +915,63 @@ __global__ void k_query_cells(const uint32_t *__restrict__ qs_key,
     }
 }
 
-__global__ void k_packets(const int32_t *__restrict__ qcs, const int32_t *__restrict__ pk_off,
-                          int64_t ncell, int64_t pk_cap, int32_t *pk_start, int32_t *pk_len) {
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell;
-         c += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t s = qcs[c], e = qcs[c + 1];
-        int32_t o = pk_off[c];
-        for (int32_t q = s; q < e && o >= 0 && o < pk_cap; q += 32, ++o) {
-            pk_start[o] = q;
-            pk_len[o] = e - q < 32 ? e - q : 32;
+// Packets of a cell: its queries 32 at a time, the last one partial.  Full
+// packets go to the front of the list and partial ones to the back (slots
+// pk_cap - 1 down), so that a persistent expansion taking the full ones first
+// ends on the cheaper partial ones.  Slots come from warp-aggregated atomic
+// counters; the order of packets changes nothing in the rows.
+__global__ void k_packets(const int32_t *__restrict__ qcs, int64_t ncell, int64_t pk_cap,
+                          int32_t *scalars, int32_t *pk_start, int32_t *pk_len) {
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t start = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    // every lane of a warp runs the same number of rounds
+    for (int64_t c0 = start - lane; c0 < ncell; c0 += stride) {
+        const int64_t c = c0 + lane;
+        int32_t s = 0, cnt = 0;
+        if (c < ncell) {
+            s = qcs[c];
+            cnt = qcs[c + 1] - s;
+            if (cnt < 0) cnt = 0;
+        }
+        const int32_t nfull = cnt >> 5;
+        const bool part = (cnt & 31) != 0;
+        int32_t inc = nfull;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(kFull, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const unsigned pm = __ballot_sync(kFull, part);
+        int32_t fbase = 0, pbase = 0;
+        if (lane == 31 && inc > 0) fbase = atomicAdd(scalars + kScalarPackets, inc);
+        if (lane == 0 && pm) pbase = atomicAdd(scalars + kScalarPartialPackets, __popc(pm));
+        fbase = __shfl_sync(kFull, fbase, 31);
+        pbase = __shfl_sync(kFull, pbase, 0);
+        const int64_t f0 = (int64_t)fbase + inc - nfull;
+        for (int32_t i = 0; i < nfull; ++i) {
+            const int64_t o = f0 + i;
+            if (o < pk_cap) {
+                pk_start[o] = s + 32 * i;
+                pk_len[o] = 32;
+            }
+        }
+        if (part) {
+            const int64_t o = pk_cap - 1 - ((int64_t)pbase + __popc(pm & ((1u << lane) - 1u)));
+            if (o >= 0) {
+                pk_start[o] = s + 32 * nfull;
+                pk_len[o] = cnt & 31;
+            }
         }
     }
 }
 
 void launch_packets(World &w, const Plan &p, int64_t n_q, cudaStream_t s) {
     const int64_t ncell = 1ll << (2 * p.Gp);
-    const int g = grid_for(ncell + 1, 256, num_sms(w.device) * 16);
+    const int g = grid_for(ncell, 256, num_sms(w.device) * 16);
     k_query_cells<<<grid_for(n_q + 1, 256, num_sms(w.device) * 8), 256, 0, s>>>(
         w.qs_key, w.scalars, p.L, p.Gp, ncell, n_q, w.qcs);
-    scan_excl(w, w.qcs, w.pk_off, ncell + 1, w.scalars + kScalarPackets, kCtrPacketScan, s,
-              true);
-    k_packets<<<g, 256, 0, s>>>(w.qcs, w.pk_off, ncell, packet_capacity(w), w.pk_start,
+    k_packets<<<g, 256, 0, s>>>(w.qcs, ncell, packet_capacity(w), w.scalars, w.pk_start,
                                 w.pk_len);
     w.launches += 2;
 }

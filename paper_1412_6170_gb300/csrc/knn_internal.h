@@ -31,11 +31,12 @@ constexpr int kScanTile = 2048;
 // right after the build and at the last tick (64-bit, two words each).
 enum Scalar : int { kScalarLeaves = 0, kScalarValidQueries = 1, kScalarPackets = 2,
                     kScalarIndexSig = 3, kScalarIndexAge = 4, kScalarRebuild = 5,
-                    kScalarCostBase = 6, kScalarCostNow = 8, kNumScalars = 16 };
+                    kScalarCostBase = 6, kScalarCostNow = 8, kScalarPartialPackets = 10,
+                    kNumScalars = 16 };
 
 // Ticket counters (one per single-pass launch site in a tick).
 enum Counter : int { kCtrObjSort = 0, kCtrQuerySort = 4, kCtrLeaves = 8, kCtrQueryScan = 9,
-                     kCtrPacketScan = 10, kCtrExpand = 11, kCtrReuseScan = 12,
+                     kCtrExpand = 11, kCtrReuseScan = 12,
                      kCtrIterLeft = 13 /* and 14: iterative expansion */ };
 
 struct Plan {
@@ -106,7 +107,7 @@ struct World {
     uint32_t *qs_key = nullptr;
     int32_t *qs_leaf = nullptr;  // a leaf at (or next to) each sorted query
     uint32_t *nav = nullptr;     // iterative expansion: per sorted query, left and right position
-    int32_t *qcs = nullptr, *npk = nullptr, *pk_off = nullptr;
+    int32_t *qcs = nullptr;
     int32_t *pk_start = nullptr, *pk_len = nullptr;
     uint64_t *status = nullptr;
     size_t status_words = 0;

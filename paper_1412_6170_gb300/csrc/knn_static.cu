@@ -93,8 +93,6 @@ size_t cut_scratch(knnq::World &w, unsigned char *base, int64_t n_q) {
     w.qs_key = c.take<uint32_t>(n_q);
     w.qs_leaf = c.take<int32_t>(n_q);
     w.qcs = c.take<int32_t>(ncell);
-    w.npk = c.take<int32_t>(ncell);
-    w.pk_off = c.take<int32_t>(ncell);
     w.pk_start = c.take<int32_t>(n_q + n_q / 32 + 2);
     w.pk_len = c.take<int32_t>(n_q + n_q / 32 + 2);
     w.status = c.take<uint64_t>(status);
