@@ -137,12 +137,34 @@ void launch_updates(World &w, const int32_t *id, const float *ux, const float *u
 __global__ void __launch_bounds__(256) k_keys_hist(
     const float *__restrict__ px, const float *__restrict__ py, int64_t n, float x0, float y0,
     float scale, int L, int passes, uint32_t *__restrict__ key, int32_t *__restrict__ val,
-    uint32_t *hist, const int32_t *rebuild) {
+    uint32_t *hist, const int32_t *rebuild, bool vec4) {
     if (rebuild && *rebuild == 0) return;  // this tick reuses the leaves
     __shared__ uint32_t h[4][256];
     for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) (&h[0][0])[i] = 0;
     __syncthreads();
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+    // four objects per thread with 16-byte loads and stores when every array
+    // is 16-byte aligned (world arrays are; caller arrays may not be)
+    const int64_t n4 = vec4 ? n & ~int64_t(3) : 0;
+    for (int64_t i = 4 * (blockIdx.x * (int64_t)blockDim.x + threadIdx.x); i < n4;
+         i += 4 * (int64_t)gridDim.x * blockDim.x) {
+        const float4 xv = *reinterpret_cast<const float4 *>(px + i);
+        const float4 yv = *reinterpret_cast<const float4 *>(py + i);
+        uint4 kv;
+        kv.x = morton_key(xv.x, yv.x, x0, y0, scale, L);
+        kv.y = morton_key(xv.y, yv.y, x0, y0, scale, L);
+        kv.z = morton_key(xv.z, yv.z, x0, y0, scale, L);
+        kv.w = morton_key(xv.w, yv.w, x0, y0, scale, L);
+        *reinterpret_cast<uint4 *>(key + i) = kv;
+        *reinterpret_cast<int4 *>(val + i) =
+            make_int4((int32_t)i, (int32_t)i + 1, (int32_t)i + 2, (int32_t)i + 3);
+        for (int p = 0; p < passes; ++p) {
+            atomicAdd(&h[p][(kv.x >> (8 * p)) & 255u], 1u);
+            atomicAdd(&h[p][(kv.y >> (8 * p)) & 255u], 1u);
+            atomicAdd(&h[p][(kv.z >> (8 * p)) & 255u], 1u);
+            atomicAdd(&h[p][(kv.w >> (8 * p)) & 255u], 1u);
+        }
+    }
+    for (int64_t i = n4 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t k = morton_key(px[i], py[i], x0, y0, scale, L);
         key[i] = k;
@@ -318,9 +340,13 @@ void launch_object_sort(World &w, const Plan &p, cudaStream_t s) {
     // with index reuse on, the sort and the leaf split run only on rebuild ticks
     const int32_t *rebuild = p.reuse_age > 0 ? w.scalars + kScalarRebuild : nullptr;
     cudaMemsetAsync(w.hist, 0, sizeof(uint32_t) * 4 * 256, s);
-    k_keys_hist<<<grid_for(w.n, 256, num_sms(w.device) * 4), 256, 0, s>>>(
+    const bool vec4 = ((reinterpret_cast<uintptr_t>(w.px) | reinterpret_cast<uintptr_t>(w.py) |
+                        reinterpret_cast<uintptr_t>(w.key[0]) |
+                        reinterpret_cast<uintptr_t>(w.val[0])) & 15u) == 0;
+    // two blocks per SM: the per-block histograms merge with few global atomics
+    k_keys_hist<<<grid_for(vec4 ? (w.n + 3) / 4 : w.n, 256, num_sms(w.device) * 2), 256, 0, s>>>(
         w.px, w.py, w.n, w.desc.x0, w.desc.y0, w.scale, p.L, p.passes, w.key[0], w.val[0],
-        w.hist, rebuild);
+        w.hist, rebuild, vec4);
     ++w.launches;
     radix_sort(w, w.n, p.passes, kCtrObjSort, s, rebuild);
 }

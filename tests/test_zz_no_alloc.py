@@ -81,6 +81,29 @@ def test_static_matches_regular_path_twice_in_a_row():
     assert same(static_path(x1, y1, q1, 16), first)
 
 
+def test_static_accepts_positions_not_16_byte_aligned():
+    # caller arrays that start 4 bytes past a 16-byte boundary take the
+    # kernels' scalar paths; the rows are the same
+    import torch
+    x, y = synth.uniform_positions(20003, 24)
+    q = np.arange(0, 20003, 3, dtype=np.int32)
+    xs = torch.zeros(len(x) + 1, dtype=torch.float32, device="cuda")
+    ys = torch.zeros(len(y) + 1, dtype=torch.float32, device="cuda")
+    xs[1:] = torch.from_numpy(x).cuda()
+    ys[1:] = torch.from_numpy(y).cuda()
+    assert (xs[1:].data_ptr() % 16) != 0
+    qd = dev(q)
+    out_ids = torch.empty((len(q), 8), dtype=torch.int32, device="cuda")
+    out_d2 = torch.empty((len(q), 8), dtype=torch.float32, device="cuda")
+    desc = knnq.knn_world_desc(0.0, 0.0, 1.0, 0, 0, 64, len(q))
+    knnq.knn_query_static(desc, xs[1:].data_ptr(), ys[1:].data_ptr(), len(x), qd.data_ptr(),
+                          None, None, len(q), 8, out_ids.data_ptr(), out_d2.data_ptr(),
+                          torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    got = (out_ids.cpu().numpy(), out_d2.cpu().numpy())
+    assert same(got, regular_path(x, y, q, 8))
+
+
 def test_static_rejects_sizes_beyond_its_scratch():
     lib = knnq.lib()
     desc = knnq.knn_world_desc(0.0, 0.0, 1.0, 0, 0, 64, 10)
