@@ -673,11 +673,11 @@ void launch_leaves(World &w, const Plan &p, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // Exclusive scan of int32 (single pass, look-back).  In place is allowed.
 
-// PACKETS: the value of entry c is the number of 32-query packets of cell c,
-// ceil((in[c+1] - in[c]) / 32) with in = the cells' first sorted query
-// (0 for the last entry); otherwise it is in[c].
-template <bool PACKETS>
-__global__ void __launch_bounds__(256) k_scan_excl(const int32_t *in, int32_t *out, int64_t len,
+// GATHER: the value of entry c is in[idx[c]] (0 for the last entry);
+// otherwise it is in[c].
+template <bool GATHER>
+__global__ void __launch_bounds__(256) k_scan_excl(const int32_t *in, const int32_t *idx,
+                                                   int32_t *out, int64_t len,
                                                    int32_t *total, uint64_t *status,
                                                    uint32_t *ticket,
                                                    const uint32_t *__restrict__ tickinfo,
@@ -700,28 +700,25 @@ __global__ void __launch_bounds__(256) k_scan_excl(const int32_t *in, int32_t *o
     // 8 consecutive entries per thread, read as two 16-byte words when whole
     // (the buffers are 256-byte aligned and base is a multiple of 8)
     const bool whole = base + 8 <= len;
-    int32_t x[9];
-    if (whole) {
+    int32_t v[8];
+    if (GATHER) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int32_t t = base + q + 1 < len ? idx[base + q] : -1;
+            v[q] = t >= 0 && t < len - 1 ? in[t] : 0;
+        }
+    } else if (whole) {
         const int4 a = *reinterpret_cast<const int4 *>(in + base);
         const int4 b = *reinterpret_cast<const int4 *>(in + base + 4);
-        x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
-        x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
     } else {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) x[q] = base + q < len ? in[base + q] : 0;
+        for (int q = 0; q < 8; ++q) v[q] = base + q < len ? in[base + q] : 0;
     }
-    x[8] = PACKETS && base + 8 < len ? in[base + 8] : 0;
-    int32_t v[8];
     uint32_t sum = 0;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const int64_t c = base + q;
-        if (PACKETS)
-            v[q] = c + 1 < len ? (x[q + 1] - x[q] + 31) / 32 : 0;
-        else
-            v[q] = c < len ? x[q] : 0;
-        sum += (uint32_t)v[q];
-    }
+    for (int q = 0; q < 8; ++q) sum += (uint32_t)v[q];
     const uint32_t off = block_excl_scan_256(sum, s_tmp, &s_total);
     if (tid < 32) {
         const uint32_t ex = lookback_warp(status, tile, tickinfo[0] + site, s_total, err);
@@ -748,16 +745,17 @@ __global__ void __launch_bounds__(256) k_scan_excl(const int32_t *in, int32_t *o
 
 // skip_if: when non-null and nonzero on the device, the launch does nothing.
 // len_minus_1: when non-null, the device value + 1 (at most len) is the length.
+// gather_idx: when non-null, entry c is in[gather_idx[c]] (and the last entry 0).
 static void scan_excl(World &w, const int32_t *in, int32_t *out, int64_t len, int32_t *total,
-                      int counter, cudaStream_t s, bool packets = false,
+                      int counter, cudaStream_t s, const int32_t *gather_idx = nullptr,
                       const int32_t *skip_if = nullptr, const int32_t *len_minus_1 = nullptr) {
     const int tiles = (int)((len + kScanTile - 1) / kScanTile);
-    if (packets)
-        k_scan_excl<true><<<tiles, 256, 0, s>>>(in, out, len, total, w.status,
+    if (gather_idx)
+        k_scan_excl<true><<<tiles, 256, 0, s>>>(in, gather_idx, out, len, total, w.status,
                                                 w.counters + counter, w.tickinfo, w.site++,
                                                 w.err, skip_if, len_minus_1);
     else
-        k_scan_excl<false><<<tiles, 256, 0, s>>>(in, out, len, total, w.status,
+        k_scan_excl<false><<<tiles, 256, 0, s>>>(in, nullptr, out, len, total, w.status,
                                                  w.counters + counter, w.tickinfo, w.site++,
                                                  w.err, skip_if, len_minus_1);
     ++w.launches;
@@ -768,7 +766,15 @@ static void scan_excl(World &w, const int32_t *in, int32_t *out, int64_t len, in
 // ordered by the issuer's place in the sorted object order (a counting sort),
 // which is the Morton order of their centres.
 
-// Counting sort, first half: every valid query counts one more query at its
+// Two counting sorts order the queries by their issuers' places p in the
+// sorted object order.  When most objects query (n_q >= n / 2) the queries are
+// counted by issuer id: the counting is then coalesced, an issuer with a
+// single query passes that query's index along with its count, and only
+// issuers with several queries need the rank placement.  With few queries the
+// per-object arrays would cost more than the queries, so they are counted by
+// place instead (the issuer's place found through the inverse order).
+
+// By place, first half: every valid query counts one more query at its
 // issuer's sorted place p and keeps p and its rank among the queries of that
 // issuer (the count before its own).
 __global__ void k_query_count(const int32_t *__restrict__ q_id, int64_t n_q, int64_t n,
@@ -793,8 +799,8 @@ __global__ void k_query_count(const int32_t *__restrict__ q_id, int64_t n_q, int
     }
 }
 
-// Counting sort, second half: every valid query takes the slot of its rank in
-// its issuer's range [qoff[p], qoff[p+1]) and records its caller index there.
+// By place, second half: every valid query takes the slot of its rank in its
+// issuer's range [qoff[p], qoff[p+1]) and records its caller index there.
 __global__ void k_query_place(int64_t n_q, int64_t n, const int32_t *__restrict__ qp,
                               const int32_t *__restrict__ qrank,
                               const int32_t *__restrict__ qoff, int32_t *qs_orig) {
@@ -808,17 +814,69 @@ __global__ void k_query_place(int64_t n_q, int64_t n, const int32_t *__restrict_
     }
 }
 
+// By issuer id, first half: every valid query counts one more query at its
+// issuer and keeps its rank among that issuer's queries and, in qidx[issuer],
+// its own index (the only one there when the issuer has a single query).  A
+// second query at one issuer raises qcnt[n], which makes k_query_place_id run.
+__global__ void k_query_count_id(const int32_t *__restrict__ q_id, int64_t n_q, int64_t n,
+                                 int32_t *qcnt, int k, int32_t *out_ids, float *out_d2,
+                                 uint32_t *err, int32_t *__restrict__ qrank,
+                                 int32_t *__restrict__ qidx) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_q;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t s = q_id[i];
+        if (s < 0 || s >= n) {
+            atomicOr(err, kErrBadQuery);
+            for (int r = 0; r < k; ++r) {
+                out_ids[i * k + r] = -1;
+                out_d2[i * k + r] = __int_as_float(0x7f800000);
+            }
+            continue;
+        }
+        const int32_t r = atomicAdd(&qcnt[s], 1);
+        qrank[i] = r;
+        qidx[s] = (int32_t)i;
+        if (r == 1) qcnt[n] = 1;
+    }
+}
+
+// By issuer id, rank placement, only when some issuer has several queries
+// (qcnt[n] set): every valid query takes the slot of its rank in the range of
+// its issuer's place p and records its caller index there.
+__global__ void k_query_place_id(const int32_t *__restrict__ q_id, int64_t n_q, int64_t n,
+                                 const int32_t *__restrict__ inv,
+                                 const int32_t *__restrict__ qrank,
+                                 const int32_t *__restrict__ qoff,
+                                 const int32_t *__restrict__ qcnt, int32_t *qs_orig) {
+    if (qcnt[n] == 0) return;  // the same for every block of the launch
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_q;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t s = q_id[i];
+        if (s < 0 || s >= n) continue;
+        const int32_t p = inv[s];
+        if (p < 0 || p >= n) continue;
+        const int32_t j = qoff[p] + qrank[i];
+        if (j < 0 || j >= n_q) continue;  // only after a timed-out look-back
+        qs_orig[j] = (int32_t)i;
+    }
+}
+
 // Walk the sorted objects in order and copy each one's position, id and key
-// into the slots of its queries: sequential reads, sequential writes.
+// into the slots of its queries: sequential reads, sequential writes.  With
+// qidx (counting by issuer id), an object with a single query also records
+// that query's caller index.
 __global__ void k_query_fill(int64_t n, int64_t n_q, const int32_t *__restrict__ qoff,
                              const float *__restrict__ xs, const float *__restrict__ ys,
                              const int32_t *__restrict__ sid, const uint32_t *__restrict__ skey,
-                             const int32_t *__restrict__ obj_leaf, float *qs_x, float *qs_y,
-                             int32_t *qs_id, uint32_t *qs_key, int32_t *qs_leaf) {
+                             const int32_t *__restrict__ obj_leaf,
+                             const int32_t *__restrict__ qidx, float *qs_x, float *qs_y,
+                             int32_t *qs_id, uint32_t *qs_key, int32_t *qs_leaf,
+                             int32_t *qs_orig) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
         int32_t a = qoff[p], b = qoff[p + 1];
         if (a >= b) continue;
+        const bool single = b - a == 1;
         if (a < 0) a = 0;
         if (b > n_q) b = (int32_t)n_q;
         const float x = xs[p], y = ys[p];
@@ -832,26 +890,44 @@ __global__ void k_query_fill(int64_t n, int64_t n_q, const int32_t *__restrict__
             qs_key[j] = key;
             qs_leaf[j] = leaf;
         }
+        if (qidx && single && a < b && id >= 0 && id < n) qs_orig[a] = qidx[id];
     }
 }
 
 void launch_queries_at_issuers(World &w, const Plan &p, const int32_t *q_id, int64_t n_q,
                                int32_t k, int32_t *out_ids, float *out_d2, cudaStream_t s) {
-    // each query's sorted place and rank live in the sort's second buffers,
-    // free once the leaf-ordered store is written
+    // per-query and per-issuer scratch lives in the sort's second buffers, free
+    // once the leaf-ordered store is written
     const int r = p.passes & 1;
-    int32_t *qp = reinterpret_cast<int32_t *>(w.key[r ^ 1]), *qrank = w.val[r ^ 1];
+    int32_t *aux = reinterpret_cast<int32_t *>(w.key[r ^ 1]), *qrank = w.val[r ^ 1];
+    const bool by_id = 2 * n_q >= w.n;
     cudaMemsetAsync(w.qcnt, 0, sizeof(int32_t) * (size_t)(w.n + 1), s);
     const int g = grid_for(n_q, 256, num_sms(w.device) * 8);
-    k_query_count<<<g, 256, 0, s>>>(q_id, n_q, w.n, w.inv, w.qcnt, k, out_ids, out_d2, w.err,
-                                    qp, qrank);
-    scan_excl(w, w.qcnt, w.qoff, w.n + 1, w.scalars + kScalarValidQueries, kCtrQueryScan, s);
-    k_query_place<<<g, 256, 0, s>>>(n_q, w.n, qp, qrank, w.qoff, w.qs_orig);
     const uint32_t *skey = w.key[p.passes & 1];
-    k_query_fill<<<grid_for(w.n, 256, num_sms(w.device) * 8), 256, 0, s>>>(
-        w.n, n_q, w.qoff, w.xs, w.ys, w.sid, skey, w.obj_leaf, w.qs_x, w.qs_y, w.qs_id,
-        w.qs_key, w.qs_leaf);
-    w.launches += 3;
+    const int gf = grid_for(w.n, 256, num_sms(w.device) * 8);
+    if (by_id) {
+        // aux: each issuer's last query
+        k_query_count_id<<<g, 256, 0, s>>>(q_id, n_q, w.n, w.qcnt, k, out_ids, out_d2, w.err,
+                                           qrank, aux);
+        scan_excl(w, w.qcnt, w.qoff, w.n + 1, w.scalars + kScalarValidQueries, kCtrQueryScan,
+                  s, w.sid);  // counts taken in sorted-object order
+        k_query_fill<<<gf, 256, 0, s>>>(w.n, n_q, w.qoff, w.xs, w.ys, w.sid, skey, w.obj_leaf,
+                                        aux, w.qs_x, w.qs_y, w.qs_id, w.qs_key, w.qs_leaf,
+                                        w.qs_orig);
+        k_query_place_id<<<g, 256, 0, s>>>(q_id, n_q, w.n, w.inv, qrank, w.qoff, w.qcnt,
+                                           w.qs_orig);
+    } else {
+        // aux: each query's issuer place
+        k_query_count<<<g, 256, 0, s>>>(q_id, n_q, w.n, w.inv, w.qcnt, k, out_ids, out_d2, w.err,
+                                        aux, qrank);
+        scan_excl(w, w.qcnt, w.qoff, w.n + 1, w.scalars + kScalarValidQueries, kCtrQueryScan,
+                  s);
+        k_query_place<<<g, 256, 0, s>>>(n_q, w.n, aux, qrank, w.qoff, w.qs_orig);
+        k_query_fill<<<gf, 256, 0, s>>>(w.n, n_q, w.qoff, w.xs, w.ys, w.sid, skey, w.obj_leaf,
+                                        nullptr, w.qs_x, w.qs_y, w.qs_id, w.qs_key, w.qs_leaf,
+                                        w.qs_orig);
+    }
+    w.launches += 4;
 }
 
 // Leaf next to a level-L key in Morton order: the last leaf of the key's
@@ -1087,7 +1163,7 @@ void launch_index_reuse(World &w, const Plan &p, cudaStream_t s) {
     cudaMemsetAsync(lcnt, 0, sizeof(int32_t) * (size_t)len, s);
     k_reuse_assign<<<g, 256, 0, s>>>(w.px, w.py, w.n, w.desc.x0, w.desc.y0, w.scale, p.L, p.G,
                                      w.cb, w.bcode, w.scalars, w.key[r ^ 1], w.val[r ^ 1], lcnt);
-    scan_excl(w, lcnt, w.bstart, len, nullptr, kCtrReuseScan, s, false,
+    scan_excl(w, lcnt, w.bstart, len, nullptr, kCtrReuseScan, s, nullptr,
               w.scalars + kScalarRebuild, w.scalars + kScalarLeaves);
     k_reuse_rank<<<g, 256, 0, s>>>(w.n, w.val[r ^ 1], w.bstart, lcnt, w.scalars, w.val[r],
                                    w.inv);

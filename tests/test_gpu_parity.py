@@ -242,6 +242,19 @@ def test_repeated_query_ids_and_empty_tick():
     compare_ticks(x, y, [tick(q, 10), tick(np.zeros(0, np.int32), 4), tick(q[:1], 1)])
 
 
+@pytest.mark.parametrize("nq", [1200, 2600, 5000])
+def test_repeated_query_ids_both_counting_sorts(nq):
+    # fewer queries than half the objects are counted by place, more by issuer
+    # id; both with issuers that query several times and issuers that query once
+    r = np.random.default_rng(17)
+    n = 5000
+    x, y = r.random(n).astype(np.float32), r.random(n).astype(np.float32)
+    q = r.integers(0, n, nq).astype(np.int32)
+    q[:40] = 23
+    q[40:43] = 4999
+    compare_ticks(x, y, [tick(q, 9), tick(r.permutation(n)[:nq].astype(np.int32), 6)])
+
+
 def test_domain_offset_and_scale():
     r = np.random.default_rng(8)
     n = 20000
