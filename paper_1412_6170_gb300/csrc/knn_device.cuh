@@ -216,18 +216,23 @@ __device__ __forceinline__ uint32_t warp_sum_u32(uint32_t v) {
     return v;
 }
 
-// Exclusive prefix of `agg` over all earlier tiles; called by one full warp.
-// Publishes this tile's aggregate, looks back 32 predecessors at a time and
-// publishes the inclusive prefix.  Returns the exclusive prefix in all lanes.
-__device__ __forceinline__ uint32_t lookback_warp(uint64_t *status, uint32_t tile,
-                                                  uint32_t epoch, uint32_t agg,
-                                                  uint32_t *err) {
+// Exclusive prefix of `agg` over all earlier tiles, called by one full warp,
+// in two halves so that a tile can publish its aggregate as soon as it is
+// known and do other work before it waits: lookback_warp_publish stores the
+// aggregate (the inclusive prefix for tile 0); lookback_warp_resolve looks
+// back 32 predecessors at a time, publishes the inclusive prefix and returns
+// the exclusive prefix in all lanes.
+__device__ __forceinline__ void lookback_warp_publish(uint64_t *status, uint32_t tile,
+                                                      uint32_t epoch, uint32_t agg) {
+    if ((threadIdx.x & 31) == 0)
+        st_status(&status[tile], pack_status(epoch, tile == 0 ? kFlagPrefix : kFlagAgg, agg));
+}
+
+__device__ __forceinline__ uint32_t lookback_warp_resolve(uint64_t *status, uint32_t tile,
+                                                          uint32_t epoch, uint32_t agg,
+                                                          uint32_t *err) {
     const int lane = threadIdx.x & 31;
-    if (tile == 0) {
-        if (lane == 0) st_status(&status[0], pack_status(epoch, kFlagPrefix, agg));
-        return 0u;
-    }
-    if (lane == 0) st_status(&status[tile], pack_status(epoch, kFlagAgg, agg));
+    if (tile == 0) return 0u;
     uint32_t excl = 0;
     int64_t t = (int64_t)tile - 1;
     uint32_t spins = 0;
@@ -259,6 +264,13 @@ __device__ __forceinline__ uint32_t lookback_warp(uint64_t *status, uint32_t til
     }
     if (lane == 0) st_status(&status[tile], pack_status(epoch, kFlagPrefix, excl + agg));
     return excl;
+}
+
+__device__ __forceinline__ uint32_t lookback_warp(uint64_t *status, uint32_t tile,
+                                                  uint32_t epoch, uint32_t agg,
+                                                  uint32_t *err) {
+    lookback_warp_publish(status, tile, epoch, agg);
+    return lookback_warp_resolve(status, tile, epoch, agg, err);
 }
 
 // Per-thread look-back over a strided status array (one digit of a radix pass

@@ -475,8 +475,22 @@ __global__ void __launch_bounds__(256) k_leaves(
     if (tid == 0) s_ngap = 0;
     const uint32_t off = block_excl_scan_256(cnt, s_tmp, &s_total);
     tile_total = s_total;
+    if (tid < 32) lookback_warp_publish(status, tile, tickinfo[0] + site, tile_total);
+    // leaf-ordered SoA (a5): needs no leaf numbers, so it runs while the
+    // predecessors' leaf counts arrive
+    for (int e = tid; e < kLeafTile; e += 256) {
+        const int64_t i = t0 + e;
+        if (i >= n) break;
+        int32_t id = svals[i];
+        if (id < 0 || id >= n) id = 0;  // only after a timed-out look-back
+        xs[i] = px[id];
+        ys[i] = py[id];
+        sid[i] = id;
+        inv[id] = (int32_t)i;
+    }
     if (tid < 32) {
-        const uint32_t ex = lookback_warp(status, tile, tickinfo[0] + site, tile_total, err);
+        const uint32_t ex =
+            lookback_warp_resolve(status, tile, tickinfo[0] + site, tile_total, err);
         if (tid == 0) s_excl = ex;
     }
     __syncthreads();
@@ -594,17 +608,6 @@ __global__ void __launch_bounds__(256) k_leaves(
                 }
             }
         }
-    }
-    // leaf-ordered SoA (a5)
-    for (int e = tid; e < kLeafTile; e += 256) {
-        const int64_t i = t0 + e;
-        if (i >= n) break;
-        int32_t id = svals[i];
-        if (id < 0 || id >= n) id = 0;  // only after a timed-out look-back
-        xs[i] = px[id];
-        ys[i] = py[id];
-        sid[i] = id;
-        inv[id] = (int32_t)i;
     }
 }
 
