@@ -39,6 +39,9 @@ struct ExpandArgs {
     int32_t *out_ids;
     float *out_d2;
     float x0, y0, scale_g, side;
+    float scale_l;  // level-L scale of the keys
+    const uint32_t *bcode;
+    int narrow;  // crowded cells: only leaves whose key range meets the packet box
     float spec2;  // alpha^2 of the speculative first threshold (0: none)
     int L, G, k;
     int vec_out;  // rows may be written with 16-byte stores
@@ -99,6 +102,46 @@ __device__ __forceinline__ void merge_top(Lane<KC> &L, WarpSmem<CAP> &sm, int la
     merge_batch<KC>(L.lst, b);
     L.count = base;
     L.thr = fminf(L.thr, __uint_as_float((uint32_t)(L.lst[KC - 1] >> 32)));
+}
+
+// The leaves of a crowded level-G cell whose key range can meet the box
+// [bx0 - R, bx1 + R] x [by0 - R, by1 + R] (binary searches on the leaf codes).
+// Every point of the box has a key between the keys of its lower-left and
+// upper-right corners (clamped to the cell, rounded outward like the cell
+// box), so a leaf whose quadrant meets the box has its first code at most
+// the upper key, and is the leaf holding the lower key or a later one.  This
+// needs every object inside its leaf's quadrant, which holds for leaves built
+// this tick (not for reused ones, whose objects may have moved).  Kept out of
+// line: the rare call costs less than the registers it would take inline
+// (measured: 3.5 % and 8 % faster on clustered objects at k = 32 and 8,
+// uniform objects unchanged).
+__device__ __noinline__ int2 narrow_leaves(const ExpandArgs &g, int2 lc, int cx, int cy, float bx0,
+                                           float bx1, float by0, float by1, float Rb) {
+    const int sh = g.L - g.G;
+    const uint32_t ax0 = (uint32_t)cx << sh, ax1 = ax0 + ((1u << sh) - 1u);
+    const uint32_t ay0 = (uint32_t)cy << sh, ay1 = ay0 + ((1u << sh) - 1u);
+    uint32_t kx0 = cell_coord(__fsub_rd(bx0, Rb), g.x0, g.scale_l, g.L);
+    uint32_t kx1 = cell_coord(__fadd_ru(bx1, Rb), g.x0, g.scale_l, g.L);
+    uint32_t ky0 = cell_coord(__fsub_rd(by0, Rb), g.y0, g.scale_l, g.L);
+    uint32_t ky1 = cell_coord(__fadd_ru(by1, Rb), g.y0, g.scale_l, g.L);
+    kx0 = kx0 > ax0 ? kx0 : ax0;
+    kx1 = kx1 < ax1 ? kx1 : ax1;
+    ky0 = ky0 > ay0 ? ky0 : ay0;
+    ky1 = ky1 < ay1 ? ky1 : ay1;
+    if (kx0 > kx1 || ky0 > ky1) return make_int2(0, 0);
+    const uint32_t zlo = interleave(kx0, ky0), zhi = interleave(kx1, ky1);
+    int32_t a0 = lc.x, b0 = lc.y, a1 = lc.x, b1 = lc.y;
+    while (a0 < b0 || a1 < b1) {  // first codes > zhi and > zlo
+        if (a0 < b0) {
+            const int32_t mid = (a0 + b0) >> 1;
+            if (g.bcode[mid] <= zhi) a0 = mid + 1; else b0 = mid;
+        }
+        if (a1 < b1) {
+            const int32_t mid = (a1 + b1) >> 1;
+            if (g.bcode[mid] <= zlo) a1 = mid + 1; else b1 = mid;
+        }
+    }
+    return make_int2(a1 > lc.x ? a1 - 1 : lc.x, a0);
 }
 
 // One packet = one pass of a single loop.  Each iteration (a) merges a batch
@@ -219,14 +262,17 @@ __global__ void __launch_bounds__(kWarps * 32, Shape<KC>::kMinBlocks) k_expand(c
         unsigned pend;
         float bx0 = 0.f, bx1 = 0.f, by0 = 0.f, by1 = 0.f;
         int ccx = 0, ccy = 0, cx0 = 0, cx1 = 0, cy0 = 0, cy1 = 0, rmax = 0;
+        float Rb = kInf;
         auto bound = [&]() {
             const float R2 = warp_max(active ? L.thr : 0.f);
             if (!(R2 < kInf)) {
                 cx0 = 0; cx1 = lim; cy0 = 0; cy1 = lim;
+                Rb = kInf;
             } else {
                 // |q - p| per axis is at most sqrt(R2) (1 + 2^-22) for any object
                 // that can enter a list; round the box outward.
                 const float R = __fmul_ru(__fsqrt_ru(R2), 1.0000010f);
+                Rb = R;
                 cx0 = cell_g(__fsub_rd(bx0, R), g.x0, g.scale_g, g.G);
                 cx1 = cell_g(__fadd_ru(bx1, R), g.x0, g.scale_g, g.G);
                 cy0 = cell_g(__fsub_rd(by0, R), g.y0, g.scale_g, g.G);
@@ -328,6 +374,8 @@ __global__ void __launch_bounds__(kWarps * 32, Shape<KC>::kMinBlocks) k_expand(c
                             lc.y = g.cb[c + 1];
                             lc.x = lc.x > 0 ? lc.x : 0;
                             lc.y = lc.y < m ? lc.y : m;
+                            if (g.narrow && lc.y - lc.x > 8 && Rb < kInf)
+                                lc = narrow_leaves(g, lc, cx, cy, bx0, bx1, by0, by1, Rb);
                         }
                     }
                     sm.lc[lane] = lc;
@@ -522,6 +570,9 @@ void launch_expand(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t *out
     a.spec2 = 1.0f + 3.0f / sqrtf((float)k) + 2.0f / (float)k;
     a.blevel = w.blevel;
     a.scale_g = ldexpf(w.scale, -(p.L - p.G));
+    a.scale_l = w.scale;
+    a.bcode = w.bcode;
+    a.narrow = p.reuse_age > 0 ? 0 : 1;
     a.L = p.L;
     a.G = p.G;
     a.k = k;

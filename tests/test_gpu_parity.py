@@ -115,6 +115,22 @@ def test_tuning_invariance(tuning):
     run_and_compare(w, tuning=tuning, what=f"tuning {tuning}")
 
 
+@pytest.mark.parametrize("k", [4, 8, 32])
+def test_crowded_cells_explicit_centres(k):
+    # a coarse cell map over small leaves: most cells hold many leaves, so the
+    # walk narrows them to the key range of the packet box; explicit centres
+    # (some outside the domain) and issuers at their positions
+    w = synth.skewed_moving(n=30000, k=k, ticks=2, seed=13, query_frac=0.4)
+    r = np.random.default_rng(14)
+    t0 = w.ticks[0]
+    nq = t0.q_id.shape[0]
+    qx = np.clip(r.normal(0.5, 0.3, nq), -0.2, 1.2).astype(np.float32)
+    qy = np.clip(r.normal(0.5, 0.3, nq), -0.2, 1.2).astype(np.float32)
+    w.ticks[0] = synth.Tick(t0.upd_id, t0.upd_x, t0.upd_y, t0.q_id, k, qx, qy)
+    run_and_compare(w, k_max=k, tuning=dict(leaf_capacity=4, grid_level=3, packet_level=3),
+                    what=f"crowded cells k={k}")
+
+
 def test_max_depth_invariance():
     w = synth.skewed_moving(n=20000, k=8, ticks=1, seed=12)
     for depth in (1, 3, 9):
