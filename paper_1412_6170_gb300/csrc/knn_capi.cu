@@ -40,14 +40,14 @@ int round_log4(double v) {
 int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
 // Automatic index parameters (none changes a result):
-//  leaf capacity th = 2k in [8, 256] (the paper ties th_quad to k);
+//  leaf capacity th = default_leaf_capacity(k);
 //  grid level G with about th/2 objects per cell, so most leaves are cells;
-//  packet level with about 48 queries per cell.
+//  packet level with about max(48, 12k) queries per cell.
 Plan make_plan(const World &w, int64_t n_q, int k) {
     Plan p{};
     p.L = w.L;
     p.passes = (2 * p.L + 7) / 8;
-    p.th = w.tuning.leaf_capacity > 0 ? w.tuning.leaf_capacity : clampi(2 * k, 8, 256);
+    p.th = w.tuning.leaf_capacity > 0 ? w.tuning.leaf_capacity : knnq::default_leaf_capacity(k);
     p.th = clampi(p.th, 1, knnq::kMaxLeafCapacity);
     const int gmax = w.gmax;
     int G = w.tuning.grid_level > 0 ? w.tuning.grid_level

@@ -170,7 +170,7 @@ extern "C" knn_status knn_query_static(const knn_world_desc *desc, const float *
     knnq::Plan p{};
     p.L = w.L;
     p.passes = (2 * p.L + 7) / 8;
-    p.th = w.tuning.leaf_capacity > 0 ? w.tuning.leaf_capacity : clampi(2 * k, 8, 256);
+    p.th = w.tuning.leaf_capacity > 0 ? w.tuning.leaf_capacity : knnq::default_leaf_capacity(k);
     const int gmax = p.L < kStaticMaxGridLevel ? p.L : kStaticMaxGridLevel;
     p.G = clampi(round_log4(2.0 * (double)n / (double)p.th), 1, gmax);
     p.Gp = clampi(round_log4((double)(n_q > 0 ? n_q : 1) / (k > 4 ? 12.0 * k : 48.0)), 0, p.G);
