@@ -680,15 +680,17 @@ knn_status knn_tick_host_submit(knn_world h, const int32_t *upd_id, const float 
     }
     cudaSetDevice(w.device);
     cudaStream_t s = (cudaStream_t)stream;
-    if (!w.h2d) {
-        if (cudaStreamCreateWithFlags(&w.h2d, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaStreamCreateWithFlags(&w.d2h, cudaStreamNonBlocking) != cudaSuccess)
+    if (!w.h2d || !w.d2h) {
+        if ((!w.h2d && cudaStreamCreateWithFlags(&w.h2d, cudaStreamNonBlocking) != cudaSuccess) ||
+            (!w.d2h && cudaStreamCreateWithFlags(&w.d2h, cudaStreamNonBlocking) != cudaSuccess))
             return cuda_fail(cudaGetLastError(), "knn_tick_host_submit: copy streams");
-        for (World::HostSlot &hs : w.hslot)
-            for (cudaEvent_t *e : {&hs.in, &hs.ran, &hs.done})
-                if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess)
-                    return cuda_fail(cudaGetLastError(), "knn_tick_host_submit: events");
     }
+    for (World::HostSlot &slot : w.hslot)
+        for (cudaEvent_t *e : {&slot.in, &slot.ran, &slot.done})
+            if (!*e && cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) {
+                *e = nullptr;
+                return cuda_fail(cudaGetLastError(), "knn_tick_host_submit: events");
+            }
     World::HostSlot &hs = w.hslot[w.tickets & 1];
     const size_t b_upd = align_up(sizeof(int32_t) * (size_t)n_upd) +
                          2 * align_up(sizeof(float) * (size_t)n_upd);
