@@ -64,6 +64,7 @@ Plan make_plan(const World &w, int64_t n_q, int k) {
     p.iterative = w.tuning.expansion == 3 && k <= knnq::kMaxPacketK;
     p.wide = !p.iterative && (w.tuning.expansion == 2 || (w.tuning.expansion != 1 && k > 32) ||
                               k > knnq::kMaxPacketK);
+    p.by_id = 2 * n_q >= w.n;
     p.reuse_age = w.reuse_age;
     p.reuse_f16 = w.reuse_factor > 0.f ? (int)std::lround(w.reuse_factor * 16.f) : 0;
     return p;

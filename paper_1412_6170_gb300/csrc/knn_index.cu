@@ -372,7 +372,7 @@ __global__ void __launch_bounds__(256) k_leaves(
     uint8_t *__restrict__ blevel, int32_t *__restrict__ obj_leaf, int32_t *__restrict__ cb,
     int64_t ncell, int32_t *scalars,
     uint64_t *status, uint32_t *ticket, const uint32_t *__restrict__ tickinfo, uint32_t site,
-    uint32_t *err, bool guarded, int32_t sig, int64_t leaf_cap) {
+    uint32_t *err, bool guarded, int32_t sig, int64_t leaf_cap, bool write_inv) {
     constexpr bool emit_empty = EMIT_EMPTY;
     if (guarded && scalars[kScalarRebuild] == 0) return;  // this tick reuses the leaves
     extern __shared__ __align__(16) unsigned char smem[];
@@ -486,7 +486,9 @@ __global__ void __launch_bounds__(256) k_leaves(
         xs[i] = px[id];
         ys[i] = py[id];
         sid[i] = id;
-        inv[id] = (int32_t)i;
+        // the inverse order (a scatter to random places) only where the
+        // queries are counted by place
+        if (write_inv) inv[id] = (int32_t)i;
     }
     if (tid < 32) {
         const uint32_t ex =
@@ -667,7 +669,7 @@ void launch_leaves(World &w, const Plan &p, cudaStream_t s) {
                                   w.sid, w.inv, w.bstart, w.bcode, w.blevel, w.obj_leaf, w.cb,
                                   ncell, w.scalars, w.status, w.counters + kCtrLeaves, w.tickinfo,
                                   w.site++, w.err, p.reuse_age > 0, index_signature(p),
-                                  w.leaf_cap);
+                                  w.leaf_cap, !p.by_id);
     const int g = grid_for(w.n, 256, num_sms(w.device) * 8);
     k_leaf_aabb<<<g, 256, 0, s>>>(w.bstart, w.scalars, w.xs, w.ys, w.baabb, w.brange, w.n);
     w.launches += 2;
@@ -844,8 +846,9 @@ __global__ void k_query_count_id(const int32_t *__restrict__ q_id, int64_t n_q, 
 }
 
 // By issuer id, rank placement, only when some issuer has several queries
-// (qcnt[n] set): every valid query takes the slot of its rank in the range of
-// its issuer's place p and records its caller index there.
+// (qcnt[n] set): every query of such an issuer takes the slot of its rank in
+// the range of the issuer's place p (which k_query_fill recorded in inv[issuer])
+// and records its caller index there.
 __global__ void k_query_place_id(const int32_t *__restrict__ q_id, int64_t n_q, int64_t n,
                                  const int32_t *__restrict__ inv,
                                  const int32_t *__restrict__ qrank,
@@ -855,7 +858,7 @@ __global__ void k_query_place_id(const int32_t *__restrict__ q_id, int64_t n_q, 
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_q;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t s = q_id[i];
-        if (s < 0 || s >= n) continue;
+        if (s < 0 || s >= n || qcnt[s] < 2) continue;  // single queries are placed
         const int32_t p = inv[s];
         if (p < 0 || p >= n) continue;
         const int32_t j = qoff[p] + qrank[i];
@@ -867,14 +870,14 @@ __global__ void k_query_place_id(const int32_t *__restrict__ q_id, int64_t n_q, 
 // Walk the sorted objects in order and copy each one's position, id and key
 // into the slots of its queries: sequential reads, sequential writes.  With
 // qidx (counting by issuer id), an object with a single query also records
-// that query's caller index.
+// that query's caller index, and one with several records its place in inv.
 __global__ void k_query_fill(int64_t n, int64_t n_q, const int32_t *__restrict__ qoff,
                              const float *__restrict__ xs, const float *__restrict__ ys,
                              const int32_t *__restrict__ sid, const uint32_t *__restrict__ skey,
                              const int32_t *__restrict__ obj_leaf,
                              const int32_t *__restrict__ qidx, float *qs_x, float *qs_y,
                              int32_t *qs_id, uint32_t *qs_key, int32_t *qs_leaf,
-                             int32_t *qs_orig) {
+                             int32_t *qs_orig, int32_t *inv) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
         int32_t a = qoff[p], b = qoff[p + 1];
@@ -893,7 +896,10 @@ __global__ void k_query_fill(int64_t n, int64_t n_q, const int32_t *__restrict__
             qs_key[j] = key;
             qs_leaf[j] = leaf;
         }
-        if (qidx && single && a < b && id >= 0 && id < n) qs_orig[a] = qidx[id];
+        if (qidx && id >= 0 && id < n) {
+            if (single && a < b) qs_orig[a] = qidx[id];
+            else if (!single) inv[id] = (int32_t)p;
+        }
     }
 }
 
@@ -903,7 +909,7 @@ void launch_queries_at_issuers(World &w, const Plan &p, const int32_t *q_id, int
     // once the leaf-ordered store is written
     const int r = p.passes & 1;
     int32_t *aux = reinterpret_cast<int32_t *>(w.key[r ^ 1]), *qrank = w.val[r ^ 1];
-    const bool by_id = 2 * n_q >= w.n;
+    const bool by_id = p.by_id;
     cudaMemsetAsync(w.qcnt, 0, sizeof(int32_t) * (size_t)(w.n + 1), s);
     const int g = grid_for(n_q, 256, num_sms(w.device) * 8);
     const uint32_t *skey = w.key[p.passes & 1];
@@ -916,7 +922,7 @@ void launch_queries_at_issuers(World &w, const Plan &p, const int32_t *q_id, int
                   s, w.sid);  // counts taken in sorted-object order
         k_query_fill<<<gf, 256, 0, s>>>(w.n, n_q, w.qoff, w.xs, w.ys, w.sid, skey, w.obj_leaf,
                                         aux, w.qs_x, w.qs_y, w.qs_id, w.qs_key, w.qs_leaf,
-                                        w.qs_orig);
+                                        w.qs_orig, w.inv);
         k_query_place_id<<<g, 256, 0, s>>>(q_id, n_q, w.n, w.inv, qrank, w.qoff, w.qcnt,
                                            w.qs_orig);
     } else {
@@ -928,7 +934,7 @@ void launch_queries_at_issuers(World &w, const Plan &p, const int32_t *q_id, int
         k_query_place<<<g, 256, 0, s>>>(n_q, w.n, aux, qrank, w.qoff, w.qs_orig);
         k_query_fill<<<gf, 256, 0, s>>>(w.n, n_q, w.qoff, w.xs, w.ys, w.sid, skey, w.obj_leaf,
                                         nullptr, w.qs_x, w.qs_y, w.qs_id, w.qs_key, w.qs_leaf,
-                                        w.qs_orig);
+                                        w.qs_orig, w.inv);
     }
     w.launches += 4;
 }

@@ -49,6 +49,8 @@ struct Plan {
     bool iterative;  // expansion in the paper's multi-pass form (an ablation)
     int reuse_age;   // index reuse: rebuild at least every reuse_age ticks (0: every tick)
     int reuse_f16;   // and when the cost proxy grows past reuse_f16 / 16 of its built value
+    bool by_id;      // queries at issuers counted by issuer id (most objects query): the
+                     // leaf split then writes no inverse order
 };
 
 // A whole tick recorded as a CUDA graph, with what it was recorded for.

@@ -175,6 +175,7 @@ extern "C" knn_status knn_query_static(const knn_world_desc *desc, const float *
     p.G = clampi(round_log4(2.0 * (double)n / (double)p.th), 1, gmax);
     p.Gp = clampi(round_log4((double)(n_q > 0 ? n_q : 1) / (k > 4 ? 12.0 * k : 48.0)), 0, p.G);
     p.wide = k > 32;
+    p.by_id = 2 * n_q >= n;
 
     cudaStream_t s = (cudaStream_t)stream;
     // what must start at zero: error words and device scalars; tile tickets
