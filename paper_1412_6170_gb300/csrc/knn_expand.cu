@@ -3,9 +3,10 @@
 //
 // One warp serves a packet of up to 32 queries that share a level-Gp cell; lane
 // i owns query i of the packet and keeps its k best (d^2, id) keys sorted in
-// registers.  Objects are read 32 at a time with coalesced loads and broadcast
-// to the lanes by warp shuffles, so every lane tests every candidate of the
-// packet while each lane keeps its own list and its own k-th distance.
+// registers.  Objects are staged 32 at a time in shared memory with coalesced
+// loads and read back by every lane (broadcast reads), so every lane tests
+// every candidate of the packet while each lane keeps its own list and its
+// own k-th distance.
 //
 // Expansion: (1) scan the leaves holding the packet's queries, widened along
 // the Morton leaf order until they hold at least k + 1 objects (the paper's
