@@ -7,8 +7,14 @@ Ten ticks are generated once and stay resident in HBM; steps cycle through
 them.  The L2 cache is flushed (a 256 MiB write) between timed steps, outside
 the timed events.
 
-Prints one JSON line.  ``--impl reference`` times the CPU oracle (brute force
-on the host cores) on a bounded sample of the same workload instead.
+Prints one JSON line.  ``e2e`` is the same metric through the host-buffer
+API: pinned host arrays, every step's inputs copied in and rows copied out
+inside the timed region, two ticks in flight (knn_tick_host_submit /
+knn_tick_host_wait); ``e2e.by_mode`` adds the synchronous knn_tick_host.
+``roofline`` reports the expansion kernel against the measured HBM copy
+bandwidth and against instruction issue.  ``--impl reference`` times the CPU
+oracle (brute force on the host cores) on a bounded sample of the same
+workload instead.
 Under torchrun each rank runs an independent replica of the workload on its
 own GPU ("replicas only": one world does not shard); value = all ranks'
 queries / the slowest rank's time.
