@@ -318,6 +318,15 @@ knn_status knn_world_leaves(knn_world w, int32_t *level_dev, uint32_t *z_dev,
  * tick identically (checkpoint / resume). */
 knn_status knn_world_positions(knn_world w, float *x_dev, float *y_dev, void *stream);
 
+/* Failure detection without a fault: enqueues on `stream` one bounded device
+ * wait that nothing will satisfy -- a look-back whose predecessor never
+ * publishes, the wait every scan of a tick uses -- so that it gives up after
+ * its poll limit (milliseconds) exactly as a stalled tick would.  The world's
+ * timeout bit is raised: knn_tick_status then reports KNN_ERR_TIMEOUT (and
+ * clears it), and the next tick runs normally.  Call between ticks of this
+ * world.  NULL world: KNN_ERR_INVALID. */
+knn_status knn_world_test_wait_timeout(knn_world w, void *stream);
+
 /* Number of CUDA kernels this world's ticks have launched so far (host-side
  * count; memsets and copies are not kernels and are not counted). */
 knn_status knn_world_launches(knn_world w, int64_t *count);

@@ -830,6 +830,18 @@ knn_status knn_world_positions(knn_world h, float *x_dev, float *y_dev, void *st
     return KNN_OK;
 }
 
+knn_status knn_world_test_wait_timeout(knn_world h, void *stream) {
+    if (!h) return fail(KNN_ERR_INVALID, "knn_world_test_wait_timeout: NULL world");
+    World &w = h->w;
+    cudaSetDevice(w.device);
+    cudaStream_t s = (cudaStream_t)stream;
+    knnq::launch_wait_runs_out(w, s);
+    w.last_stream = s;
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "knn_world_test_wait_timeout");
+    return KNN_OK;
+}
+
 knn_status knn_world_launches(knn_world h, int64_t *count) {
     if (!h || !count) return fail(KNN_ERR_INVALID, "knn_world_launches: NULL argument");
     *count = h->w.launches;

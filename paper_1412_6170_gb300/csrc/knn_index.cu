@@ -1227,6 +1227,20 @@ __global__ void k_export_leaves(const int32_t *__restrict__ bstart,
     }
 }
 
+// Failure detection without a fault: one warp resolves the look-back of tile 1
+// of a chain whose tile 0 never publishes -- its status word carries an older
+// epoch than the one asked for (epochs advance by 64 per tick from 0, so
+// 2^30 - 1 is never reached) -- and so waits exactly as a stalled tick's
+// look-back would, until the poll limit (or the tick's abort flag): then the
+// timeout bit and the abort flag are raised and the kernel returns.
+__global__ void k_wait_runs_out(uint64_t *status, uint32_t *err) {
+    lookback_warp_resolve(status, 1u, 0x3FFFFFFFu, 0u, err);
+}
+
+void launch_wait_runs_out(World &w, cudaStream_t s) {
+    k_wait_runs_out<<<1, 32, 0, s>>>(w.status, w.err);
+}
+
 void launch_export_leaves(World &w, int64_t m, int32_t *level, uint32_t *z, int32_t *start,
                           int32_t *count, cudaStream_t s) {
     if (m <= 0) return;

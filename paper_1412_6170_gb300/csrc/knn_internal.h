@@ -197,6 +197,8 @@ void launch_queries_explicit(World &w, const Plan &p, const int32_t *q_id, const
                              const float *q_y, int64_t n_q, int32_t k, int32_t *out_ids,
                              float *out_d2, cudaStream_t s);
 void launch_packets(World &w, const Plan &p, int64_t n_q, cudaStream_t s);
+// One bounded device wait that nothing satisfies (failure-detection check).
+void launch_wait_runs_out(World &w, cudaStream_t s);
 void launch_export_leaves(World &w, int64_t m, int32_t *level, uint32_t *z, int32_t *start,
                           int32_t *count, cudaStream_t s);
 

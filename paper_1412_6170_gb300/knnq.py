@@ -90,6 +90,7 @@ _SIGNATURES = {
     "knn_world_set_profiling": ([_vp, _i32], ctypes.c_int),
     "knn_world_set_graphs": ([_vp, _i32], ctypes.c_int),
     "knn_world_set_host_io": ([_vp, _i32], ctypes.c_int),
+    "knn_world_test_wait_timeout": ([_vp, _vp], ctypes.c_int),
     "knn_tick_host_submit": ([_vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _i64, _i32, _vp, _vp,
                               _vp, ctypes.POINTER(_i64)], ctypes.c_int),
     "knn_tick_host_wait": ([_vp, _i64], ctypes.c_int),
@@ -235,6 +236,10 @@ def knn_world_set_graphs(w: int, enable: bool) -> None:
 
 def knn_world_set_host_io(w: int, mode: int) -> None:
     _check(lib().knn_world_set_host_io(w, mode))
+
+
+def knn_world_test_wait_timeout(w: int, stream: int = 0) -> None:
+    _check(lib().knn_world_test_wait_timeout(w, stream))
 
 
 def knn_brute_force(x_dev, y_dev, n: int, q_id_dev, q_x_dev, q_y_dev, n_q: int, k: int,
@@ -484,6 +489,10 @@ class World:
 
     def set_graphs(self, enable: bool = True):
         knn_world_set_graphs(self.handle, enable)
+
+    def test_wait_timeout(self, stream=None):
+        """Run one bounded device wait that runs out (see knn_world_test_wait_timeout)."""
+        knn_world_test_wait_timeout(self.handle, _stream(stream))
 
     def set_host_io(self, write_rows: bool = True, read_inputs: bool = False):
         """How tick_host uses pinned host arrays in place (see knn_world_set_host_io)."""

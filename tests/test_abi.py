@@ -66,3 +66,4 @@ def test_null_world_calls_are_rejected(lib):
     t = ctypes.c_int64(0)
     assert lib.knn_tick_host_submit(None, None, None, None, 0, None, None, None, 0, 1, None, None,
                                     None, ctypes.byref(t)) == knnq.KNN_ERR_INVALID
+    assert lib.knn_world_test_wait_timeout(None, None) == knnq.KNN_ERR_INVALID

@@ -402,6 +402,36 @@ def test_pipelined_host_ticks_match_device_ticks(pinned):
         b.close()
 
 
+def test_bounded_wait_runs_out_and_world_stays_usable():
+    # failure detection without a fault: a look-back wait that nothing
+    # satisfies gives up after its poll limit, the status reports the timeout,
+    # and the next tick is exact again
+    import time
+    torch, _ = torch_dev()
+    w = synth.plain_uniform_moving(n=20000, k=8, ticks=2, seed=15)
+    world = make_world(w.x0, w.y0, k_max=8)
+    try:
+        x, y, _ = oracle.apply_updates(w.x0, w.y0, w.ticks[0].upd_id, w.ticks[0].upd_x,
+                                       w.ticks[0].upd_y)
+        gpu_tick(world, w.ticks[0])
+        assert world.status()[0] == knnq.KNN_OK
+        t0 = time.perf_counter()
+        world.test_wait_timeout()
+        torch.cuda.synchronize()
+        assert time.perf_counter() - t0 < 10.0
+        st, bits = world.status()
+        assert st == knnq.KNN_ERR_TIMEOUT and bits & 8
+        assert world.status()[0] == knnq.KNN_OK  # reported once, then cleared
+        t = w.ticks[1]
+        x, y, _ = oracle.apply_updates(x, y, t.upd_id, t.upd_x, t.upd_y)
+        ids, d2 = gpu_tick(world, t)
+        rid, rd2, _ = oracle.knn(x, y, t.q_id, t.k)
+        assert_rows_equal(ids, d2, rid, rd2, what="tick after a timed-out wait")
+        assert world.status()[0] == knnq.KNN_OK
+    finally:
+        world.close()
+
+
 def test_checkpoint_resume_bit_identical():
     w = synth.plain_uniform_moving(n=40000, k=8, ticks=6, seed=4)
     a = make_world(w.x0, w.y0, k_max=8)
