@@ -393,10 +393,13 @@ const char *knn_stage_name(int32_t i);
  * The first call on each device looks the array's device address up (with
  * that device current); make that first call before any stream capture.
  * Every call reuses the same array and finds the previous call's contents in
- * it, so calls that overlap on the GPU (other streams, other host threads
- * without ordering) race and corrupt each other's results.  Device-side input
- * problems give padded rows, as in knn_tick, but are not reported (there is
- * no world to hold a status).  Asynchronous on `stream`. */
+ * it; each call clears what must start at zero (error words, scan status
+ * words) before its first kernel.  Calls that overlap on the GPU (other
+ * streams, other host threads without ordering) race and corrupt each other's
+ * results.  Device-side input problems give padded rows, as in knn_tick, but
+ * are not reported (there is no world to hold a status); a bounded device wait
+ * that gave up turns every row of the call into padding (-1, +inf).
+ * Asynchronous on `stream`. */
 knn_status knn_query_static(const knn_world_desc *desc, const float *x_dev,
                             const float *y_dev, int64_t n, const int32_t *q_id_dev,
                             const float *q_x_dev, const float *q_y_dev, int64_t n_q,

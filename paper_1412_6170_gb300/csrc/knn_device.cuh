@@ -180,8 +180,11 @@ __device__ __forceinline__ void ring_cell(int u, int r, int ccx, int ccy, int &c
 // Decoupled look-back (single pass scans).  A status word packs
 // [63:34] epoch (30 bits) | [33:32] flag | [31:0] value.  Every launch uses a
 // fresh epoch (the tick's device-side epoch base plus the launch's index in
-// the tick), so words left by earlier launches read as "not ready" and the
-// arrays never need clearing.
+// the tick).  A world's status array is cleared once when its scratch is
+// attached and sits at a fixed place afterwards, so words left by earlier
+// launches carry older epochs and read as "not ready" without clearing (the
+// 30-bit epoch repeats only after 2^24 ticks).  The allocation-free call, whose
+// status words move with its sizes, clears them on every call.
 constexpr uint32_t kFlagAgg = 1u, kFlagPrefix = 2u;
 
 __device__ __forceinline__ uint64_t pack_status(uint32_t epoch, uint32_t flag, uint32_t v) {

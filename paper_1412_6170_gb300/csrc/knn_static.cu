@@ -17,6 +17,7 @@
 #include <mutex>
 
 #include "knn.h"
+#include "knn_device.cuh"
 #include "knn_internal.h"
 
 namespace {
@@ -30,8 +31,10 @@ static __device__ __align__(256) unsigned char g_scratch[kStaticScratchBytes];
 
 // Host-side state per device: the scratch array's device address, looked up
 // once with cudaGetSymbolAddress with that device current.  The look-back
-// epoch lives in the scratch itself (it starts at zero and keeps increasing
-// across calls, because status words left by earlier calls are never cleared).
+// epoch base lives in the scratch too.  Its place moves with n and n_q, so it
+// may hold any leftover value; that is harmless because every call clears its
+// look-back status words first, and within one call every launch that scans
+// uses its own epoch (base + launch index).
 struct Slot {
     unsigned char *base = nullptr;
 };
@@ -103,6 +106,20 @@ size_t cut_scratch(knnq::World &w, unsigned char *base, int64_t n_q) {
     w.scalars = c.take<int32_t>(knnq::kNumScalars);
     w.err = c.take<uint32_t>(4);
     return c.off;
+}
+
+// A bounded look-back wait that gave up (error bit kErrTimeout) leaves the
+// scans' offsets unreliable.  This call has no world to hold a status, so the
+// rows say it instead: every row becomes padding (-1, +inf).
+__global__ void k_pad_rows_on_timeout(const uint32_t *err, int32_t *ids, float *d2,
+                                      int64_t total) {
+    if ((*reinterpret_cast<const volatile uint32_t *>(err) & knnq::kErrTimeout) == 0u) return;
+    const float inf = __int_as_float(0x7f800000);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        ids[i] = -1;
+        d2[i] = inf;
+    }
 }
 
 int round_log4(double v) {
@@ -178,10 +195,13 @@ extern "C" knn_status knn_query_static(const knn_world_desc *desc, const float *
     p.by_id = 2 * n_q >= n;
 
     cudaStream_t s = (cudaStream_t)stream;
-    // what must start at zero: error words and device scalars; tile tickets
+    // what must start at zero: error words, device scalars and the look-back
+    // status words (their place moves with n and n_q, so they may hold another
+    // call's ids or offsets, which could read as a ready status); tile tickets
     // are cleared (and the epoch advanced) by the tick-begin kernel
     cudaMemsetAsync(w.err, 0, sizeof(uint32_t) * 4, s);
     cudaMemsetAsync(w.scalars, 0, sizeof(int32_t) * knnq::kNumScalars, s);
+    cudaMemsetAsync(w.status, 0, sizeof(uint64_t) * w.status_words, s);
     knnq::launch_tick_begin(w, p, s);
     knnq::launch_object_sort(w, p, s);
     knnq::launch_leaves(w, p, s);
@@ -197,6 +217,8 @@ extern "C" knn_status knn_query_static(const knn_world_desc *desc, const float *
             knnq::launch_packets(w, p, n_q, s);
             knnq::launch_expand(w, p, k, n_q, out_ids_dev, out_d2_dev, nullptr, s);
         }
+        k_pad_rows_on_timeout<<<64, 256, 0, s>>>(w.err, out_ids_dev, out_d2_dev,
+                                                 n_q * (int64_t)k);
     }
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return bad(KNN_ERR_CUDA, cudaGetErrorString(e));

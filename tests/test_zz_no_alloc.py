@@ -4,16 +4,17 @@ This entry point is for callers that must not allocate device memory:
 latency-critical loops where cudaMalloc/cudaFree would synchronize the device,
 services whose device memory belongs to another allocator or a fixed budget,
 and code that must not fail mid-request because an allocation did.  Its
-scratch is a static device array, so the test checks that two calls in a row
-(the second one finding the first one's leftovers in that array) both give
-exactly the rows of the regular path: knn_world_create + knn_tick without
-updates.  This file is collected last on purpose.
+scratch is a static device array, so the tests check that calls in a row
+(each one finding the previous one's leftovers in that array, at other sizes)
+give exactly the rows of the regular path, knn_world_create + knn_tick without
+updates, and of the CPU oracle.  This file is collected last on purpose.
 """
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_1412_6170_gb300 import knnq, synth
 
 pytestmark = pytest.mark.gpu
@@ -79,6 +80,51 @@ def test_static_matches_regular_path_twice_in_a_row():
     assert same(second, regular_path(x2, y2, q2, 5, qx, qy, leaf_capacity=12))
     # and call 1 again gives call 1's rows
     assert same(static_path(x1, y1, q1, 16), first)
+
+
+def oracle_path(x, y, q_id, k, q_x=None, q_y=None):
+    ids, d2, _ = oracle.knn(x, y, q_id, k, q_x, q_y)
+    return ids, d2
+
+
+def test_static_matches_oracle_directly():
+    # the rows of the allocation-free call against the CPU oracle itself (Def. 1
+    # brute force), not only against the regular path: issuer queries at k = 8
+    # and anonymous explicit centres at k = 3
+    x, y = synth.uniform_positions(12007, 31)
+    q = np.arange(0, 12007, 2, dtype=np.int32)
+    assert same(static_path(x, y, q, 8), oracle_path(x, y, q, 8))
+    r = np.random.default_rng(32)
+    qa = np.full(2000, -1, dtype=np.int32)
+    qx = r.random(2000).astype(np.float32)
+    qy = r.random(2000).astype(np.float32)
+    assert same(static_path(x, y, qa, 3, qx, qy), oracle_path(x, y, qa, 3, qx, qy))
+
+
+def test_static_many_calls_alternating_sizes():
+    # every call finds the previous call's arrays at other places of the shared
+    # scratch: large and small (n, n_q) alternate so that a call's scan status
+    # words fall where the last call kept ids and offsets; every call must
+    # still match the regular path bit for bit
+    worlds = []
+    for i, n in enumerate((65536, 3001, 50000, 777, 65000, 12345)):
+        x, y = (synth.clustered_positions(n, 40 + i) if i % 2 == 0
+                else synth.uniform_positions(n, 40 + i))
+        worlds.append((x, y))
+    ks = (16, 4, 8, 1, 32, 5)
+    expected = {}
+    for call in range(24):
+        j = call % len(worlds)
+        x, y = worlds[j]
+        n = len(x)
+        nq = n if call % 4 < 2 else max(1, n // 3)
+        q = np.arange(n, dtype=np.int32)[:nq] if nq == n else \
+            np.random.default_rng(100 + j).choice(n, nq, replace=False).astype(np.int32)
+        got = static_path(x, y, q, ks[j])
+        key = (j, nq)
+        if key not in expected:
+            expected[key] = regular_path(x, y, q, ks[j])
+        assert same(got, expected[key]), f"call {call}: world {j}, n_q {nq}, k {ks[j]}"
 
 
 def test_static_accepts_positions_not_16_byte_aligned():
