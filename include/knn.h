@@ -273,13 +273,18 @@ knn_status knn_brute_force(const float *x_dev, const float *y_dev, int64_t n,
  * packet_level: queries are packed 32 to a warp within one cell of this
  *   level (<= grid_level).
  * expansion: the expansion kernel.  1 = packets of up to 32 queries per warp,
- *   each lane keeping its query's list in registers (k <= 64); 2 = one warp
+ *   each lane keeping its query's list in registers (k <= 64), each packet
+ *   walking the quadtree leaf by leaf; 4 = gathered packets (k <= 32): each
+ *   packet fixes its search box from the local density first, gathers the
+ *   box's useful leaves and objects in one pass (Section 4.2.2) and tests
+ *   them in one loop; a packet it cannot finish goes to the walk; 2 = one warp
  *   per query, the list in shared memory and the row written by the whole
  *   warp (any k; the paper's coalesced-writes variant, Section 3.3.2); 3 =
  *   the paper's multi-pass form (Section 4.2: first iteration on the query's
  *   own cell, then alternating left/right Morton sub-visits, one cell per
  *   iteration; k <= 64), an ablation with the same rows, never recorded in a
- *   tick graph.  The automatic choice is 1 for k <= 32 and 2 above.
+ *   tick graph.  The automatic choice is 4 for k <= 16, 1 for k <= 32 and 2
+ *   above.
  * Any field set to 0 keeps (or restores) the automatic choice. */
 typedef struct {
     int32_t leaf_capacity;
@@ -357,6 +362,14 @@ knn_status knn_world_index_info(knn_world w, int32_t *age, int32_t *rebuilt);
  * launch overhead.  enable = 0 launches the kernels directly.  A stream that
  * is itself being recorded always gets direct launches.  On by default. */
 knn_status knn_world_set_graphs(knn_world w, int32_t enable);
+
+/* How the last tick's expansion was served (synchronizes the world's last
+ * stream): *gathered = packets (of up to 32 queries) the gathered form
+ * finished, *handed_back = packets it handed to the packet walk (no object
+ * near the packet, a search box of more than 4096 cells, or queries still
+ * short of k objects after two thresholds); both 0 unless the tick used the
+ * gathered form.  Either may be NULL.  Rows are identical either way. */
+knn_status knn_world_expand_info(knn_world w, int64_t *gathered, int64_t *handed_back);
 
 /* Records the graph of a tick with these arguments without running it, so
  * that a later knn_tick with the same arguments (and the same tuning and

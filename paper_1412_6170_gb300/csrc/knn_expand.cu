@@ -35,6 +35,7 @@ struct ExpandArgs {
     const float *qs_x, *qs_y;
     const int32_t *qs_id, *qs_orig, *qs_leaf;
     const int32_t *pk_start, *pk_len;
+    const int2 *hb;  // non-null: the packets are hb[0 .. scalars[kScalarHandedBack])
     const int32_t *scalars;
     uint32_t *pk_counter;
     int32_t *out_ids;
@@ -165,11 +166,12 @@ __global__ void __launch_bounds__(kWarps * 32, Shape<KC>::kMinBlocks) k_expand(c
     WarpSmem<Shape<KC>::kBufCap> &sm = smem[threadIdx.x >> 5];
     // device scalars are exact unless a look-back timed out; clamp anyway
     // full packets at the front of the list, partial ones at its back
-    int32_t F = g.scalars[kScalarPackets];
+    int32_t F = g.scalars[g.hb ? kScalarHandedBack : kScalarPackets];
     F = F < 0 ? 0 : (F > g.pk_cap ? (int32_t)g.pk_cap : F);
-    int32_t Pp = g.scalars[kScalarPartialPackets];
+    int32_t Pp = g.hb ? 0 : g.scalars[kScalarPartialPackets];
     Pp = Pp < 0 ? 0 : (Pp > g.pk_cap - F ? (int32_t)(g.pk_cap - F) : Pp);
     const int32_t P = F + Pp;
+    if (P == 0) return;  // (the gathered form finished every packet)
     int32_t m = g.scalars[kScalarLeaves];
     m = m < 0 ? 0 : (m > g.leaf_cap ? (int32_t)g.leaf_cap : m);
     const int k = g.k;
@@ -182,8 +184,8 @@ __global__ void __launch_bounds__(kWarps * 32, Shape<KC>::kMinBlocks) k_expand(c
         p = __shfl_sync(kFull, p, 0);
         if (p >= P) break;
         const int64_t pi = p < F ? (int64_t)p : g.pk_cap - 1 - (int64_t)(p - F);
-        const int32_t q0 = g.pk_start[pi];
-        int32_t ql = g.pk_len[pi];
+        const int32_t q0 = g.hb ? g.hb[pi].x : g.pk_start[pi];
+        int32_t ql = g.hb ? g.hb[pi].y : g.pk_len[pi];
         if (q0 < 0 || ql < 1 || q0 >= g.n_q) continue;
         if (ql > 32) ql = 32;
         if (q0 + ql > g.n_q) ql = (int32_t)(g.n_q - q0);
@@ -540,10 +542,10 @@ static void run(const ExpandArgs &a, int device, cudaStream_t s) {
     k_expand<KC><<<num_sms(device) * per_sm, kWarps * 32, 0, s>>>(a);
 }
 
-void launch_expand(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t *out_ids,
-                   float *out_d2, const int32_t *q_k, cudaStream_t s) {
-    if (n_q <= 0) return;
+static ExpandArgs expand_args(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t *out_ids,
+                              float *out_d2, const int32_t *q_k) {
     ExpandArgs a;
+    a.hb = nullptr;
     a.xs = w.xs;
     a.ys = w.ys;
     a.sid = w.sid;
@@ -586,12 +588,32 @@ void launch_expand(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t *out
                  15u) == 0;
     a.q_k = q_k;
     a.err = w.err;
-    if (k <= 4) run<4>(a, w.device, s);
-    else if (k <= 8) run<8>(a, w.device, s);
-    else if (k <= 16) run<16>(a, w.device, s);
-    else if (k <= 32) run<32>(a, w.device, s);
-    else run<64>(a, w.device, s);
+    return a;
+}
+
+static void run_expand(const ExpandArgs &a, int32_t k, int device, cudaStream_t s) {
+    if (k <= 4) run<4>(a, device, s);
+    else if (k <= 8) run<8>(a, device, s);
+    else if (k <= 16) run<16>(a, device, s);
+    else if (k <= 32) run<32>(a, device, s);
+    else run<64>(a, device, s);
+}
+
+void launch_expand(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t *out_ids,
+                   float *out_d2, const int32_t *q_k, cudaStream_t s) {
+    if (n_q <= 0) return;
+    run_expand(expand_args(w, p, k, n_q, out_ids, out_d2, q_k), k, w.device, s);
     ++w.launches;
 }
 
+void launch_expand_handed_back(World &w, const Plan &p, int32_t k, int64_t n_q,
+                               int32_t *out_ids, float *out_d2, const int32_t *q_k,
+                               cudaStream_t s) {
+    if (n_q <= 0) return;
+    ExpandArgs a = expand_args(w, p, k, n_q, out_ids, out_d2, q_k);
+    a.hb = w.hb;
+    a.pk_counter = w.counters + kCtrHandBack;
+    run_expand(a, k, w.device, s);
+    ++w.launches;
+}
 }  // namespace knnq

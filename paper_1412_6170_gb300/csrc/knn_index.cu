@@ -1015,6 +1015,7 @@ __global__ void k_query_cells(const uint32_t *__restrict__ qs_key, int32_t *scal
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         scalars[kScalarPackets] = 0;
         scalars[kScalarPartialPackets] = 0;
+        scalars[kScalarHandedBack] = 0;
     }
     const int sh = 2 * (L - Gp);
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j <= nv;
@@ -1077,14 +1078,20 @@ __global__ void k_packets(const int32_t *__restrict__ qcs, int64_t ncell, int64_
     }
 }
 
+void launch_query_cells(World &w, const Plan &p, int64_t n_q, cudaStream_t s) {
+    const int64_t ncell = 1ll << (2 * p.Gp);
+    k_query_cells<<<grid_for(n_q + 1, 256, num_sms(w.device) * 8), 256, 0, s>>>(
+        w.qs_key, w.scalars, p.L, p.Gp, ncell, n_q, w.qcs);
+    ++w.launches;
+}
+
 void launch_packets(World &w, const Plan &p, int64_t n_q, cudaStream_t s) {
     const int64_t ncell = 1ll << (2 * p.Gp);
     const int g = grid_for(ncell, 256, num_sms(w.device) * 16);
-    k_query_cells<<<grid_for(n_q + 1, 256, num_sms(w.device) * 8), 256, 0, s>>>(
-        w.qs_key, w.scalars, p.L, p.Gp, ncell, n_q, w.qcs);
+    launch_query_cells(w, p, n_q, s);
     k_packets<<<g, 256, 0, s>>>(w.qcs, ncell, packet_capacity(w), w.scalars, w.pk_start,
                                 w.pk_len);
-    w.launches += 2;
+    ++w.launches;
 }
 
 // ---------------------------------------------------------------------------
@@ -1193,6 +1200,7 @@ void prepare_kernels() {
     num_sms(dev);          // fill the per-device caches now: the query APIs
     prepare_expand(dev);   // must not run while a batch is being recorded
     prepare_expand_wide(dev);
+    prepare_expand_gather(dev);
     done[dev] = true;
 }
 

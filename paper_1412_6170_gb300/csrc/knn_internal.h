@@ -32,12 +32,13 @@ constexpr int kScanTile = 2048;
 enum Scalar : int { kScalarLeaves = 0, kScalarValidQueries = 1, kScalarPackets = 2,
                     kScalarIndexSig = 3, kScalarIndexAge = 4, kScalarRebuild = 5,
                     kScalarCostBase = 6, kScalarCostNow = 8, kScalarPartialPackets = 10,
-                    kNumScalars = 16 };
+                    kScalarHandedBack = 11, kNumScalars = 16 };
 
 // Ticket counters (one per single-pass launch site in a tick).
 enum Counter : int { kCtrObjSort = 0, kCtrQuerySort = 4, kCtrLeaves = 8, kCtrQueryScan = 9,
                      kCtrExpand = 11, kCtrReuseScan = 12,
-                     kCtrIterLeft = 13 /* and 14: iterative expansion */ };
+                     kCtrIterLeft = 13 /* and 14: iterative expansion */, kCtrGather = 15,
+                     kCtrHandBack = 16 };
 
 struct Plan {
     int L;           // max depth (key has 2L bits)
@@ -46,6 +47,7 @@ struct Plan {
     int Gp;          // packet level
     int passes;      // radix passes over 2L bits
     bool wide;       // expansion by one warp per query (else packets)
+    bool gather;     // packets gather their search box at once (the rest: packet walk)
     bool iterative;  // expansion in the paper's multi-pass form (an ablation)
     int reuse_age;   // index reuse: rebuild at least every reuse_age ticks (0: every tick)
     int reuse_f16;   // and when the cost proxy grows past reuse_f16 / 16 of its built value
@@ -111,6 +113,7 @@ struct World {
     uint32_t *nav = nullptr;     // iterative expansion: per sorted query, left and right position
     int32_t *qcs = nullptr;
     int32_t *pk_start = nullptr, *pk_len = nullptr;
+    int2 *hb = nullptr;          // packets handed from the gathered form to the walk
     uint64_t *status = nullptr;
     size_t status_words = 0;
     uint32_t *hist = nullptr;
@@ -197,6 +200,9 @@ void launch_queries_explicit(World &w, const Plan &p, const int32_t *q_id, const
                              const float *q_y, int64_t n_q, int32_t k, int32_t *out_ids,
                              float *out_d2, cudaStream_t s);
 void launch_packets(World &w, const Plan &p, int64_t n_q, cudaStream_t s);
+// First sorted query of every level-Gp cell (qcs); also clears the packet
+// counts.
+void launch_query_cells(World &w, const Plan &p, int64_t n_q, cudaStream_t s);
 // One bounded device wait that nothing satisfies (failure-detection check).
 void launch_wait_runs_out(World &w, cudaStream_t s);
 void launch_export_leaves(World &w, int64_t m, int32_t *level, uint32_t *z, int32_t *start,
@@ -209,6 +215,14 @@ void launch_expand_wide(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t
                         float *out_d2, const int32_t *q_k, cudaStream_t s);
 void launch_expand_iter(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t *out_ids,
                         float *out_d2, const int32_t *q_k, cudaStream_t s);
+// The packet walk over the packets the gathered form handed back.
+void launch_expand_handed_back(World &w, const Plan &p, int32_t k, int64_t n_q,
+                               int32_t *out_ids, float *out_d2, const int32_t *q_k,
+                               cudaStream_t s);
+// ---- launcher (knn_expand_gather.cu) -----------------------------------------
+// The gathered form, then the packet walk over the packets it handed back.
+void launch_expand_gather(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t *out_ids,
+                          float *out_d2, const int32_t *q_k, cudaStream_t s);
 
 int num_sms(int device);
 // One-time kernel attributes and cached device queries (called outside any
@@ -216,6 +230,7 @@ int num_sms(int device);
 void prepare_kernels();
 void prepare_expand(int device);
 void prepare_expand_wide(int device);
+void prepare_expand_gather(int device);
 
 // Device memory layout of a world (knn_capi.cu).  base == nullptr only sizes.
 size_t carve_resident(World &w, char *base);

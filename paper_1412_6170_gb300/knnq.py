@@ -97,6 +97,7 @@ _SIGNATURES = {
     "knn_brute_force": ([_vp, _vp, _i64, _vp, _vp, _vp, _i64, _i32, _vp, _vp, _vp], ctypes.c_int),
     "knn_world_set_index_reuse": ([_vp, _i32, ctypes.c_float], ctypes.c_int),
     "knn_world_index_info": ([_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)], ctypes.c_int),
+    "knn_world_expand_info": ([_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)], ctypes.c_int),
     "knn_world_record_tick": ([_vp, ctypes.POINTER(knn_tick_args)], ctypes.c_int),
     "knn_world_stage_times": ([_vp, ctypes.POINTER(ctypes.c_float), _i32], ctypes.c_int),
     "knn_stage_name": ([_i32], ctypes.c_char_p),
@@ -267,6 +268,12 @@ def knn_world_index_info(w: int) -> dict:
     age, rebuilt = _i32(), _i32()
     _check(lib().knn_world_index_info(w, ctypes.byref(age), ctypes.byref(rebuilt)))
     return {"age": age.value, "rebuilt": rebuilt.value}
+
+
+def knn_world_expand_info(w: int) -> dict:
+    gathered, back = _i64(0), _i64(0)
+    _check(lib().knn_world_expand_info(w, ctypes.byref(gathered), ctypes.byref(back)))
+    return {"gathered": int(gathered.value), "handed_back": int(back.value)}
 
 
 def knn_world_record_tick(w: int, args: knn_tick_args) -> None:
@@ -503,6 +510,9 @@ class World:
 
     def index_info(self) -> dict:
         return knn_world_index_info(self.handle)
+
+    def expand_info(self) -> dict:
+        return knn_world_expand_info(self.handle)
 
     def record_tick(self, k: int, q_id=None, upd_id=None, upd_x=None, upd_y=None, q_x=None,
                     q_y=None, out_ids=None, out_d2=None):

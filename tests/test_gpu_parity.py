@@ -76,7 +76,7 @@ def test_large_k_clustered_subset_sampled(k):
     run_and_compare(w, k_max=512, sample=3000, what=f"120k clustered k={k}")
 
 
-@pytest.mark.parametrize("expansion", [1, 2, 3])
+@pytest.mark.parametrize("expansion", [1, 2, 3, 4])
 @pytest.mark.parametrize("k", [1, 16, 64])
 def test_expansion_kernels_agree(k, expansion):
     w = synth.skewed_moving(n=40000, k=k, ticks=2, seed=23, query_frac=0.5)
