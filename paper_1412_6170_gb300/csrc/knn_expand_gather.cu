@@ -41,6 +41,7 @@ template <int KC>
 struct GatherShape {
     static constexpr int kCap = 32;  // buffer slots per lane
     static constexpr int kFlushAt = kCap - kBatch;
+    static constexpr int kMinBlocks = KC <= 16 ? 5 : 4;  // 20 or 16 warps per SM
 };
 
 struct GatherArgs {
@@ -84,13 +85,27 @@ struct GatherSmem {
 
 template <int KC>
 struct GLane {
-    unsigned long long lst[KC];  // ascending; slots below KC - k hold 0
+    unsigned long long lst[KC];  // ascending by d^2; slots below KC - k hold 0
     float thr;                   // d^2 bound of what may still enter the list
     int count;                   // buffered candidates
+    uint32_t dropped;            // smallest d^2 bits a merge pushed out of the list
 };
 
-// Merge the newest kBatch buffered candidates (or all, if fewer) into the list;
-// the issuer's own key (id + 1 == self) never enters it.
+// Compare-exchange on the d^2 word alone (the high half of a key): one 32-bit
+// compare instead of a 64-bit one.  Keys of equal d^2 keep an arbitrary order;
+// such ties are detected at the end of a pass (gtie) and the packet is then
+// handed to the packet walk, which orders by the full (d^2, id) key.
+__device__ __forceinline__ void cmpx_hi(unsigned long long &x, unsigned long long &y) {
+    const bool s = (uint32_t)(y >> 32) < (uint32_t)(x >> 32);
+    const unsigned long long lo = s ? y : x;
+    y = s ? x : y;
+    x = lo;
+}
+
+// Merge the newest kBatch buffered candidates (or all, if fewer) into the list
+// (the batch sorted by a network, then the KC smallest of list and batch by a
+// bitonic merge), recording the smallest d^2 pushed out; the issuer's own key
+// (id + 1 == self) never enters it.
 template <int KC>
 __device__ __forceinline__ void gmerge(GLane<KC> &L, GatherSmem<KC> &sm, int lane, uint32_t self) {
     const int base = L.count > kBatch ? L.count - kBatch : 0;
@@ -100,10 +115,46 @@ __device__ __forceinline__ void gmerge(GLane<KC> &L, GatherSmem<KC> &sm, int lan
         const unsigned long long v = base + t < L.count ? sm.buf[base + t][lane] : kPad;
         b[t] = (uint32_t)v == self ? kPad : v;
     }
-    sort8(b);
-    merge_batch<KC>(L.lst, b);
+    cmpx_hi(b[0], b[2]); cmpx_hi(b[1], b[3]); cmpx_hi(b[4], b[6]); cmpx_hi(b[5], b[7]);
+    cmpx_hi(b[0], b[4]); cmpx_hi(b[1], b[5]); cmpx_hi(b[2], b[6]); cmpx_hi(b[3], b[7]);
+    cmpx_hi(b[0], b[1]); cmpx_hi(b[2], b[3]); cmpx_hi(b[4], b[5]); cmpx_hi(b[6], b[7]);
+    cmpx_hi(b[2], b[4]); cmpx_hi(b[3], b[5]);
+    cmpx_hi(b[1], b[4]); cmpx_hi(b[3], b[6]);
+    cmpx_hi(b[1], b[2]); cmpx_hi(b[3], b[4]); cmpx_hi(b[5], b[6]);
+    // c_i = min(a_i, b_{KC-1-i}) is bitonic and holds the KC smallest; the
+    // larger of each pair leaves the list
+    uint32_t drop = L.dropped;
+    if (KC < kBatch) drop = min(drop, (uint32_t)(b[KC] >> 32));
+#pragma unroll
+    for (int i = (KC > kBatch ? KC - kBatch : 0); i < KC; ++i) {
+        const unsigned long long v = b[KC - 1 - i];
+        const uint32_t vh = (uint32_t)(v >> 32), ah = (uint32_t)(L.lst[i] >> 32);
+        const bool sv = vh < ah;
+        drop = min(drop, sv ? ah : vh);
+        L.lst[i] = sv ? v : L.lst[i];
+    }
+    L.dropped = drop;
+#pragma unroll
+    for (int span = KC / 2; span >= 1; span >>= 1) {
+#pragma unroll
+        for (int i = 0; i < KC; ++i)
+            if ((i & span) == 0) cmpx_hi(L.lst[i], L.lst[i + span]);
+    }
     L.count = base;
     L.thr = fminf(L.thr, __uint_as_float((uint32_t)(L.lst[KC - 1] >> 32)));
+}
+
+// After the last merge of a pass: could the (d^2, id) order differ from the
+// d^2-only order the networks used?  Only when two listed keys (or the last
+// leading 0 and the first key) share a d^2, or a key pushed out shares the
+// k-th d^2.
+template <int KC>
+__device__ __forceinline__ bool gtie(const GLane<KC> &L, int kq) {
+    bool tie = L.dropped == (uint32_t)(L.lst[KC - 1] >> 32);
+#pragma unroll
+    for (int i = 0; i + 1 < KC; ++i)
+        if (i + 1 >= KC - kq) tie |= (uint32_t)(L.lst[i] >> 32) == (uint32_t)(L.lst[i + 1] >> 32);
+    return tie;
 }
 
 // Two binary32 operations at once (sm_100 packed pairs): each half is rounded
@@ -122,6 +173,16 @@ __device__ __forceinline__ unsigned long long f2pack(float lo, float hi) {
     return ((unsigned long long)__float_as_uint(hi) << 32) | __float_as_uint(lo);
 }
 
+// Float bits mapped to an unsigned key of the same order (for warp min/max by
+// one integer reduction), and back.
+__device__ __forceinline__ uint32_t ord_key(float x) {
+    const uint32_t u = __float_as_uint(x);
+    return u ^ ((u >> 31) ? 0xFFFFFFFFu : 0x80000000u);
+}
+__device__ __forceinline__ float ord_val(uint32_t k) {
+    return __uint_as_float(k ^ ((k >> 31) ? 0x80000000u : 0xFFFFFFFFu));
+}
+
 // Lower bound of the squared distance from (x, y) to the box [bx0, bx1] x
 // [by0, by1], rounded like the exact distances (so it never exceeds the exact
 // d^2 from any point of the box).
@@ -138,7 +199,8 @@ __device__ __forceinline__ float point_box_lb(float x, float y, float bx0, float
 }  // namespace
 
 template <int KC>
-__global__ void __launch_bounds__(kGatherWarps * 32) k_expand_gather(const GatherArgs g) {
+__global__ void __launch_bounds__(kGatherWarps * 32, GatherShape<KC>::kMinBlocks)
+    k_expand_gather(const GatherArgs g) {
     constexpr int FLUSH = GatherShape<KC>::kFlushAt;
     __shared__ GatherSmem<KC> smem[kGatherWarps];
     const int lane = threadIdx.x & 31;
@@ -183,10 +245,10 @@ __global__ void __launch_bounds__(kGatherWarps * 32) k_expand_gather(const Gathe
                 kq = 0;
             }
         }
-        const float bx0 = warp_min(active ? qx : kInf);
-        const float bx1 = warp_max(active ? qx : -kInf);
-        const float by0 = warp_min(active ? qy : kInf);
-        const float by1 = warp_max(active ? qy : -kInf);
+        const float bx0 = ord_val(__reduce_min_sync(kFull, active ? ord_key(qx) : 0xFFFFFFFFu));
+        const float bx1 = ord_val(__reduce_max_sync(kFull, active ? ord_key(qx) : 0u));
+        const float by0 = ord_val(__reduce_min_sync(kFull, active ? ord_key(qy) : 0xFFFFFFFFu));
+        const float by1 = ord_val(__reduce_max_sync(kFull, active ? ord_key(qy) : 0u));
 
         // local density: objects of the level-G cells under the packet's box
         // grown by one cell (the packet's density), then for each lane the
@@ -252,10 +314,11 @@ __global__ void __launch_bounds__(kGatherWarps * 32) k_expand_gather(const Gathe
                 }
                 if (lc > 0)
                     spec = g.spec2 * (float)k * (float)lcells * cs * cs / (3.14159265f * (float)lc);
-                // the lane's own cell far off the block's mean (density changes
-                // within the block): the adaptive leaves instead -- the query's
-                // leaf, widened along the leaf order to 2k + 2 objects
-                if (2u * own * (uint32_t)lcells < lc || own * (uint32_t)lcells > 2u * lc) {
+                // the lane's own cell four times off the block's mean (density
+                // changes within the block, not count noise): the adaptive leaves
+                // instead -- the query's leaf, widened along the leaf order to
+                // 2k + 2 objects
+                if (4u * own * (uint32_t)lcells < lc || own * (uint32_t)lcells > 4u * lc) {
                     int32_t b = g.qs_leaf[j];
                     b = b < 0 ? 0 : (b >= m ? m - 1 : b);
                     if (b >= 0) {
@@ -293,6 +356,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32) k_expand_gather(const Gathe
         for (int i = 0; i < KC; ++i) Ln.lst[i] = i < KC - kq ? 0ull : kPad;
         Ln.thr = active && kq > 0 ? spec_q : -kInf;
         Ln.count = 0;
+        Ln.dropped = 0xFFFFFFFFu;
         bool hand_back = __any_sync(kFull, active && !(spec < kInf));
         const int ccx = cell_g(0.5f * (bx0 + bx1), g.x0, g.scale_g, g.G);
         const int ccy = cell_g(0.5f * (by0 + by1), g.y0, g.scale_g, g.G);
@@ -323,7 +387,8 @@ __global__ void __launch_bounds__(kGatherWarps * 32) k_expand_gather(const Gathe
             const ulonglong2 *sxy2 = reinterpret_cast<const ulonglong2 *>(sm.xy);
             for (;;) {
                 // (a) merge a batch (the one merge site): a buffer near full; between
-                // steps every accepting lane holding a full batch, or the pass over
+                // passes over the list every accepting lane holding a full batch,
+                // or the walk over
                 const bool accepting = Ln.thr > -kInf;
                 if (__any_sync(kFull, Ln.count >= FLUSH) ||
                     (!(testing && tpos < kept) && __any_sync(kFull, Ln.count > 0) &&
@@ -336,7 +401,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32) k_expand_gather(const Gathe
                 // pairs) per step, until a buffer is near full or the list is done
                 if (testing) {
                     while (tpos < kept) {
-                        if (__any_sync(kFull, Ln.count >= FLUSH)) break;
+                        if (__any_sync(kFull, Ln.count >= FLUSH)) break;  // to the merge site
                         const float thr = Ln.thr;
 #pragma unroll
                         for (int t = 0; t < kBatch / 2; ++t) {
@@ -373,34 +438,63 @@ __global__ void __launch_bounds__(kGatherWarps * 32) k_expand_gather(const Gathe
                 }
                 // (c) gather until the list is nearly full or the walk is over; the
                 // segment of a flattened index comes from one OR-reduction of the
-                // segment starts that fall in the 32-index window
-                while (!gdone && kept <= kObjCap - 32) {
-                    R2 = warp_max(Ln.thr > 0.f ? Ln.thr : 0.f);
+                // segment starts that fall in its 32-index window.  The search box
+                // follows the lanes' thresholds as they stand after the last merge.
+                R2 = warp_max(Ln.thr > 0.f ? Ln.thr : 0.f);
+                {
+                    const float R = __fmul_ru(__fsqrt_ru(R2), 1.0000010f);
+                    cx0 = cell_g(__fsub_rd(bx0, R), g.x0, g.scale_g, g.G);
+                    cx1 = cell_g(__fadd_ru(bx1, R), g.x0, g.scale_g, g.G);
+                    cy0 = cell_g(__fsub_rd(by0, R), g.y0, g.scale_g, g.G);
+                    cy1 = cell_g(__fadd_ru(by1, R), g.y0, g.scale_g, g.G);
+                    rmax = max(max(ccx - cx0, cx1 - ccx), max(ccy - cy0, cy1 - ccy));
+                }
+                while (!gdone && kept <= kObjCap - 64) {
                     if (o0 < nobj) {
-                        // 32 objects of the kept leaves; those within reach join the list
-                        const unsigned win = __reduce_or_sync(
+                        // 64 objects of the kept leaves (two per lane, both loads in
+                        // flight together); those within reach join the list
+                        const unsigned win0 = __reduce_or_sync(
                             kFull, oseg_on && oseg_at >= o0 && oseg_at < o0 + 32 ? 1u << (oseg_at - o0) : 0u);
-                        bool keep = false;
-                        float x = 0.f, y = 0.f;
-                        int32_t idp1 = 0;
-                        if (o0 + lane < nobj) {
-                            const int r = obefore + __popc(win & lanemask_le) - 1;
-                            const int32_t i = sm.oseg_base[r] + (o0 + lane - sm.oseg_start[r]);
-                            x = g.xs[i];
-                            y = g.ys[i];
-                            idp1 = g.sid[i] + 1;
-                            keep = point_box_lb(x, y, bx0, bx1, by0, by1) <= R2;
+                        const unsigned win1 = __reduce_or_sync(
+                            kFull, oseg_on && oseg_at >= o0 + 32 && oseg_at < o0 + 64
+                                       ? 1u << (oseg_at - o0 - 32) : 0u);
+                        bool keep0 = false, keep1 = false;
+                        float x0 = 0.f, y0 = 0.f, x1 = 0.f, y1 = 0.f;
+                        int32_t id0 = 0, id1 = 0;
+                        const int32_t j0 = o0 + lane, j1 = o0 + 32 + lane;
+                        if (j0 < nobj) {
+                            const int r = obefore + __popc(win0 & lanemask_le) - 1;
+                            const int32_t i = sm.oseg_base[r] + (j0 - sm.oseg_start[r]);
+                            x0 = g.xs[i];
+                            y0 = g.ys[i];
+                            id0 = g.sid[i] + 1;
                         }
-                        obefore += __popc(win);
-                        const unsigned km = __ballot_sync(kFull, keep);
-                        if (keep) {
-                            const int pos = kept + __popc(km & lanemask_lt);
-                            sxy[4 * (pos >> 1) + (pos & 1)] = x;
-                            sxy[4 * (pos >> 1) + 2 + (pos & 1)] = y;
-                            sm.idp1[pos] = idp1;
+                        if (j1 < nobj) {
+                            const int r = obefore + __popc(win0) + __popc(win1 & lanemask_le) - 1;
+                            const int32_t i = sm.oseg_base[r] + (j1 - sm.oseg_start[r]);
+                            x1 = g.xs[i];
+                            y1 = g.ys[i];
+                            id1 = g.sid[i] + 1;
                         }
-                        kept += __popc(km);
-                        o0 += 32;
+                        if (j0 < nobj) keep0 = point_box_lb(x0, y0, bx0, bx1, by0, by1) <= R2;
+                        if (j1 < nobj) keep1 = point_box_lb(x1, y1, bx0, bx1, by0, by1) <= R2;
+                        obefore += __popc(win0) + __popc(win1);
+                        const unsigned km0 = __ballot_sync(kFull, keep0);
+                        const unsigned km1 = __ballot_sync(kFull, keep1);
+                        if (keep0) {
+                            const int pos = kept + __popc(km0 & lanemask_lt);
+                            sxy[4 * (pos >> 1) + (pos & 1)] = x0;
+                            sxy[4 * (pos >> 1) + 2 + (pos & 1)] = y0;
+                            sm.idp1[pos] = id0;
+                        }
+                        if (keep1) {
+                            const int pos = kept + __popc(km0) + __popc(km1 & lanemask_lt);
+                            sxy[4 * (pos >> 1) + (pos & 1)] = x1;
+                            sxy[4 * (pos >> 1) + 2 + (pos & 1)] = y1;
+                            sm.idp1[pos] = id1;
+                        }
+                        kept += __popc(km0) + __popc(km1);
+                        o0 += 64;
                         continue;
                     }
                     if (l0 < nleaves) {
@@ -445,14 +539,6 @@ __global__ void __launch_bounds__(kGatherWarps * 32) k_expand_gather(const Gathe
                         continue;
                     }
                     // the next 32 cells, ring by ring, inside the current box
-                    {
-                        const float R = __fmul_ru(__fsqrt_ru(R2), 1.0000010f);
-                        cx0 = cell_g(__fsub_rd(bx0, R), g.x0, g.scale_g, g.G);
-                        cx1 = cell_g(__fadd_ru(bx1, R), g.x0, g.scale_g, g.G);
-                        cy0 = cell_g(__fsub_rd(by0, R), g.y0, g.scale_g, g.G);
-                        cy1 = cell_g(__fadd_ru(by1, R), g.y0, g.scale_g, g.G);
-                        rmax = max(max(ccx - cx0, cx1 - ccx), max(ccy - cy0, cy1 - ccy));
-                    }
                     if (ring_of(u0) > rmax) {
                         gdone = true;
                         break;
@@ -516,7 +602,11 @@ __global__ void __launch_bounds__(kGatherWarps * 32) k_expand_gather(const Gathe
             // expected count then at least doubles past k); the others take no
             // part
             const bool redo = active && kq > 0 && Ln.lst[KC - 1] == kPad;
-            if (!__any_sync(kFull, redo)) break;
+            if (!__any_sync(kFull, redo)) {
+                // a d^2 tie that the (d^2, id) order could resolve otherwise
+                if (__any_sync(kFull, active && kq > 0 && gtie<KC>(Ln, kq))) hand_back = true;
+                break;
+            }
             if (attempt >= 2) {
                 hand_back = true;
                 break;
@@ -530,6 +620,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32) k_expand_gather(const Gathe
                 for (int i = 0; i < KC; ++i) Ln.lst[i] = i < KC - kq ? 0ull : kPad;
                 spec_q *= grow;
                 Ln.thr = spec_q;
+                Ln.dropped = 0xFFFFFFFFu;
             } else {
                 Ln.thr = -kInf;
             }
@@ -550,6 +641,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32) k_expand_gather(const Gathe
             __syncwarp();
             sm.orig[lane] = active ? orig : -1;
             sm.kq[lane] = kq;
+            const bool full_rows = g.vec_out && k == KC;  // rows of KC entries, 16-byte stores
             const int vw = g.vec_out ? 4 : 1;
             const int per_row = k / vw;
             const int total = ql * per_row;
@@ -570,21 +662,34 @@ __global__ void __launch_bounds__(kGatherWarps * 32) k_expand_gather(const Gathe
                 __syncwarp();
                 uint32_t *out = pass == 0 ? reinterpret_cast<uint32_t *>(g.out_ids)
                                           : reinterpret_cast<uint32_t *>(g.out_d2);
-                for (int base = 0; base < total; base += 32) {
-                    const int v = base + lane;
-                    if (v < total) {
-                        const int row = v / per_row;
-                        const int c = (v - row * per_row) * vw;
-                        const int32_t o = sm.orig[row];
-                        if (o >= 0) {
-                            uint32_t *dst = out + (int64_t)o * k + c;
-                            if (vw == 4) {
-                                *reinterpret_cast<uint4 *>(dst) =
-                                    *reinterpret_cast<const uint4 *>(rows + row * S + (KC - k) + c);
-                            } else {
-                                const int kr = sm.kq[row];
-                                *dst = c < kr ? rows[row * S + (KC - kr) + c]
-                                              : (pass == 0 ? 0xFFFFFFFFu : 0x7f800000u);
+                if (full_rows) {
+                    constexpr int PR = KC / 4;  // 16-byte pieces per row
+#pragma unroll
+                    for (int base = 0; base < 32 * PR; base += 32) {
+                        const int v = base + lane;
+                        const int row = v / PR, c = (v % PR) * 4;
+                        const int32_t o = row < ql ? sm.orig[row] : -1;
+                        if (o >= 0)
+                            *reinterpret_cast<uint4 *>(out + (int64_t)o * KC + c) =
+                                *reinterpret_cast<const uint4 *>(rows + row * S + c);
+                    }
+                } else {
+                    for (int base = 0; base < total; base += 32) {
+                        const int v = base + lane;
+                        if (v < total) {
+                            const int row = v / per_row;
+                            const int c = (v - row * per_row) * vw;
+                            const int32_t o = sm.orig[row];
+                            if (o >= 0) {
+                                uint32_t *dst = out + (int64_t)o * k + c;
+                                if (vw == 4) {
+                                    *reinterpret_cast<uint4 *>(dst) =
+                                        *reinterpret_cast<const uint4 *>(rows + row * S + (KC - k) + c);
+                                } else {
+                                    const int kr = sm.kq[row];
+                                    *dst = c < kr ? rows[row * S + (KC - kr) + c]
+                                                  : (pass == 0 ? 0xFFFFFFFFu : 0x7f800000u);
+                                }
                             }
                         }
                     }
