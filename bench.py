@@ -54,13 +54,13 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def expand_profile():
-    """Per-launch DRAM traffic and ALU-pipe use of k_expand from the committed ncu
-    summary, or None when the kernel source changed since that capture."""
+def expand_profile(kernel="k_expand_gather", source="knn_expand_gather.cu"):
+    """Per-launch DRAM traffic and ALU-pipe use of the expansion kernel from the
+    committed ncu summary, or None when the kernel source changed since that capture."""
     import hashlib
     import re
-    prof = os.path.join(ROOT, "profiles", "k_expand_uniform1M_k16.md")
-    src = os.path.join(ROOT, "paper_1412_6170_gb300", "csrc", "knn_expand.cu")
+    prof = os.path.join(ROOT, "profiles", f"{kernel}_uniform1M_k16.md")
+    src = os.path.join(ROOT, "paper_1412_6170_gb300", "csrc", source)
     try:
         text = open(prof).read()
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
@@ -178,123 +178,313 @@ def cpu_baseline(workload, target_s: float = 12.0):
 
 
 def pct(v, q):
-    v = sorted(v)
+    v = sorted(float(x) for x in v)
     return v[min(len(v) - 1, int(round(q * (len(v) - 1))))]
 
 
-def serving_vs_plain(dev, n_worlds=8, n_obj=N_OBJ, k=K, n_req=128, load=0.8, n_slots=4,
-                     seed=7):
-    """Tick requests over several resident 1M-object worlds: the serving loop
-    (continuous batching over n_slots streams) against the same request stream
-    run one tick at a time (plain).  Arrivals are Poisson at `load` times the
-    plain capacity; each request is a full tick (all objects move and query)."""
+def _json_default(o):
+    """numpy scalars (and anything else with .item()) as plain JSON values."""
+    if hasattr(o, "item"):
+        return o.item()
+    raise TypeError(f"not JSON serializable: {type(o).__name__}")
+
+
+def _spawn_map(fn, items):
+    """Map over a spawn-context process pool (the GPU is in use in this process, so
+    workers must not be forked from it)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    with cf.ProcessPoolExecutor(max_workers=max(1, min(16, os.cpu_count() or 1)),
+                                mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(fn, items))
+
+
+def rows_vs_oracle(x, y, q_id, k, ids, d2, count=256, seed=0):
+    """Sampled rows of one tick (numpy ids/d2 for all of q_id) against the oracle."""
+    import numpy as np
+
+    import oracle
+    r = np.random.default_rng(seed)
+    rows = np.unique(r.choice(q_id.shape[0], min(count, q_id.shape[0]), replace=False))
+    rid, rd2, _ = oracle.knn(x, y, q_id[rows], k)
+    return bool(np.array_equal(ids[rows], rid)
+                and np.array_equal(d2[rows].view(np.uint32), rd2.view(np.uint32)))
+
+
+def serving_config5(dev, n_worlds=64, loads=(0.5, 0.8, 0.95), n_req=1000, n_slots=4, seed=5,
+                    check=True):
+    """The serving workload: a Poisson stream of tick requests over 64 resident
+    clustered worlds (10k-4M objects, k up to 64, 10-100 % of the objects query),
+    served by the request loop under a device-memory budget below the worlds'
+    total tick scratch (admission evicts idle worlds' scratch), against the same
+    requests run one knn_tick at a time (plain).  Each request is a tick of one
+    world: every object moves, a subset queries.  Offered loads are fractions of
+    the plain capacity (1 / mean plain service time)."""
     import numpy as np
     import torch
 
     from paper_1412_6170_gb300 import knnq, synth
+    from functools import partial
+    wl = _spawn_map(partial(synth.serving_world, seed=seed, n_worlds=n_worlds), range(n_worlds))
     ws = []
-    for i in range(n_worlds):
-        w = synth.plain_uniform_moving(n=n_obj, k=k, ticks=2, seed=seed * 100 + i)
-        ws.append({
-            "x": torch.from_numpy(w.x0).to(dev), "y": torch.from_numpy(w.y0).to(dev),
-            "ids": torch.from_numpy(w.ticks[0].upd_id).to(dev),
-            "ux": [torch.from_numpy(t.upd_x).to(dev) for t in w.ticks],
-            "uy": [torch.from_numpy(t.upd_y).to(dev) for t in w.ticks],
-            "oi": torch.empty((n_obj, k), dtype=torch.int32, device=dev),
-            "od": torch.empty((n_obj, k), dtype=torch.float32, device=dev)})
-
-    def req_args(i):
-        d = ws[i % n_worlds]
-        j = (i // n_worlds) % 2
-        return knnq.tick_args(k, d["ids"], d["ids"], d["ux"][j], d["uy"][j],
-                              out_ids=d["oi"], out_d2=d["od"])
-
+    for w in wl:
+        t = w.ticks[0]
+        x0, y0 = torch.from_numpy(w.x0).to(dev), torch.from_numpy(w.y0).to(dev)
+        nq = t.q_id.shape[0]
+        ws.append({"n": w.n, "k": w.k, "x": x0, "y": y0,
+                   "ids": torch.from_numpy(t.upd_id).to(dev),
+                   # two position sets used in turn: the tick's moves, then back
+                   "pos": [(torch.from_numpy(t.upd_x).to(dev), torch.from_numpy(t.upd_y).to(dev)),
+                           (x0, y0)],
+                   "q": torch.from_numpy(t.q_id).to(dev),
+                   "oi": torch.empty((nq, w.k), dtype=torch.int32, device=dev),
+                   "od": torch.empty((nq, w.k), dtype=torch.float32, device=dev)})
     stream = torch.cuda.current_stream()
-    plain = [knnq.World(d["x"], d["y"], k_max=k, max_queries=n_obj) for d in ws]
-    for i in range(2 * n_worlds):  # warm-up
-        a = req_args(i)
-        knnq.knn_tick(plain[i % n_worlds].handle, a.upd_id_dev, a.upd_x_dev, a.upd_y_dev,
-                      a.n_upd, a.q_id_dev, None, None, a.n_q, k, a.out_ids_dev, a.out_d2_dev,
+    total_q = sum(int(d["q"].shape[0]) for d in ws)
+
+    def args_for(i, parity, out=None):
+        d = ws[i]
+        ux, uy = d["pos"][parity]
+        oi, od = out if out is not None else (d["oi"], d["od"])
+        return knnq.tick_args(d["k"], d["q"], d["ids"], ux, uy, out_ids=oi, out_d2=od)
+
+    def plain_tick(worlds, i, a):
+        knnq.knn_tick(worlds[i].handle, a.upd_id_dev, a.upd_x_dev, a.upd_y_dev, a.n_upd,
+                      a.q_id_dev, None, None, a.n_q, a.k, a.out_ids_dev, a.out_d2_dev,
                       stream.cuda_stream)
+
+    # plain service time of every world (graphs recorded first)
+    plain = [knnq.World(d["x"], d["y"], k_max=d["k"], max_queries=d["n"]) for d in ws]
+    for i in range(n_worlds):
+        for par in (0, 1, 0, 1):
+            plain_tick(plain, i, args_for(i, par))
     torch.cuda.synchronize()
-    # plain service time (one tick, synchronised)
     svc = []
-    for i in range(2 * n_worlds):
+    for i in range(n_worlds):
         t0 = time.perf_counter()
-        a = req_args(i)
-        knnq.knn_tick(plain[i % n_worlds].handle, a.upd_id_dev, a.upd_x_dev, a.upd_y_dev,
-                      a.n_upd, a.q_id_dev, None, None, a.n_q, k, a.out_ids_dev, a.out_d2_dev,
-                      stream.cuda_stream)
+        plain_tick(plain, i, args_for(i, 0))
         torch.cuda.synchronize()
-        svc.append(time.perf_counter() - t0)
-    service = statistics.median(svc)
-    rng = np.random.default_rng(seed)
-    gaps = rng.exponential(service / load, n_req)
-    arrive = np.cumsum(gaps) - gaps[0]
+        t1 = time.perf_counter()
+        plain_tick(plain, i, args_for(i, 1))
+        torch.cuda.synchronize()
+        svc.append(0.5 * (time.perf_counter() - t0))
+        del t1
+    mean_service = float(np.mean(svc))
+
+    # request streams: a world drawn uniformly per request, Poisson arrivals
+    plans = {}
+    for li, load in enumerate(loads):
+        r = np.random.default_rng(seed * 1000 + li)
+        who = r.integers(0, n_worlds, n_req)
+        gaps = r.exponential(mean_service / load, n_req)
+        checked = set(int(v) for v in np.linspace(n_req // 8, n_req - 1, 4).astype(int))
+        plans[load] = (who, np.cumsum(gaps) - gaps[0], checked)
+    outs = {}  # (load, request) -> dedicated output tensors of a checked request
+
+    def out_for(load, j, i):
+        key = (load, j)
+        if key not in outs:
+            d = ws[i]
+            outs[key] = {"plain": (torch.empty_like(d["oi"]), torch.empty_like(d["od"])),
+                         "served": (torch.empty_like(d["oi"]), torch.empty_like(d["od"]))}
+        return outs[key]
 
     def spin_until(t_abs):
         while time.perf_counter() < t_abs:
             pass
 
-    # plain: FIFO, one tick at a time
-    lat_p = []
-    t_base = time.perf_counter() + 0.01
-    for i in range(n_req):
-        spin_until(t_base + arrive[i])
-        a = req_args(i)
-        knnq.knn_tick(plain[i % n_worlds].handle, a.upd_id_dev, a.upd_x_dev, a.upd_y_dev,
-                      a.n_upd, a.q_id_dev, None, None, a.n_q, k, a.out_ids_dev, a.out_d2_dev,
-                      stream.cuda_stream)
-        torch.cuda.synchronize()
-        lat_p.append(time.perf_counter() - (t_base + arrive[i]))
-    span_p = (time.perf_counter() - t_base)
+    parity = [0] * n_worlds
+    results = {}
+    for load in loads:
+        who, arrive, checked = plans[load]
+        par_seq = []
+        for j in range(n_req):
+            i = int(who[j])
+            par_seq.append(parity[i])
+            parity[i] ^= 1
+        plans[load] = (who, arrive, checked, par_seq)
+        for j in checked:  # graphs of the checked requests' own outputs, before timing
+            i = int(who[j])
+            plain[i].record_tick(ws[i]["k"], ws[i]["q"], ws[i]["ids"], *ws[i]["pos"][par_seq[j]],
+                                 out_ids=out_for(load, j, i)["plain"][0],
+                                 out_d2=out_for(load, j, i)["plain"][1])
+        lat = []
+        t_base = time.perf_counter() + 0.01
+        for j in range(n_req):
+            i = int(who[j])
+            spin_until(t_base + arrive[j])
+            o = out_for(load, j, i)["plain"] if j in checked else None
+            plain_tick(plain, i, args_for(i, par_seq[j], o))
+            torch.cuda.synchronize()
+            lat.append(time.perf_counter() - (t_base + arrive[j]))
+        span = time.perf_counter() - t_base
+        q = sum(int(ws[int(i)]["q"].shape[0]) for i in who)
+        results[load] = {"plain": {"p50_ms": 1e3 * pct(lat, 0.5), "p99_ms": 1e3 * pct(lat, 0.99),
+                                   "queries_per_s_at_load": q / span}}
+    # plain saturated: every request of the 0.8 stream back to back
+    who, _, _, par_seq = plans[loads[len(loads) // 2]]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for j in range(n_req):
+        plain_tick(plain, int(who[j]), args_for(int(who[j]), par_seq[j]))
+    torch.cuda.synchronize()
+    sat_plain = time.perf_counter() - t0
+    q_sat = sum(int(ws[int(i)]["q"].shape[0]) for i in who)
     for w in plain:
         w.close()
+    del plain
+    torch.cuda.synchronize()
 
-    # served: the serving loop, same arrivals
-    srv = knnq.knn_server_create(n_slots, 0)
-    idx = [knnq.knn_server_add_world(srv, knnq.knn_world_desc(0.0, 0.0, 1.0, 0, 0, k, n_obj),
-                                     d["x"].data_ptr(), d["y"].data_ptr(), n_obj) for d in ws]
-    warm = [knnq.knn_server_submit(srv, idx[i % n_worlds], req_args(i)) for i in range(n_worlds)]
-    for r in warm:
-        knnq.knn_server_wait(srv, r)
-    rids = []
-    t_base = time.perf_counter() + 0.01
-    for i in range(n_req):
-        spin_until(t_base + arrive[i])
-        rids.append(knnq.knn_server_submit(srv, idx[i % n_worlds], req_args(i)))
-    lat_s = [knnq.knn_server_wait(srv, r) / 1e3 for r in rids]
-    span_s = (time.perf_counter() - t_base)
-    # saturation: every request submitted at once
+    # the total tick scratch of the worlds, then a budget below it
+    probe = knnq.knn_server_create(n_slots, 0)
+    idx = [knnq.knn_server_add_world(probe, knnq.knn_world_desc(0.0, 0.0, 1.0, 0, 0, d["k"],
+                                                                d["n"]),
+                                     d["x"].data_ptr(), d["y"].data_ptr(), d["n"]) for d in ws]
+    for r in [knnq.knn_server_submit(probe, idx[i], args_for(i, 1)) for i in range(n_worlds)]:
+        knnq.knn_server_wait(probe, r)
+    st0 = knnq.knn_server_stats(probe)
+    knnq.knn_server_destroy(probe)
+    total_scratch = int(st0["scratch_bytes"])
+    budget = max(int(1.5 * st0["largest_world_scratch"]), int(0.35 * total_scratch))
+    srv = knnq.knn_server_create(n_slots, budget)
+    idx = [knnq.knn_server_add_world(srv, knnq.knn_world_desc(0.0, 0.0, 1.0, 0, 0, d["k"], d["n"]),
+                                     d["x"].data_ptr(), d["y"].data_ptr(), d["n"]) for d in ws]
+    # warm-up: every world once on each position set (the worlds end where the
+    # plain ones started each stream: parity bookkeeping as in the plain runs)
+    for par in (0, 1):
+        for r in [knnq.knn_server_submit(srv, idx[i], args_for(i, par)) for i in range(n_worlds)]:
+            knnq.knn_server_wait(srv, r)
+    base = knnq.knn_server_stats(srv)
+    for load in loads:
+        who, arrive, checked, par_seq = plans[load]
+        before = knnq.knn_server_stats(srv)
+        rids = []
+        t_base = time.perf_counter() + 0.01
+        for j in range(n_req):
+            i = int(who[j])
+            spin_until(t_base + arrive[j])
+            o = out_for(load, j, i)["served"] if j in checked else None
+            rids.append(knnq.knn_server_submit(srv, idx[i], args_for(i, par_seq[j], o)))
+        lat = [knnq.knn_server_wait(srv, r) / 1e3 for r in rids]
+        span = time.perf_counter() - t_base
+        after = knnq.knn_server_stats(srv)
+        q = sum(int(ws[int(i)]["q"].shape[0]) for i in who)
+        results[load]["served"] = {"p50_ms": 1e3 * pct(lat, 0.5), "p99_ms": 1e3 * pct(lat, 0.99),
+                                   "queries_per_s_at_load": q / span,
+                                   "admitted": after["admitted"] - before["admitted"],
+                                   "evictions": after["evictions"] - before["evictions"]}
+    who, _, _, par_seq = plans[loads[len(loads) // 2]]
     t0 = time.perf_counter()
-    rids = [knnq.knn_server_submit(srv, idx[i % n_worlds], req_args(i)) for i in range(n_req)]
+    rids = [knnq.knn_server_submit(srv, idx[int(who[j])], args_for(int(who[j]), par_seq[j]))
+            for j in range(n_req)]
     for r in rids:
         knnq.knn_server_wait(srv, r)
-    sat_s = time.perf_counter() - t0
+    sat_served = time.perf_counter() - t0
+    st = knnq.knn_server_stats(srv)
+    status_ok = all(knnq.knn_server_world_status(srv, j)[0] == knnq.KNN_OK for j in idx)
     knnq.knn_server_destroy(srv)
-    plain = [knnq.World(d["x"], d["y"], k_max=k, max_queries=n_obj) for d in ws]
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for i in range(n_req):
-        a = req_args(i)
-        knnq.knn_tick(plain[i % n_worlds].handle, a.upd_id_dev, a.upd_x_dev, a.upd_y_dev,
-                      a.n_upd, a.q_id_dev, None, None, a.n_q, k, a.out_ids_dev, a.out_d2_dev,
-                      stream.cuda_stream)
-    torch.cuda.synchronize()
-    sat_p = time.perf_counter() - t0
-    for w in plain:
-        w.close()
-    q = n_req * n_obj
+
+    # checked requests: served rows = plain rows, and sampled rows = the oracle
+    same = True
+    oracle_ok = True if check else None
+    n_checked = 0
+    for (load, j), o in outs.items():
+        who, _, _, par_seq = plans[load]
+        i = int(who[j])
+        pi, pd = (t.cpu().numpy() for t in o["plain"])
+        si, sd = (t.cpu().numpy() for t in o["served"])
+        same = same and np.array_equal(pi, si) and np.array_equal(pd.view(np.uint32),
+                                                                  sd.view(np.uint32))
+        if check:
+            w = wl[i]
+            x, y = (w.ticks[0].upd_x, w.ticks[0].upd_y) if par_seq[j] == 0 else (w.x0, w.y0)
+            oracle_ok = oracle_ok and rows_vs_oracle(x, y, w.ticks[0].q_id, w.k, si, sd,
+                                                     count=128, seed=j)
+        n_checked += 1
+    for load in loads:
+        results[load]["served_beats_plain_p99"] = \
+            results[load]["served"]["p99_ms"] < results[load]["plain"]["p99_ms"]
     return {
-        "workload": f"{n_worlds} resident worlds x {n_obj} uniform objects, k={k}, "
-                    f"{n_req} tick requests (all objects move and query), Poisson arrivals "
-                    f"at {load} x plain capacity; served: {n_slots} stream slots",
-        "plain_service_ms": 1e3 * service,
-        "served": {"p50_ms": 1e3 * pct(lat_s, 0.5), "p99_ms": 1e3 * pct(lat_s, 0.99),
-                   "queries_per_s_at_load": q / span_s, "queries_per_s_saturated": q / sat_s},
-        "plain": {"p50_ms": 1e3 * pct(lat_p, 0.5), "p99_ms": 1e3 * pct(lat_p, 0.99),
-                  "queries_per_s_at_load": q / span_p, "queries_per_s_saturated": q / sat_p},
+        "workload": f"{n_worlds} resident clustered worlds, {sum(d['n'] for d in ws)} objects "
+                    f"(10k-4M each, log-uniform), k in {{4,8,16,32,64}}, 10-100 % querying "
+                    f"({total_q} queries if every world ticks once); {n_req} Poisson tick "
+                    f"requests per offered load, a world drawn uniformly per request",
+        "plain_mean_service_ms": 1e3 * mean_service,
+        "served_config": {"stream_slots": n_slots, "hbm_budget_bytes": budget,
+                          "worlds_total_scratch_bytes": total_scratch,
+                          "largest_world_scratch_bytes": int(st0["largest_world_scratch"])},
+        "by_load": {str(load): results[load] for load in loads},
+        "saturated_queries_per_s": {"served": q_sat / sat_served, "plain": q_sat / sat_plain},
+        "server_totals": {"admitted": st["admitted"] - base["admitted"],
+                          "evictions": st["evictions"] - base["evictions"],
+                          "completed": st["completed"]},
+        "rows_checked": {"requests": n_checked, "served_equals_plain": bool(same),
+                         "sampled_rows_equal_oracle": oracle_ok, "device_status_ok": status_ok},
     }
+
+
+def skewed_config3(dev, ticks=10, rounds=3, seed=0, check=True):
+    """The skewed workload: 4M objects, 90 % in 64 Gaussian hotspots, a fresh random
+    25 % querying each tick, k = 32, N(0, 5e-4) moves; the ten ticks are replayed
+    `rounds` times (each tick sets every position, so a replay is a valid tick) for
+    per-tick latency, with per-stage events for the expansion's roofline."""
+    import numpy as np
+    import torch
+
+    from paper_1412_6170_gb300 import knnq, synth
+    k, n = 32, 4_000_000
+    w = synth.skewed_moving(n=n, k=k, ticks=ticks, seed=seed)
+    x0, y0 = torch.from_numpy(w.x0).to(dev), torch.from_numpy(w.y0).to(dev)
+    ids = torch.from_numpy(w.ticks[0].upd_id).to(dev)
+    tk = [(torch.from_numpy(t.upd_x).to(dev), torch.from_numpy(t.upd_y).to(dev),
+           torch.from_numpy(t.q_id).to(dev)) for t in w.ticks]
+    nq = w.ticks[0].q_id.shape[0]
+    oi = torch.empty((nq, k), dtype=torch.int32, device=dev)
+    od = torch.empty((nq, k), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    world = knnq.World(x0, y0, k_max=k, max_queries=nq)
+    world.set_profiling(True)
+    stream = torch.cuda.current_stream()
+    try:
+        for t in range(ticks):  # warm-up: records the tick graphs
+            world.tick(k, tk[t][2], ids, tk[t][0], tk[t][1], out_ids=oi, out_d2=od)
+        torch.cuda.synchronize()
+        ms, exp_ms = [], []
+        for r in range(rounds):
+            for t in range(ticks):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                world.tick(k, tk[t][2], ids, tk[t][0], tk[t][1], out_ids=oi, out_d2=od)
+                b.record(stream)
+                b.synchronize()
+                ms.append(a.elapsed_time(b))
+                exp_ms.append(world.stage_times()["expand"])
+        ok = None
+        if check:
+            t = w.ticks[ticks - 1]
+            ok = rows_vs_oracle(t.upd_x, t.upd_y, t.q_id, k, oi.cpu().numpy(), od.cpu().numpy(),
+                                count=2000, seed=3)
+        info = world.expand_info()
+        st = world.status()[0]
+    finally:
+        world.close()
+    hbm, hbm_kind = peaks()
+    bpq = 12 + 12 * n / nq + 8 * k
+    e = statistics.median(exp_ms)
+    return {"workload": f"{n} objects, 90% in 64 Gaussian hotspots (sigma 0.01), a random 25% "
+                        f"({nq}) query each tick, k={k}, N(0,5e-4) moves, {ticks} ticks x "
+                        f"{rounds} rounds, L2 flushed between ticks",
+            "queries_per_s": nq * len(ms) / (sum(ms) / 1e3),
+            "ms_per_tick": sum(ms) / len(ms), "p50_tick_ms": pct(ms, 0.5),
+            "p99_tick_ms": pct(ms, 0.99), "ticks_timed": len(ms),
+            "expand_ms": e,
+            "expand_roofline": {"algorithmic_bytes_per_query": bpq,
+                                "achieved_gbs": bpq * nq / (e / 1e3) / 1e9, "peak_gbs": hbm,
+                                "peak_kind": hbm_kind,
+                                "frac": bpq * nq / (e / 1e3) / 1e9 / hbm},
+            "expand_form": info, "rows_vs_oracle": ok, "device_status_ok": st == knnq.KNN_OK}
 
 
 def index_reuse_vs_rebuild(dev, ticks=20, max_age=8):
@@ -339,9 +529,9 @@ def index_reuse_vs_rebuild(dev, ticks=20, max_age=8):
 
 
 def expansion_ablation(dev, ticks=3):
-    """The headline workload's expansion in each form: packets (the default for
-    k = 16), one warp per query, and the paper's multi-pass iterative form; tick
-    times and whether the rows agree."""
+    """The headline workload's expansion in each form: gathered packets (the
+    default for k = 16), packets walking the quadtree, one warp per query, and
+    the paper's multi-pass iterative form; tick times and whether the rows agree."""
     import torch
 
     from paper_1412_6170_gb300 import knnq, synth
@@ -351,7 +541,8 @@ def expansion_ablation(dev, ticks=3):
     uy = [torch.from_numpy(t.upd_y).to(dev) for t in wl.ticks]
     stream = torch.cuda.current_stream()
     out, rows = {}, {}
-    for name, exp in (("packets", 1), ("warp per query", 2), ("multi-pass iterative", 3)):
+    for name, exp in (("gathered packets", 4), ("packets", 1), ("warp per query", 2),
+                      ("multi-pass iterative", 3)):
         x0, y0 = torch.from_numpy(wl.x0).to(dev), torch.from_numpy(wl.y0).to(dev)
         world = knnq.World(x0, y0, k_max=K, max_queries=N_OBJ)
         world.set_tuning(expansion=exp)
@@ -455,8 +646,8 @@ def k_sweep(dev, ks=(1, 4, 16, 32, 64, 128, 256, 512), iters=3):
             e1.record(stream)
             e1.synchronize()
             ms = e0.elapsed_time(e1) / iters
-            kernel = "warp per query" if world.get_tuning(N_OBJ, k)["expansion"] == 2 \
-                else "packets"
+            kernel = {1: "packets", 2: "warp per query", 4: "gathered packets"}.get(
+                world.get_tuning(N_OBJ, k)["expansion"], "packets")
             out[str(k)] = {"tick_ms": ms, "queries_per_s": N_OBJ / (ms * 1e-3),
                            "expansion": kernel}
             del oi, od
@@ -468,7 +659,9 @@ def k_sweep(dev, ks=(1, 4, 16, 32, 64, 128, 256, 512), iters=3):
 
 def batched_vs_plain(dev, n_worlds=256, seed=0, iters=5):
     """Many uneven worlds (1k-200k objects, uniform or clustered, k in {4,8,16,32}, all
-    query): one knn_batch_tick (a recorded CUDA graph) against one knn_tick per world."""
+    query): one knn_batch_tick (a recorded CUDA graph) against one knn_tick per world,
+    with the automatic settings and after knn_world_autotune chose each world's; the
+    batched rows are compared with the plain ones, world by world."""
     import torch
 
     from paper_1412_6170_gb300 import knnq, synth
@@ -480,33 +673,41 @@ def batched_vs_plain(dev, n_worlds=256, seed=0, iters=5):
         d = {"ids": torch.from_numpy(t.upd_id).to(dev), "ux": torch.from_numpy(t.upd_x).to(dev),
              "uy": torch.from_numpy(t.upd_y).to(dev), "q": torch.from_numpy(t.q_id).to(dev),
              "oi": torch.empty((t.q_id.shape[0], w.k), dtype=torch.int32, device=dev),
-             "od": torch.empty((t.q_id.shape[0], w.k), dtype=torch.float32, device=dev)}
+             "od": torch.empty((t.q_id.shape[0], w.k), dtype=torch.float32, device=dev),
+             "pi": torch.empty((t.q_id.shape[0], w.k), dtype=torch.int32, device=dev),
+             "pd": torch.empty((t.q_id.shape[0], w.k), dtype=torch.float32, device=dev)}
         data.append(d)
         x, y = torch.from_numpy(w.x0).to(dev), torch.from_numpy(w.y0).to(dev)
         worlds_b.append(knnq.World(x, y, k_max=w.k, max_queries=w.n))
         worlds_p.append(knnq.World(x, y, k_max=w.k, max_queries=w.n))
     args = [knnq.tick_args(w.k, d["q"], d["ids"], d["ux"], d["uy"], out_ids=d["oi"],
                            out_d2=d["od"]) for w, d in zip(wl, data)]
+    pargs = [knnq.tick_args(w.k, d["q"], d["ids"], d["ux"], d["uy"], out_ids=d["pi"],
+                            out_d2=d["pd"]) for w, d in zip(wl, data)]
     handles = [w.handle for w in worlds_b]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t0 = time.perf_counter()
-    knnq.knn_batch_tick(handles, args, stream.cuda_stream)  # records the graph
-    torch.cuda.synchronize()
-    record_s = time.perf_counter() - t0
-    for _ in range(2):
-        knnq.knn_batch_tick(handles, args, stream.cuda_stream)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(iters):
-        knnq.knn_batch_tick(handles, args, stream.cuda_stream)
-    e1.record(stream)
-    e1.synchronize()
-    batch_ms = e0.elapsed_time(e1) / iters
+
+    def batched_ms():
+        knnq.knn_batch_tick(handles, args, stream.cuda_stream)  # (re)records the graph
+        torch.cuda.synchronize()
+        for _ in range(2):
+            knnq.knn_batch_tick(handles, args, stream.cuda_stream)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(iters):
+            knnq.knn_batch_tick(handles, args, stream.cuda_stream)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / iters
 
     def plain_pass():
-        for w, a in zip(worlds_p, args):
+        for w, a in zip(worlds_p, pargs):
             knnq.knn_tick(w.handle, a.upd_id_dev, a.upd_x_dev, a.upd_y_dev, a.n_upd, a.q_id_dev,
                           None, None, a.n_q, a.k, a.out_ids_dev, a.out_d2_dev, stream.cuda_stream)
+
+    t0 = time.perf_counter()
+    batch_default = batched_ms()
+    record_s = time.perf_counter() - t0
     plain_pass()
     torch.cuda.synchronize()
     e0.record(stream)
@@ -517,15 +718,34 @@ def batched_vs_plain(dev, n_worlds=256, seed=0, iters=5):
     e1.synchronize()
     plain_ms = e0.elapsed_time(e1) / iters
     plain_host_ms = 1e3 * (time.perf_counter() - t0) / iters
+    same_default = all(torch.equal(d["oi"], d["pi"]) and torch.equal(d["od"].view(torch.int32),
+                                                                     d["pd"].view(torch.int32))
+                       for d in data)
+    # autotune every batched world on its own queries, then time the batch again
+    t0 = time.perf_counter()
+    chosen = {}
+    for w, d, wb in zip(wl, data, worlds_b):
+        c = wb.autotune(w.k, d["q"], trials=1)
+        key = f"expansion {c['expansion']}"
+        chosen[key] = chosen.get(key, 0) + 1
+    tune_s = time.perf_counter() - t0
+    batch_tuned = batched_ms()
+    same_tuned = all(torch.equal(d["oi"], d["pi"]) and torch.equal(d["od"].view(torch.int32),
+                                                                   d["pd"].view(torch.int32))
+                     for d in data)
     q = sum(int(a.n_q) for a in args)
     for w in worlds_b + worlds_p:
         w.close()
     return {"workload": f"{n_worlds} worlds, {sum(w.n for w in wl)} objects, {q} queries per "
                         "batch tick; objects log-uniform in [1k, 200k], uniform or clustered, "
                         "k in {4,8,16,32}",
-            "batched_ms": batch_ms, "plain_ms": plain_ms, "plain_host_ms": plain_host_ms,
-            "batched_queries_per_s": q / (batch_ms / 1e3),
-            "plain_queries_per_s": q / (plain_ms / 1e3), "graph_record_s": record_s}
+            "batched_ms": batch_tuned, "batched_default_ms": batch_default,
+            "plain_ms": plain_ms, "plain_host_ms": plain_host_ms,
+            "batched_queries_per_s": q / (batch_tuned / 1e3),
+            "batched_default_queries_per_s": q / (batch_default / 1e3),
+            "plain_queries_per_s": q / (plain_ms / 1e3), "graph_record_s": record_s,
+            "autotune_s": tune_s, "autotune_chosen_forms": chosen,
+            "rows_identical_to_plain": {"default": same_default, "tuned": same_tuned}}
 
 
 def run_reference(args):
@@ -565,7 +785,7 @@ def run_reference(args):
                                        f"{N_OBJ} objects"},
             "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+    print(json.dumps(line, default=_json_default), flush=True)
 
 
 def run_gpu(args):
@@ -667,6 +887,18 @@ def run_gpu(args):
         dist.barrier()
     launches = world.launches() - launches0
     step_ms = [a.elapsed_time(b) for a, b in ev]
+    # tick latency over many ticks (same steps: moves copied in, L2 flushed, one
+    # tick timed by events each)
+    lat_ms = []
+    for s in range(args.latency_ticks):
+        stage_inputs(s)
+        flush.zero_()
+        a, b = ev[s % len(ev)]
+        a.record(stream)
+        tick(s)
+        b.record(stream)
+        b.synchronize()
+        lat_ms.append(a.elapsed_time(b))
     total_ms = max_over_ranks([sum(step_ms)], dist, dev)[0]
     st, bits = world.status()
     if st != knnq.KNN_OK:
@@ -745,18 +977,20 @@ def run_gpu(args):
                                                                     rd2.view(np.uint32)))
         if not e2e_spot:
             raise RuntimeError("host-buffer rows differ from the oracle on the spot check")
+    form = world.get_tuning(N_OBJ, K)["expansion"]
     world.close()
     if rank != 0:
         return
     n_gpus = world_size
     value = replicas_value(n_gpus, N_OBJ * args.steps, total_ms / 1e3)
-    srt = sorted(step_ms)
-    p99 = srt[min(len(srt) - 1, int(round(0.99 * (len(srt) - 1))))]
-    p50 = statistics.median(step_ms)
+    p99 = pct(lat_ms, 0.99) if lat_ms else pct(step_ms, 0.99)
+    p50 = pct(lat_ms, 0.5) if lat_ms else statistics.median(step_ms)
     exp_ms = stage_sums["expand"] / args.steps
     hbm, hbm_kind = peaks()
     achieved = ALGO_BYTES_PER_QUERY * N_OBJ / (exp_ms / 1e3) / 1e9
-    prof = expand_profile()
+    kernel, source = ("k_expand_gather", "knn_expand_gather.cu") if form == 4 else \
+        ("k_expand", "knn_expand.cu")
+    prof = expand_profile(kernel, source)
     traffic = None if prof is None else prof["traffic"]
     n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
     clk_sum = clk.summary()
@@ -771,9 +1005,9 @@ def run_gpu(args):
                            "device, copied in before each step's timed region)",
                    "l2": "flushed between steps",
                    "parallelism": "replicas" if n_gpus > 1 else "single GPU"},
-        "p50_tick_ms": p50, "p99_tick_ms": p99,
+        "p50_tick_ms": p50, "p99_tick_ms": p99, "latency_ticks": len(lat_ms),
         "stages_ms": {k: v / args.steps for k, v in stage_sums.items()},
-        "roofline": {"kernel": "k_expand", "bound": "hbm", "achieved": achieved, "peak": hbm,
+        "roofline": {"kernel": kernel, "bound": "hbm", "achieved": achieved, "peak": hbm,
                      "peak_kind": hbm_kind, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": traffic,
                      "algorithmic_bytes_per_query": ALGO_BYTES_PER_QUERY,
@@ -808,7 +1042,8 @@ def run_gpu(args):
         "wall_s": wall,
     }
     if not args.no_patterns:
-        line["serving"] = serving_vs_plain(dev)
+        line["serving"] = serving_config5(dev, check=not args.no_check)
+        line["skewed"] = skewed_config3(dev, check=not args.no_check)
         line["batching"] = batched_vs_plain(dev)
         line["k_sweep"] = k_sweep(dev)
         line["index_reuse"] = index_reuse_vs_rebuild(dev)
@@ -816,7 +1051,7 @@ def run_gpu(args):
         line["expansion_ablation"] = expansion_ablation(dev)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
-    print(json.dumps(line), flush=True)
+    print(json.dumps(line, default=_json_default), flush=True)
     if dist is not None:
         dist.destroy_process_group()
 
@@ -830,7 +1065,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-patterns", action="store_true",
-                    help="skip the serving and batching comparisons")
+                    help="skip the serving, skewed, batching and other comparison legs")
+    ap.add_argument("--latency-ticks", type=int, default=200,
+                    help="ticks timed one by one for p50/p99 tick latency")
     args = ap.parse_args()
     if args.warmup < 1:
         args.warmup = 1

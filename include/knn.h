@@ -296,10 +296,12 @@ typedef struct {
 knn_status knn_world_set_tuning(knn_world w, const knn_tuning *t);
 /* Autotuner: runs `trials` ticks without updates for each of a small set of
  * leaf capacities, cell-map levels and packet levels around the automatic
- * choice, with the given queries (device arrays as for knn_tick; the output
- * arrays receive the rows, identical for every setting), keeps the fastest
- * in the world and writes it to *chosen (may be NULL).  Synchronizes
- * `stream`.  The world's positions are unchanged. */
+ * choice, then for the fastest of those each expansion form (threads per
+ * query: a lane in packets or a warp per query; candidates staged along the
+ * walk or gathered at once), with the given queries (device arrays as for
+ * knn_tick; the output arrays receive the rows, identical for every setting),
+ * keeps the fastest in the world and writes it to *chosen (may be NULL).
+ * Synchronizes `stream`.  The world's positions are unchanged. */
 knn_status knn_world_autotune(knn_world w, const int32_t *q_id_dev, const float *q_x_dev,
                               const float *q_y_dev, int64_t n_q, int32_t k,
                               int32_t *out_ids_dev, float *out_d2_dev, int32_t trials,

@@ -91,11 +91,12 @@ extern "C" knn_status knn_batch_tick(int32_t n_worlds, const knn_world *worlds,
 
     // Shape: the plan of every world (and whether updates run) fixes the graph's nodes.
     std::vector<int> shape;
-    shape.reserve(7 * n_worlds);
+    shape.reserve(8 * n_worlds);
     for (int32_t i = 0; i < n_worlds; ++i) {
         const knnq::Plan p = knnq::plan_for(worlds[i]->w, args[i].n_q, args[i].k);
-        shape.insert(shape.end(), {p.th, p.G, p.Gp, (int)p.wide, args[i].n_upd > 0,
-                                   args[i].q_x_dev != nullptr, args[i].n_q > 0});
+        shape.insert(shape.end(), {p.th, p.G, p.Gp, (int)p.wide, (int)p.gather,
+                                   args[i].n_upd > 0, args[i].q_x_dev != nullptr,
+                                   args[i].n_q > 0});
     }
     bool reuse = g.exec && (int32_t)g.worlds.size() == n_worlds && g.shape == shape;
     for (int32_t i = 0; reuse && i < n_worlds; ++i)
@@ -205,6 +206,33 @@ extern "C" knn_status knn_world_autotune(knn_world h, const int32_t *q_id_dev,
     float best = 1e30f;
     knn_tuning best_t = cand.empty() ? automatic : cand[0];
     for (const knn_tuning &t : cand) {
+        w.tuning = t;
+        knnq::enqueue_tick(w, a, s, false);  // warm
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < trials; ++r) knnq::enqueue_tick(w, a, s, false);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            w.tuning = saved;
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return bad(KNN_ERR_CUDA, "knn_world_autotune: a trial tick failed");
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            best_t = t;
+        }
+    }
+    // then the expansion form on the best index setting: threads per query (one
+    // lane in packets, or a whole warp) and how candidates are staged (leaf by
+    // leaf along the walk, or gathered for the whole search box at once)
+    std::vector<int> forms = {1, 2};
+    if (k <= 32) forms.push_back(4);
+    const knn_tuning base_t = best_t;
+    for (int f : forms) {
+        knn_tuning t = base_t;
+        t.expansion = f;
         w.tuning = t;
         knnq::enqueue_tick(w, a, s, false);  // warm
         cudaEventRecord(e0, s);

@@ -191,6 +191,34 @@ def world_positions(n: int, seed: int, clustered: bool) -> tuple[np.ndarray, np.
     return clustered_positions(n, seed) if clustered else uniform_positions(n, seed)
 
 
+def serving_world(i: int, seed: int = 0, n_worlds: int = 64, n_lo: int = 10_000,
+                  n_hi: int = 4_000_000, ks=(4, 8, 16, 32, 64), query_frac=(0.1, 1.0),
+                  sigma: float = 5e-4) -> "Workload":
+    """World ``i`` of :func:`serving_worlds` (each world is drawn from its own streams,
+    so the worlds can be generated independently, e.g. in worker processes)."""
+    u = uniform_f64(seed, 202, 3 * n_worlds).reshape(n_worlds, 3)
+    n = int(round(np.exp(np.log(n_lo) + u[i, 0] * (np.log(n_hi) - np.log(n_lo)))))
+    k = int(ks[min(len(ks) - 1, int(u[i, 1] * len(ks)))])
+    qf = query_frac[0] + u[i, 2] * (query_frac[1] - query_frac[0])
+    ws = seed * 7919 + 5000 + i
+    x, y = clustered_positions(n, ws)
+    w = Workload(f"world {i}: n={n} k={k} clustered, {qf:.0%} query", n, k, x, y)
+    cx, cy = random_walk(x, y, sigma, ws, 1)
+    nq = max(1, int(round(n * qf)))
+    w.ticks.append(Tick(np.arange(n, dtype=np.int32), cx, cy, random_subset(n, nq, ws, 1), k))
+    return w
+
+
+def serving_worlds(n_worlds: int = 64, seed: int = 0, map_fn=map, **kw) -> list:
+    """Resident worlds of a serving loop: object counts log-uniform in [10k, 4M], all
+    clustered as the 4M skewed workload, k drawn from {4, 8, 16, 32, 64}, a query
+    fraction uniform in [0.1, 1]; one tick of N(0, 5e-4) moves of every object and a
+    random subset of querying objects.  ``map_fn`` may be a process pool's map."""
+    from functools import partial
+    return list(map_fn(partial(serving_world, seed=seed, n_worlds=n_worlds, **kw),
+                       range(n_worlds)))
+
+
 def many_worlds(n_worlds: int = 256, seed: int = 0, n_lo: int = 1_000, n_hi: int = 200_000,
                 ks=(4, 8, 16, 32), ticks: int = 2, sigma: float = 1e-3,
                 query_frac=(1.0, 1.0)) -> list:

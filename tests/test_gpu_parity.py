@@ -95,6 +95,14 @@ def test_uniform_1m_k16_full_size_sampled():
     run_and_compare(w, k_max=16, sample=20000, what="1M uniform k=16")
 
 
+@pytest.mark.slow
+def test_uniform_1m_k16_one_tick_every_row():
+    # the benchmark workload's first tick, every one of its 1M rows against the
+    # oracle (about a minute and a half of brute force on 16 host cores)
+    w = synth.plain_uniform_moving(n=1_000_000, k=16, ticks=1, seed=0)
+    run_and_compare(w, k_max=16, what="1M uniform k=16, every row")
+
+
 def test_clustered_4m_k32_full_size_sampled():
     w = synth.skewed_moving(n=4_000_000, k=32, ticks=2, seed=0)
     run_and_compare(w, k_max=32, sample=8000, what="4M clustered k=32")

@@ -1,11 +1,12 @@
 """Serving loop (GPU): every request's rows are the same whether it runs alone
 or mixed with other worlds' requests on several streams under a device-memory
-budget that forces scratch evictions, and equal to plain knn_tick rows."""
+budget that forces scratch evictions, equal to plain knn_tick rows, and equal
+to the CPU oracle (sampled rows of every request)."""
 import numpy as np
 import pytest
 
 from paper_1412_6170_gb300 import knnq, synth
-from tests.gpu_util import to_dev, torch_dev
+from tests.gpu_util import assert_rows_equal, oracle_rows, sample_rows, to_dev, torch_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -30,7 +31,17 @@ def make_requests(ws, ticks):
     return order
 
 
-def run_server(ws, order, n_slots, budget, torch, dev):
+def check_against_oracle(ws, order, res, count=200):
+    """Every request of a world tick sets all positions, so a request's rows depend
+    only on its own tick: sampled rows of each against the oracle."""
+    for j, ((i, ti), (ids, d2)) in enumerate(zip(order, res)):
+        t = ws[i].ticks[ti]
+        rows = sample_rows(t.q_id.shape[0], count, seed=j)
+        rid, rd2 = oracle_rows(t.upd_x, t.upd_y, t, rows, k=ws[i].k)
+        assert_rows_equal(ids, d2, rid, rd2, rows, what=f"request {j} (world {i}, tick {ti})")
+
+
+def run_server(ws, order, n_slots, budget, torch, dev, k_max=32):
     srv = knnq.knn_server_create(n_slots, budget)
     keep = []
     try:
@@ -38,7 +49,7 @@ def run_server(ws, order, n_slots, budget, torch, dev):
         for w in ws:
             x, y = to_dev(w.x0), to_dev(w.y0)
             keep += [x, y]
-            d = knnq.knn_world_desc(0.0, 0.0, 1.0, 0, 0, 32, w.n)
+            d = knnq.knn_world_desc(0.0, 0.0, 1.0, 0, 0, k_max, w.n)
             idx.append(knnq.knn_server_add_world(srv, d, x.data_ptr(), y.data_ptr(), w.n))
         outs, rids = [], []
         for i, ti in order:
@@ -90,6 +101,26 @@ def test_alone_and_mixed_give_identical_rows():
     for (i, ti), (mi, md) in zip(order, mixed):
         pi, pd = plain[(i, ti)]
         assert np.array_equal(pi, mi) and np.array_equal(pd.view(np.uint32), md.view(np.uint32))
+    # and the oracle, request by request
+    check_against_oracle(ws, order, mixed)
+
+
+def test_serving_mix_like_the_serving_workload_matches_oracle():
+    # clustered worlds of uneven size, k up to 64, 10-100 % of the objects
+    # querying, a budget of a third of the worlds' total scratch: admission
+    # evicts and re-admits, and every request's sampled rows equal the oracle
+    torch, dev = torch_dev()
+    ws = [synth.serving_world(i, seed=3, n_worlds=10, n_lo=5000, n_hi=120000) for i in range(10)]
+    order = make_requests(ws, 1) * 2  # every world twice (the same tick again)
+    order = [order[j] for j in np.random.default_rng(5).permutation(len(order))]
+    _, _, st_a = run_server(ws, order[:len(ws)], n_slots=2, budget=0, torch=torch, dev=dev,
+                            k_max=64)
+    budget = max(int(1.5 * st_a["largest_world_scratch"]), st_a["scratch_bytes"] // 3)
+    res, lat, st = run_server(ws, order, n_slots=4, budget=budget, torch=torch, dev=dev,
+                              k_max=64)
+    assert st["completed"] == len(order) and st["evictions"] > 0
+    assert all(v > 0 for v in lat)
+    check_against_oracle(ws, order, res)
 
 
 def test_world_that_can_never_fit_is_refused():
