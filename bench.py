@@ -725,7 +725,7 @@ def batched_vs_plain(dev, n_worlds=256, seed=0, iters=5):
     t0 = time.perf_counter()
     chosen = {}
     for w, d, wb in zip(wl, data, worlds_b):
-        c = wb.autotune(w.k, d["q"], trials=1)
+        c = wb.autotune(w.k, d["q"], trials=3)
         key = f"expansion {c['expansion']}"
         chosen[key] = chosen.get(key, 0) + 1
     tune_s = time.perf_counter() - t0

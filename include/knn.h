@@ -283,8 +283,7 @@ knn_status knn_brute_force(const float *x_dev, const float *y_dev, int64_t n,
  *   the paper's multi-pass form (Section 4.2: first iteration on the query's
  *   own cell, then alternating left/right Morton sub-visits, one cell per
  *   iteration; k <= 64), an ablation with the same rows, never recorded in a
- *   tick graph.  The automatic choice is 4 for k <= 16, 1 for k <= 32 and 2
- *   above.
+ *   tick graph.  The automatic choice is 4 for k <= 32 and 2 above.
  * Any field set to 0 keeps (or restores) the automatic choice. */
 typedef struct {
     int32_t leaf_capacity;
@@ -300,7 +299,9 @@ knn_status knn_world_set_tuning(knn_world w, const knn_tuning *t);
  * query: a lane in packets or a warp per query; candidates staged along the
  * walk or gathered at once), with the given queries (device arrays as for
  * knn_tick; the output arrays receive the rows, identical for every setting),
- * keeps the fastest in the world and writes it to *chosen (may be NULL).
+ * keeps the fastest in the world and writes it to *chosen (may be NULL).  Each
+ * setting is timed as a recorded CUDA graph of `trials` ticks (device time),
+ * and the automatic setting stays unless another is at least 3 % faster.
  * Synchronizes `stream`.  The world's positions are unchanged. */
 knn_status knn_world_autotune(knn_world w, const int32_t *q_id_dev, const float *q_x_dev,
                               const float *q_y_dev, int64_t n_q, int32_t k,

@@ -200,25 +200,61 @@ extern "C" knn_status knn_world_autotune(knn_world h, const int32_t *q_id_dev,
             }
         }
     }
+    // Each setting is timed as a recorded graph of `trials` ticks (device time,
+    // as the ticks run inside a batch or a replayed tick graph; direct launches
+    // would time the host's launch gaps of small worlds instead).
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    float best = 1e30f;
-    knn_tuning best_t = cand.empty() ? automatic : cand[0];
-    for (const knn_tuning &t : cand) {
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        w.tuning = saved;
+        return bad(KNN_ERR_CUDA, "knn_world_autotune: stream creation failed");
+    }
+    auto time_setting = [&](const knn_tuning &t, float *ms) -> bool {
         w.tuning = t;
-        knnq::enqueue_tick(w, a, s, false);  // warm
-        cudaEventRecord(e0, s);
-        for (int r = 0; r < trials; ++r) knnq::enqueue_tick(w, a, s, false);
-        cudaEventRecord(e1, s);
-        if (cudaEventSynchronize(e1) != cudaSuccess) {
-            w.tuning = saved;
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            return bad(KNN_ERR_CUDA, "knn_world_autotune: a trial tick failed");
-        }
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return false;
+        for (int r = 0; r < trials; ++r) knnq::enqueue_tick(w, a, cs, false);
+        if (cudaStreamEndCapture(cs, &graph) != cudaSuccess) return false;
+        bool ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+        cudaGraphDestroy(graph);
+        ok = ok && cudaGraphLaunch(exec, s) == cudaSuccess;  // warm
+        ok = ok && cudaEventRecord(e0, s) == cudaSuccess;
+        ok = ok && cudaGraphLaunch(exec, s) == cudaSuccess;
+        ok = ok && cudaEventRecord(e1, s) == cudaSuccess;
+        ok = ok && cudaEventSynchronize(e1) == cudaSuccess;
+        if (ok) cudaEventElapsedTime(ms, e0, e1);
+        if (exec) cudaGraphExecDestroy(exec);
+        return ok;
+    };
+    auto finish = [&](knn_status st) {
+        cudaStreamDestroy(cs);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        // the timed graphs ran on s, the last one with the last plan captured
+        w.last_stream = s;
+        return st;
+    };
+    float auto_ms = 0.f;
+    if (!time_setting(automatic, &auto_ms)) {
+        w.tuning = saved;
+        cudaGetLastError();
+        return finish(bad(KNN_ERR_CUDA, "knn_world_autotune: a trial tick failed"));
+    }
+    float best = auto_ms;
+    knn_tuning best_t = automatic;
+    for (const knn_tuning &t : cand) {
         float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
+        if (!time_setting(t, &ms)) {
+            w.tuning = saved;
+            cudaGetLastError();
+            return finish(bad(KNN_ERR_CUDA, "knn_world_autotune: a trial tick failed"));
+        }
         if (ms < best) {
             best = ms;
             best_t = t;
@@ -233,27 +269,20 @@ extern "C" knn_status knn_world_autotune(knn_world h, const int32_t *q_id_dev,
     for (int f : forms) {
         knn_tuning t = base_t;
         t.expansion = f;
-        w.tuning = t;
-        knnq::enqueue_tick(w, a, s, false);  // warm
-        cudaEventRecord(e0, s);
-        for (int r = 0; r < trials; ++r) knnq::enqueue_tick(w, a, s, false);
-        cudaEventRecord(e1, s);
-        if (cudaEventSynchronize(e1) != cudaSuccess) {
-            w.tuning = saved;
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            return bad(KNN_ERR_CUDA, "knn_world_autotune: a trial tick failed");
-        }
         float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
+        if (!time_setting(t, &ms)) {
+            w.tuning = saved;
+            cudaGetLastError();
+            return finish(bad(KNN_ERR_CUDA, "knn_world_autotune: a trial tick failed"));
+        }
         if (ms < best) {
             best = ms;
             best_t = t;
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    // keep the automatic setting unless another one is clearly (3 %) faster
+    if (!(best < 0.97f * auto_ms)) best_t = automatic;
     w.tuning = best_t;
     if (chosen) *chosen = best_t;
-    return KNN_OK;
+    return finish(KNN_OK);
 }

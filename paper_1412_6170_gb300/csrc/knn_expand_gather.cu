@@ -85,26 +85,14 @@ struct GatherSmem {
 
 template <int KC>
 struct GLane {
-    unsigned long long lst[KC];  // ascending by d^2; slots below KC - k hold 0
+    unsigned long long lst[KC];  // ascending (d^2, id) keys; slots below KC - k hold 0
     float thr;                   // d^2 bound of what may still enter the list
     int count;                   // buffered candidates
-    uint32_t dropped;            // smallest d^2 bits a merge pushed out of the list
 };
-
-// Compare-exchange on the d^2 word alone (the high half of a key): one 32-bit
-// compare instead of a 64-bit one.  Keys of equal d^2 keep an arbitrary order;
-// such ties are detected at the end of a pass (gtie) and the packet is then
-// handed to the packet walk, which orders by the full (d^2, id) key.
-__device__ __forceinline__ void cmpx_hi(unsigned long long &x, unsigned long long &y) {
-    const bool s = (uint32_t)(y >> 32) < (uint32_t)(x >> 32);
-    const unsigned long long lo = s ? y : x;
-    y = s ? x : y;
-    x = lo;
-}
 
 // Merge the newest kBatch buffered candidates (or all, if fewer) into the list
 // (the batch sorted by a network, then the KC smallest of list and batch by a
-// bitonic merge), recording the smallest d^2 pushed out; the issuer's own key
+// bitonic merge, on the full 64-bit (d^2, id) keys); the issuer's own key
 // (id + 1 == self) never enters it.
 template <int KC>
 __device__ __forceinline__ void gmerge(GLane<KC> &L, GatherSmem<KC> &sm, int lane, uint32_t self) {
@@ -115,46 +103,10 @@ __device__ __forceinline__ void gmerge(GLane<KC> &L, GatherSmem<KC> &sm, int lan
         const unsigned long long v = base + t < L.count ? sm.buf[base + t][lane] : kPad;
         b[t] = (uint32_t)v == self ? kPad : v;
     }
-    cmpx_hi(b[0], b[2]); cmpx_hi(b[1], b[3]); cmpx_hi(b[4], b[6]); cmpx_hi(b[5], b[7]);
-    cmpx_hi(b[0], b[4]); cmpx_hi(b[1], b[5]); cmpx_hi(b[2], b[6]); cmpx_hi(b[3], b[7]);
-    cmpx_hi(b[0], b[1]); cmpx_hi(b[2], b[3]); cmpx_hi(b[4], b[5]); cmpx_hi(b[6], b[7]);
-    cmpx_hi(b[2], b[4]); cmpx_hi(b[3], b[5]);
-    cmpx_hi(b[1], b[4]); cmpx_hi(b[3], b[6]);
-    cmpx_hi(b[1], b[2]); cmpx_hi(b[3], b[4]); cmpx_hi(b[5], b[6]);
-    // c_i = min(a_i, b_{KC-1-i}) is bitonic and holds the KC smallest; the
-    // larger of each pair leaves the list
-    uint32_t drop = L.dropped;
-    if (KC < kBatch) drop = min(drop, (uint32_t)(b[KC] >> 32));
-#pragma unroll
-    for (int i = (KC > kBatch ? KC - kBatch : 0); i < KC; ++i) {
-        const unsigned long long v = b[KC - 1 - i];
-        const uint32_t vh = (uint32_t)(v >> 32), ah = (uint32_t)(L.lst[i] >> 32);
-        const bool sv = vh < ah;
-        drop = min(drop, sv ? ah : vh);
-        L.lst[i] = sv ? v : L.lst[i];
-    }
-    L.dropped = drop;
-#pragma unroll
-    for (int span = KC / 2; span >= 1; span >>= 1) {
-#pragma unroll
-        for (int i = 0; i < KC; ++i)
-            if ((i & span) == 0) cmpx_hi(L.lst[i], L.lst[i + span]);
-    }
+    sort8(b);
+    merge_batch<KC>(L.lst, b);
     L.count = base;
     L.thr = fminf(L.thr, __uint_as_float((uint32_t)(L.lst[KC - 1] >> 32)));
-}
-
-// After the last merge of a pass: could the (d^2, id) order differ from the
-// d^2-only order the networks used?  Only when two listed keys (or the last
-// leading 0 and the first key) share a d^2, or a key pushed out shares the
-// k-th d^2.
-template <int KC>
-__device__ __forceinline__ bool gtie(const GLane<KC> &L, int kq) {
-    bool tie = L.dropped == (uint32_t)(L.lst[KC - 1] >> 32);
-#pragma unroll
-    for (int i = 0; i + 1 < KC; ++i)
-        if (i + 1 >= KC - kq) tie |= (uint32_t)(L.lst[i] >> 32) == (uint32_t)(L.lst[i + 1] >> 32);
-    return tie;
 }
 
 // Two binary32 operations at once (sm_100 packed pairs): each half is rounded
@@ -356,7 +308,6 @@ __global__ void __launch_bounds__(kGatherWarps * 32, GatherShape<KC>::kMinBlocks
         for (int i = 0; i < KC; ++i) Ln.lst[i] = i < KC - kq ? 0ull : kPad;
         Ln.thr = active && kq > 0 ? spec_q : -kInf;
         Ln.count = 0;
-        Ln.dropped = 0xFFFFFFFFu;
         bool hand_back = __any_sync(kFull, active && !(spec < kInf));
         const int ccx = cell_g(0.5f * (bx0 + bx1), g.x0, g.scale_g, g.G);
         const int ccy = cell_g(0.5f * (by0 + by1), g.y0, g.scale_g, g.G);
@@ -602,11 +553,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32, GatherShape<KC>::kMinBlocks
             // expected count then at least doubles past k); the others take no
             // part
             const bool redo = active && kq > 0 && Ln.lst[KC - 1] == kPad;
-            if (!__any_sync(kFull, redo)) {
-                // a d^2 tie that the (d^2, id) order could resolve otherwise
-                if (__any_sync(kFull, active && kq > 0 && gtie<KC>(Ln, kq))) hand_back = true;
-                break;
-            }
+            if (!__any_sync(kFull, redo)) break;
             if (attempt >= 2) {
                 hand_back = true;
                 break;
@@ -620,7 +567,6 @@ __global__ void __launch_bounds__(kGatherWarps * 32, GatherShape<KC>::kMinBlocks
                 for (int i = 0; i < KC; ++i) Ln.lst[i] = i < KC - kq ? 0ull : kPad;
                 spec_q *= grow;
                 Ln.thr = spec_q;
-                Ln.dropped = 0xFFFFFFFFu;
             } else {
                 Ln.thr = -kInf;
             }
