@@ -79,7 +79,11 @@ typedef struct {
 } knn_world_desc;
 
 /* Create a world of n objects (ids 0..n-1) at the positions x_dev[i], y_dev[i]
- * (device arrays of n floats, copied; all must be finite).  Allocates every
+ * (device arrays of n floats, copied; all must be finite): the set O of
+ * moving objects with their last known positions (Section 2.1, the moving
+ * object model, and Section 2.2: positions stay valid until an update
+ * arrives).  No index is built here: the PR quadtree is rebuilt every tick
+ * (Section 4.1.1), so a world is just positions plus scratch.  Allocates every
  * device buffer the ticks need (sized from n, k_max, max_queries), so ticks
  * never allocate.  May synchronize `stream`.  Returns KNN_ERR_INVALID for a
  * bad description, n outside [1, 2^30] or a non-finite position. */
@@ -235,12 +239,18 @@ knn_status knn_server_destroy(knn_server s);
 
 /* Waits for the world's last tick and reports device-detected problems since
  * the previous call: KNN_ERR_TIMEOUT, then KNN_ERR_DEVICE_INPUT (skipped
- * updates, non-finite coordinates, invalid queries), else KNN_OK.  Clears the
+ * updates, non-finite coordinates, invalid queries), else KNN_OK.  Section
+ * 2.2 keeps, per object, only the most recent valid update of a batch; an
+ * update or query the device finds invalid is dropped from the batch (the
+ * query's row is padding) and reported here instead of failing the tick.  Clears the
  * recorded bits.  If `bits_out` is non-NULL it receives the raw bit set
- * (1 = bad update id, 2 = non-finite update, 4 = invalid query, 8 = timeout). */
+ * (1 = bad update id, 2 = non-finite update, 4 = invalid query, 8 = timeout,
+ * 16 = a failed bounds check of a debug build: KNN_ERR_CUDA). */
 knn_status knn_tick_status(knn_world w, uint32_t *bits_out);
 
-/* Release every device buffer of the world (synchronizes its device). */
+/* Release every device buffer of the world (synchronizes its device): the end
+ * of the iterated batch processing of Section 2.3 for this set of objects.
+ * The handle is invalid afterwards; NULL returns KNN_ERR_INVALID. */
 knn_status knn_world_destroy(knn_world w);
 
 /* Thread-local description of the last error returned on this thread. */
@@ -334,6 +344,20 @@ knn_status knn_world_positions(knn_world w, float *x_dev, float *y_dev, void *st
  * clears it), and the next tick runs normally.  Call between ticks of this
  * world.  NULL world: KNN_ERR_INVALID. */
 knn_status knn_world_test_wait_timeout(knn_world w, void *stream);
+
+/* Debug builds (the library compiled with -DKNN_DEBUG: paper_1412_6170_gb300/
+ * build.py, build_debug()).  No passage of the paper corresponds; this is the
+ * library's own bounds checking.  In a debug build the kernels check their
+ * index arithmetic at the main array accesses (objects, leaves, the gathered
+ * list, candidate buffers, row writes, radix scatters); an index out of range
+ * raises error bit 16 and the access is skipped -- nothing traps -- and
+ * knn_tick_status then returns KNN_ERR_CUDA.  knn_debug_build returns KNN_OK
+ * in a debug build, else KNN_ERR_INVALID.  knn_world_test_bounds_check
+ * enqueues one check that fails on purpose (an index one past the world's
+ * objects; the access is skipped), so that knn_tick_status reports bit 16;
+ * KNN_ERR_INVALID in a regular build. */
+knn_status knn_debug_build(void);
+knn_status knn_world_test_bounds_check(knn_world w, void *stream);
 
 /* Number of CUDA kernels this world's ticks have launched so far (host-side
  * count; memsets and copies are not kernels and are not counted). */

@@ -2,6 +2,9 @@
 
 Each translation unit compiles in its own nvcc process (in parallel), then the
 objects are linked into one shared library next to this file under ``_build/``.
+``build_debug()`` builds the same sources with ``-DKNN_DEBUG`` (device bounds
+checks that record a failure instead of trapping) under ``_build_debug/``; the
+binding loads it when the environment variable KNNQ_DEBUG is 1.
 """
 from __future__ import annotations
 
@@ -16,6 +19,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libknnq.so")
+DEBUG_DIR = os.path.join(HERE, "_build_debug")
+DEBUG_LIB = os.path.join(DEBUG_DIR, "libknnq.so")
 SOURCES = ["knn_index.cu", "knn_expand.cu", "knn_expand_gather.cu", "knn_expand_wide.cu",
            "knn_expand_iter.cu",
            "knn_brute.cu", "knn_capi.cu", "knn_static.cu", "knn_batch.cu", "knn_server.cu"]
@@ -37,21 +42,22 @@ def _deps():
             + [os.path.join(ROOT, "include", "knn.h"), os.path.abspath(__file__)])
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra=(), out_dir: str = OUT_DIR) -> str:
+    lib = os.path.join(out_dir, "libknnq.so")
+    if not force and up_to_date(lib):
+        return lib
+    os.makedirs(out_dir, exist_ok=True)
     cc = nvcc()
 
     def compile_one(src):
-        obj = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
+        obj = os.path.join(out_dir, src.replace(".cu", ".o"))
         cmd = [cc, *ARCH, *NVCC_FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
@@ -65,13 +71,18 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     for _, err in results:
         if verbose and err.strip():
             print(err, flush=True)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [cc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *[o for o, _ in results]]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
+
+
+def build_debug(force: bool = False, verbose: bool = False) -> str:
+    """The library with device bounds checks (-DKNN_DEBUG) under _build_debug/."""
+    return build(force=force, verbose=verbose, extra=["-DKNN_DEBUG"], out_dir=DEBUG_DIR)
 
 
 if __name__ == "__main__":

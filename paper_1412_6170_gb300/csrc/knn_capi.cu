@@ -799,6 +799,9 @@ knn_status knn_tick_status(knn_world h, uint32_t *bits_out) {
     if (e != cudaSuccess) return cuda_fail(e, "knn_tick_status");
     if (bits_out) *bits_out = bits;
     if (bits & 8u) return fail(KNN_ERR_TIMEOUT, "a bounded device wait ran out");
+    if (bits & 16u)
+        return fail(KNN_ERR_CUDA, "a device bounds check of the debug build failed (bits 0x%x)",
+                    bits);
     if (bits) return fail(KNN_ERR_DEVICE_INPUT, "device skipped invalid input (bits 0x%x)", bits);
     return KNN_OK;
 }
@@ -838,6 +841,30 @@ knn_status knn_world_positions(knn_world h, float *x_dev, float *y_dev, void *st
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "knn_world_positions");
     return KNN_OK;
+}
+
+knn_status knn_debug_build(void) {
+#ifdef KNN_DEBUG
+    return KNN_OK;
+#else
+    return fail(KNN_ERR_INVALID, "not a debug build (compiled without KNN_DEBUG)");
+#endif
+}
+
+knn_status knn_world_test_bounds_check(knn_world h, void *stream) {
+    if (!h) return fail(KNN_ERR_INVALID, "knn_world_test_bounds_check: NULL world");
+#ifndef KNN_DEBUG
+    return fail(KNN_ERR_INVALID, "knn_world_test_bounds_check: not a debug build");
+#else
+    World &w = h->w;
+    cudaSetDevice(w.device);
+    cudaStream_t s = (cudaStream_t)stream;
+    knnq::launch_bounds_check_probe(w, s);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "knn_world_test_bounds_check");
+    w.last_stream = s;
+    return KNN_OK;
+#endif
 }
 
 knn_status knn_world_test_wait_timeout(knn_world h, void *stream) {

@@ -14,7 +14,24 @@ enum : uint32_t {
     kErrNonFiniteUpdate = 1u << 1,
     kErrBadQuery = 1u << 2,
     kErrTimeout = 1u << 3,
+    kErrDebugBounds = 1u << 4,  // a bounds check of a KNN_DEBUG build failed
 };
+
+// Device bounds checks of a debug build (compiled with -DKNN_DEBUG): an index
+// outside [lo, hi) raises kErrDebugBounds in the error word and the access is
+// skipped; nothing traps.  In a regular build the check is the constant true
+// and costs nothing.  Use as: if (KNN_IN_BOUNDS(i, 0, n, err)) { access i }.
+#ifdef KNN_DEBUG
+__device__ __forceinline__ bool knn_in_bounds(int64_t i, int64_t lo, int64_t hi, uint32_t *err) {
+    if (i >= lo && i < hi) return true;
+    atomicOr(err, kErrDebugBounds);
+    return false;
+}
+#define KNN_IN_BOUNDS(i, lo, hi, err) \
+    knnq::knn_in_bounds((int64_t)(i), (int64_t)(lo), (int64_t)(hi), (err))
+#else
+#define KNN_IN_BOUNDS(i, lo, hi, err) true
+#endif
 
 // Bounded spins: a wait gives up after this many polls (each poll after the
 // first few sleeps ~0.1-1 us), records kErrTimeout and continues; once the

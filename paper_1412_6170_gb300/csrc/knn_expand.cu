@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(kWarps * 32, Shape<KC>::kMinBlocks) k_expand(c
             if (cur < staged || cur >= staged_end) {
                 const int32_t cnt = end - cur < 32 ? end - cur : 32;
                 __syncwarp();
-                if (lane < cnt)
+                if (lane < cnt && KNN_IN_BOUNDS(cur + lane, 0, g.n, g.err))
                     sm.obj[lane] = make_float4(g.xs[cur + lane], g.ys[cur + lane],
                                                __int_as_float(g.sid[cur + lane] + 1), 0.f);
                 __syncwarp();

@@ -368,11 +368,13 @@ __global__ void __launch_bounds__(kGatherWarps * 32, GatherShape<KC>::kMinBlocks
                             const uint32_t d1 = __float_as_uint(__fadd_rn(
                                 __uint_as_float((uint32_t)(xx >> 32)),
                                 __uint_as_float((uint32_t)(yy >> 32))));
-                            if (__uint_as_float(d0) <= thr) {
+                            if (__uint_as_float(d0) <= thr &&
+                                KNN_IN_BOUNDS(Ln.count, 0, GatherShape<KC>::kCap, g.err)) {
                                 sm.buf[Ln.count][lane] = ((unsigned long long)d0 << 32) | (uint32_t)id.x;
                                 ++Ln.count;
                             }
-                            if (__uint_as_float(d1) <= thr) {
+                            if (__uint_as_float(d1) <= thr &&
+                                KNN_IN_BOUNDS(Ln.count, 0, GatherShape<KC>::kCap, g.err)) {
                                 sm.buf[Ln.count][lane] = ((unsigned long long)d1 << 32) | (uint32_t)id.y;
                                 ++Ln.count;
                             }
@@ -415,14 +417,16 @@ __global__ void __launch_bounds__(kGatherWarps * 32, GatherShape<KC>::kMinBlocks
                         const int32_t j0 = o0 + lane, j1 = o0 + 32 + lane;
                         if (j0 < nobj) {
                             const int r = obefore + __popc(win0 & lanemask_le) - 1;
-                            const int32_t i = sm.oseg_base[r] + (j0 - sm.oseg_start[r]);
+                            int32_t i = sm.oseg_base[r] + (j0 - sm.oseg_start[r]);
+                            if (!KNN_IN_BOUNDS(i, 0, g.n, g.err)) i = 0;
                             x0 = g.xs[i];
                             y0 = g.ys[i];
                             id0 = g.sid[i] + 1;
                         }
                         if (j1 < nobj) {
                             const int r = obefore + __popc(win0) + __popc(win1 & lanemask_le) - 1;
-                            const int32_t i = sm.oseg_base[r] + (j1 - sm.oseg_start[r]);
+                            int32_t i = sm.oseg_base[r] + (j1 - sm.oseg_start[r]);
+                            if (!KNN_IN_BOUNDS(i, 0, g.n, g.err)) i = 0;
                             x1 = g.xs[i];
                             y1 = g.ys[i];
                             id1 = g.sid[i] + 1;
@@ -432,13 +436,14 @@ __global__ void __launch_bounds__(kGatherWarps * 32, GatherShape<KC>::kMinBlocks
                         obefore += __popc(win0) + __popc(win1);
                         const unsigned km0 = __ballot_sync(kFull, keep0);
                         const unsigned km1 = __ballot_sync(kFull, keep1);
-                        if (keep0) {
+                        if (keep0 && KNN_IN_BOUNDS(kept + __popc(km0 & lanemask_lt), 0, kObjCap, g.err)) {
                             const int pos = kept + __popc(km0 & lanemask_lt);
                             sxy[4 * (pos >> 1) + (pos & 1)] = x0;
                             sxy[4 * (pos >> 1) + 2 + (pos & 1)] = y0;
                             sm.idp1[pos] = id0;
                         }
-                        if (keep1) {
+                        if (keep1 && KNN_IN_BOUNDS(kept + __popc(km0) + __popc(km1 & lanemask_lt), 0,
+                                                   kObjCap, g.err)) {
                             const int pos = kept + __popc(km0) + __popc(km1 & lanemask_lt);
                             sxy[4 * (pos >> 1) + (pos & 1)] = x1;
                             sxy[4 * (pos >> 1) + 2 + (pos & 1)] = y1;
@@ -456,7 +461,8 @@ __global__ void __launch_bounds__(kGatherWarps * 32, GatherShape<KC>::kMinBlocks
                         int32_t ostart = 0, no = 0;
                         if (l0 + lane < nleaves) {
                             const int r = lbefore + __popc(win & lanemask_le) - 1;
-                            const int32_t b = sm.lseg_base[r] + (l0 + lane - sm.lseg_start[r]);
+                            int32_t b = sm.lseg_base[r] + (l0 + lane - sm.lseg_start[r]);
+                            if (!KNN_IN_BOUNDS(b, 0, m, g.err)) b = 0;
                             const int2 rg = g.brange[b];
                             if (rg.y > rg.x) {
                                 const float4 bb = g.baabb[b];
@@ -615,7 +621,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32, GatherShape<KC>::kMinBlocks
                         const int v = base + lane;
                         const int row = v / PR, c = (v % PR) * 4;
                         const int32_t o = row < ql ? sm.orig[row] : -1;
-                        if (o >= 0)
+                        if (o >= 0 && KNN_IN_BOUNDS(o, 0, g.n_q, g.err))
                             *reinterpret_cast<uint4 *>(out + (int64_t)o * KC + c) =
                                 *reinterpret_cast<const uint4 *>(rows + row * S + c);
                     }
@@ -626,7 +632,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32, GatherShape<KC>::kMinBlocks
                             const int row = v / per_row;
                             const int c = (v - row * per_row) * vw;
                             const int32_t o = sm.orig[row];
-                            if (o >= 0) {
+                            if (o >= 0 && KNN_IN_BOUNDS(o, 0, g.n_q, g.err)) {
                                 uint32_t *dst = out + (int64_t)o * k + c;
                                 if (vw == 4) {
                                     *reinterpret_cast<uint4 *>(dst) =

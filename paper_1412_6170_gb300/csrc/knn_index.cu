@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
         const uint32_t key = s_keys[i];
         const uint32_t dd = (key >> shift) & 255u;
         const uint32_t dst = s_gbase[dd] + (uint32_t)(i - (int)s_texcl[dd]);
-        if (dst < (uint64_t)n) {  // always true unless a look-back timed out
+        if (dst < (uint64_t)n && KNN_IN_BOUNDS(i, 0, kSortTile, err)) {  // (a look-back timeout)
             kout[dst] = key;
             vout[dst] = s_vals[i];
         }
@@ -1243,6 +1243,20 @@ __global__ void k_export_leaves(const int32_t *__restrict__ bstart,
 // timeout bit and the abort flag are raised and the kernel returns.
 __global__ void k_wait_runs_out(uint64_t *status, uint32_t *err) {
     lookback_warp_resolve(status, 1u, 0x3FFFFFFFu, 0u, err);
+}
+
+// Debug builds: evaluates one bounds check that fails (index n of an array of
+// n objects); the check records the failure and the access is skipped.
+// (A regular build compiles an empty body: there the check is the constant true.)
+__global__ void k_bounds_check_probe(int64_t n, const float *xs, float *sink, uint32_t *err) {
+#ifdef KNN_DEBUG
+    if (threadIdx.x == 0 && blockIdx.x == 0 && KNN_IN_BOUNDS(n, 0, n, err)) sink[0] = xs[n];
+#endif
+}
+
+void launch_bounds_check_probe(World &w, cudaStream_t s) {
+    k_bounds_check_probe<<<1, 32, 0, s>>>(w.n, w.xs, w.xs, w.err);
+    ++w.launches;
 }
 
 void launch_wait_runs_out(World &w, cudaStream_t s) {

@@ -205,6 +205,8 @@ void launch_packets(World &w, const Plan &p, int64_t n_q, cudaStream_t s);
 void launch_query_cells(World &w, const Plan &p, int64_t n_q, cudaStream_t s);
 // One bounded device wait that nothing satisfies (failure-detection check).
 void launch_wait_runs_out(World &w, cudaStream_t s);
+// One failing bounds check (debug builds only; the access is skipped).
+void launch_bounds_check_probe(World &w, cudaStream_t s);
 void launch_export_leaves(World &w, int64_t m, int32_t *level, uint32_t *z, int32_t *start,
                           int32_t *count, cudaStream_t s);
 

@@ -15,7 +15,9 @@ import re
 from typing import Optional
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libknnq.so")
+# KNNQ_DEBUG=1 loads the build with device bounds checks (build.build_debug())
+LIB_PATH = os.path.join(HERE, "_build_debug" if os.environ.get("KNNQ_DEBUG") == "1" else "_build",
+                        "libknnq.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "knn.h")
 
 KNN_OK = 0
@@ -30,6 +32,7 @@ ERR_BAD_UPDATE_ID = 1
 ERR_NONFINITE_UPDATE = 2
 ERR_BAD_QUERY = 4
 ERR_TIMEOUT = 8
+ERR_DEBUG_BOUNDS = 16
 
 
 class KnnError(RuntimeError):
@@ -98,6 +101,8 @@ _SIGNATURES = {
     "knn_world_set_index_reuse": ([_vp, _i32, ctypes.c_float], ctypes.c_int),
     "knn_world_index_info": ([_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)], ctypes.c_int),
     "knn_world_expand_info": ([_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)], ctypes.c_int),
+    "knn_debug_build": ([], ctypes.c_int),
+    "knn_world_test_bounds_check": ([_vp, _vp], ctypes.c_int),
     "knn_world_record_tick": ([_vp, ctypes.POINTER(knn_tick_args)], ctypes.c_int),
     "knn_world_stage_times": ([_vp, ctypes.POINTER(ctypes.c_float), _i32], ctypes.c_int),
     "knn_stage_name": ([_i32], ctypes.c_char_p),
@@ -274,6 +279,15 @@ def knn_world_expand_info(w: int) -> dict:
     gathered, back = _i64(0), _i64(0)
     _check(lib().knn_world_expand_info(w, ctypes.byref(gathered), ctypes.byref(back)))
     return {"gathered": int(gathered.value), "handed_back": int(back.value)}
+
+
+def knn_debug_build() -> bool:
+    """True when the loaded library was built with device bounds checks."""
+    return lib().knn_debug_build() == KNN_OK
+
+
+def knn_world_test_bounds_check(w: int, stream: int = 0) -> None:
+    _check(lib().knn_world_test_bounds_check(w, stream))
 
 
 def knn_world_record_tick(w: int, args: knn_tick_args) -> None:
