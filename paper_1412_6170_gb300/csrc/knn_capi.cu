@@ -62,15 +62,15 @@ Plan make_plan(const World &w, int64_t n_q, int k) {
     // one warp per query pays off above k = 32 (measured on 1M uniform objects:
     // k = 64 takes 2.8 ms that way against 3.5 ms in packets)
     p.iterative = w.tuning.expansion == 3 && k <= knnq::kMaxPacketK;
-    p.wide = !p.iterative && (w.tuning.expansion == 2 || (w.tuning.expansion != 1 && k > 32) ||
+    p.wide = !p.iterative && (w.tuning.expansion == 2 || (w.tuning.expansion == 0 && k > 32) ||
                               k > knnq::kMaxPacketK);
     // packets gather their search box at once (k <= 32) unless the packet walk
     // is asked for (measured on 1M uniform objects, all querying: k = 8 0.26
     // against 0.33 ms, k = 16 0.39 against 0.43 ms, k = 32 0.87 against 0.86
     // ms for the walk; 4M clustered objects, a quarter querying, k = 32: 1.53
     // against 1.58 ms)
-    p.gather = !p.iterative && !p.wide && k <= 32 &&
-               (w.tuning.expansion == 4 || w.tuning.expansion == 0);
+    p.gather = !p.iterative && !p.wide && k <= knnq::kMaxPacketK &&
+               (w.tuning.expansion == 4 || (w.tuning.expansion == 0 && k <= 32));
     p.by_id = 2 * n_q >= w.n;
     p.reuse_age = w.reuse_age;
     p.reuse_f16 = w.reuse_factor > 0.f ? (int)std::lround(w.reuse_factor * 16.f) : 0;

@@ -39,9 +39,11 @@ constexpr int kDensityCells = 64;      // cells counted around a packet for per-
 
 template <int KC>
 struct GatherShape {
-    static constexpr int kCap = 32;  // buffer slots per lane
+    // buffer slots per lane (lists of 64 need 36: the row write reuses the
+    // buffer for 32 rows of KC + 4 words)
+    static constexpr int kCap = KC <= 32 ? 32 : 36;
     static constexpr int kFlushAt = kCap - kBatch;
-    static constexpr int kMinBlocks = KC <= 16 ? 5 : 4;  // 20 or 16 warps per SM
+    static constexpr int kMinBlocks = KC <= 16 ? 5 : (KC <= 32 ? 4 : 2);  // 20, 16 or 8 warps per SM
 };
 
 struct GatherArgs {
@@ -680,6 +682,7 @@ void prepare_expand_gather(int device) {
     gather_blocks_per_sm<8>(device);
     gather_blocks_per_sm<16>(device);
     gather_blocks_per_sm<32>(device);
+    gather_blocks_per_sm<64>(device);
 }
 
 void launch_expand_gather(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t *out_ids,
@@ -725,7 +728,8 @@ void launch_expand_gather(World &w, const Plan &p, int32_t k, int64_t n_q, int32
     if (k <= 4) run_gather<4>(a, w.device, s);
     else if (k <= 8) run_gather<8>(a, w.device, s);
     else if (k <= 16) run_gather<16>(a, w.device, s);
-    else run_gather<32>(a, w.device, s);
+    else if (k <= 32) run_gather<32>(a, w.device, s);
+    else run_gather<64>(a, w.device, s);
     ++w.launches;
     // the packets handed back, through the packet walk
     launch_expand_handed_back(w, p, k, n_q, out_ids, out_d2, q_k, s);

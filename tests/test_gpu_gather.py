@@ -57,7 +57,7 @@ def test_gather_serves_the_uniform_workload():
         assert info["handed_back"] <= packets // 100, info
 
 
-@pytest.mark.parametrize("k", [1, 4, 8, 16, 32])
+@pytest.mark.parametrize("k", [1, 4, 8, 16, 32, 48, 64])
 def test_gather_clustered_subset_full(k):
     # dense hotspots with deep leaves and a sparse background; every row
     # against the oracle
