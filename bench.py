@@ -659,9 +659,10 @@ def k_sweep(dev, ks=(1, 4, 16, 32, 64, 128, 256, 512), iters=3):
 
 def batched_vs_plain(dev, n_worlds=256, seed=0, iters=5):
     """Many uneven worlds (1k-200k objects, uniform or clustered, k in {4,8,16,32}, all
-    query): one knn_batch_tick (a recorded CUDA graph) against one knn_tick per world,
-    with the automatic settings and after knn_world_autotune chose each world's; the
-    batched rows are compared with the plain ones, world by world."""
+    query): one knn_batch_tick (a recorded CUDA graph: the worlds' index stages side by
+    side, then one batched expansion grid per list size) against one knn_tick per world,
+    with the automatic settings and after knn_batch_autotune chose the settings per
+    list-size class; the batched rows are compared with the plain ones, world by world."""
     import torch
 
     from paper_1412_6170_gb300 import knnq, synth
@@ -721,14 +722,16 @@ def batched_vs_plain(dev, n_worlds=256, seed=0, iters=5):
     same_default = all(torch.equal(d["oi"], d["pi"]) and torch.equal(d["od"].view(torch.int32),
                                                                      d["pd"].view(torch.int32))
                        for d in data)
-    # autotune every batched world on its own queries, then time the batch again
+    # the batch autotuner (settings per list-size class, timed as whole batches),
+    # then the batch again
     t0 = time.perf_counter()
-    chosen = {}
-    for w, d, wb in zip(wl, data, worlds_b):
-        c = wb.autotune(w.k, d["q"], trials=3)
-        key = f"expansion {c['expansion']}"
-        chosen[key] = chosen.get(key, 0) + 1
+    tunings = knnq.knn_batch_autotune(handles, args, trials=3, stream=stream.cuda_stream)
     tune_s = time.perf_counter() - t0
+    chosen = {}
+    for w, t in zip(wl, tunings):
+        c = chosen.setdefault(f"k={w.k}", {})
+        key = f"expansion {t['expansion']} leaf_capacity {t['leaf_capacity']}"
+        c[key] = c.get(key, 0) + 1
     batch_tuned = batched_ms()
     same_tuned = all(torch.equal(d["oi"], d["pi"]) and torch.equal(d["od"].view(torch.int32),
                                                                    d["pd"].view(torch.int32))

@@ -176,13 +176,21 @@ knn_status knn_world_set_host_io(knn_world w, int32_t mode);
 /* Batch processing over many worlds (Section 2.3 per world): one tick of every
  * world in `worlds` (distinct handles on the current device), with args[i]
  * for worlds[i] exactly as knn_tick takes them; the rows are bit-identical to
- * separate knn_tick calls.  The batch is recorded into one CUDA graph (each
- * world an independent chain, spread over internal streams between a fork and
- * a join on `stream`) and launched as one graph; while the same worlds, sizes
- * and pointers come back, the recorded graph is replayed without recording.
- * Asynchronous on `stream`; a call that has to record the batch again does
- * host work proportional to the number of worlds.  Not thread-safe with other
- * batch calls on the same device. */
+ * separate knn_tick calls.  The batch is recorded into one CUDA graph: each
+ * world's index stages (updates, sort, leaves, query order, packets) form an
+ * independent chain, spread over internal streams between a fork and a join
+ * on `stream`; then the expansion (Section 4.2) runs batched: per form and
+ * list size (4, 8, 16, 32, 64) one persistent grid takes the packets of every
+ * world of that class through a device-built prefix of the worlds' packet
+ * counts, and one packet-walk grid per list size finishes the packets the
+ * gathered form handed back.  Worlds whose expansion is one warp per query
+ * (k > 32 by default) or the multi-pass ablation expand in their own chains.
+ * While the same worlds, sizes and pointers come back, the recorded graph is
+ * replayed without recording.  Asynchronous on `stream`; a call that has to
+ * record the batch again does host work proportional to the number of worlds
+ * and first waits for the last batch launched on this device to finish (its
+ * expansion table is rewritten).  Not thread-safe with other batch calls on
+ * the same device. */
 knn_status knn_batch_tick(int32_t n_worlds, const knn_world *worlds, const knn_tick_args *args,
                           void *stream);
 
@@ -317,6 +325,21 @@ knn_status knn_world_autotune(knn_world w, const int32_t *q_id_dev, const float 
                               const float *q_y_dev, int64_t n_q, int32_t k,
                               int32_t *out_ids_dev, float *out_d2_dev, int32_t trials,
                               knn_tuning *chosen, void *stream);
+
+/* Autotuner for a batch: chooses the settings of the batch's worlds by timing
+ * whole batch ticks (knn_batch_tick with args[i] but without updates, so the
+ * positions are unchanged; the output arrays receive the rows).  The worlds
+ * are grouped by list size class (k <= 4, 8, 16, 32, 64); per class, largest
+ * query count first, each expansion form (packet walk, one warp per query,
+ * gathered packets) and then half and twice the leaf capacity are tried for
+ * all worlds of the class at once, each as `trials` timed replays of the
+ * recorded batch (device time), and a change is kept only if the batch gets
+ * at least 3 % faster.  The chosen settings stay in the worlds and go to
+ * chosen[i] (n_worlds entries; may be NULL).  Synchronizes `stream`.  On an
+ * error every world keeps the setting it had. */
+knn_status knn_batch_autotune(int32_t n_worlds, const knn_world *worlds,
+                              const knn_tick_args *args, int32_t trials, knn_tuning *chosen,
+                              void *stream);
 
 /* The parameters the next tick with query count n_q and k will use. */
 knn_status knn_world_get_tuning(knn_world w, int64_t n_q, int32_t k, knn_tuning *out);

@@ -9,6 +9,7 @@
 // change records the batch again and updates the graph in place.  Every tick
 // takes its look-back epochs and update stamps from device counters, so a
 // replay is a genuine new tick.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -36,7 +37,35 @@ struct BatchGraph {
     cudaStream_t streams[kMaxStreams] = {};
     cudaEvent_t fork = nullptr, join[kMaxStreams] = {};
     int64_t nodes = 0;
+    // The batched expansion: the worlds' expansion arguments by list size
+    // class (device table, written when the batch is recorded, after the last
+    // replay that read it has finished), the prefix arrays and the tickets.
+    void *table = nullptr;
+    size_t table_bytes = 0;
+    std::vector<char> host;
+    cudaEvent_t fork2 = nullptr, join2[kMaxStreams] = {};
+    cudaEvent_t done = nullptr;  // after the last launch of the graph
+    bool pending = false;
 };
+
+// One list size class of the batched expansion, and where its parts sit in
+// the table.
+struct ExpandClass {
+    int kc = 0;
+    bool walk = false;             // worlds on the packet walk (else the gathered form)
+    std::vector<int32_t> members;  // world indices
+    size_t gather_off = 0, walk_off = 0, pfx_g_off = 0, pfx_w_off = 0, ctr_off = 0;
+};
+
+constexpr int kClasses[5] = {4, 8, 16, 32, 64};
+
+int class_of(int32_t k) {
+    for (int c = 0; c < 5; ++c)
+        if (k <= kClasses[c]) return c;
+    return 4;
+}
+
+size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 std::mutex g_mu;
 BatchGraph g_batch[64];
@@ -52,13 +81,82 @@ bool same_args(const knn_tick_args &a, const knn_tick_args &b) {
 
 knn_status ensure_streams(BatchGraph &g) {
     if (g.fork) return KNN_OK;
-    if (cudaEventCreateWithFlags(&g.fork, cudaEventDisableTiming) != cudaSuccess)
+    if (cudaEventCreateWithFlags(&g.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&g.fork2, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming) != cudaSuccess)
         return bad(KNN_ERR_CUDA, "knn_batch_tick: event creation failed");
     for (int i = 0; i < kMaxStreams; ++i) {
         if (cudaStreamCreateWithFlags(&g.streams[i], cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&g.join[i], cudaEventDisableTiming) != cudaSuccess)
+            cudaEventCreateWithFlags(&g.join[i], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&g.join2[i], cudaEventDisableTiming) != cudaSuccess)
             return bad(KNN_ERR_CUDA, "knn_batch_tick: stream creation failed");
     }
+    return KNN_OK;
+}
+
+// Lays out the batched-expansion table of the worlds whose plan is the
+// gathered form, fills its host copy and copies it to the device (growing the
+// device buffer), after the graph's last replay has finished with it.
+knn_status build_expand_table(BatchGraph &g, int32_t n_worlds, const knn_world *worlds,
+                              const knn_tick_args *args, const std::vector<knnq::Plan> &plans,
+                              std::vector<ExpandClass> &classes, std::vector<char> &batched) {
+    classes.clear();
+    batched.assign(n_worlds, 0);
+    ExpandClass by[10];  // gathered form by list size, then the packet walk by list size
+    for (int32_t i = 0; i < n_worlds; ++i) {
+        const knnq::Plan &p = plans[i];
+        if (p.wide || p.iterative || args[i].n_q <= 0) continue;
+        batched[i] = 1;
+        by[(p.gather ? 0 : 5) + class_of(args[i].k)].members.push_back(i);
+    }
+    const size_t gsz = knnq::gather_batch_entry_bytes(), wsz = knnq::walk_batch_entry_bytes();
+    size_t off = 0;
+    for (int c = 0; c < 10; ++c) {
+        ExpandClass &e = by[c];
+        if (e.members.empty()) continue;
+        const size_t n = e.members.size();
+        e.kc = kClasses[c % 5];
+        e.walk = c >= 5;
+        e.gather_off = off;
+        if (!e.walk) off = align16(off + n * gsz);
+        e.walk_off = off;
+        off = align16(off + n * wsz);
+        e.pfx_g_off = off;
+        off = align16(off + (n + 1) * sizeof(long long));
+        e.pfx_w_off = off;
+        off = align16(off + (n + 1) * sizeof(long long));
+        e.ctr_off = off;
+        off = align16(off + 2 * sizeof(unsigned long long));
+        classes.push_back(e);
+    }
+    if (classes.empty()) return KNN_OK;
+    g.host.assign(off, 0);
+    for (const ExpandClass &e : classes) {
+        for (size_t j = 0; j < e.members.size(); ++j) {
+            const int32_t i = e.members[j];
+            knnq::World &w = worlds[i]->w;
+            if (!e.walk)
+                knnq::gather_batch_entry(w, plans[i], args[i],
+                                         g.host.data() + e.gather_off + j * gsz);
+            knnq::walk_batch_entry(w, plans[i], args[i], !e.walk,
+                                   g.host.data() + e.walk_off + j * wsz);
+        }
+    }
+    if (g.pending && cudaEventSynchronize(g.done) != cudaSuccess)
+        return bad(KNN_ERR_CUDA, "knn_batch_tick: waiting for the last batch failed");
+    g.pending = false;
+    if (off > g.table_bytes) {
+        if (g.table) cudaFree(g.table);
+        g.table = nullptr;
+        g.table_bytes = 0;
+        if (cudaMalloc(&g.table, off) != cudaSuccess) {
+            cudaGetLastError();
+            return bad(KNN_ERR_OOM, "knn_batch_tick: no device memory for the expansion table");
+        }
+        g.table_bytes = off;
+    }
+    if (cudaMemcpy(g.table, g.host.data(), off, cudaMemcpyHostToDevice) != cudaSuccess)
+        return bad(KNN_ERR_CUDA, "knn_batch_tick: copying the expansion table failed");
     return KNN_OK;
 }
 
@@ -91,9 +189,12 @@ extern "C" knn_status knn_batch_tick(int32_t n_worlds, const knn_world *worlds,
 
     // Shape: the plan of every world (and whether updates run) fixes the graph's nodes.
     std::vector<int> shape;
+    std::vector<knnq::Plan> plans;
     shape.reserve(8 * n_worlds);
+    plans.reserve(n_worlds);
     for (int32_t i = 0; i < n_worlds; ++i) {
         const knnq::Plan p = knnq::plan_for(worlds[i]->w, args[i].n_q, args[i].k);
+        plans.push_back(p);
         shape.insert(shape.end(), {p.th, p.G, p.Gp, (int)p.wide, (int)p.gather,
                                    args[i].n_upd > 0, args[i].q_x_dev != nullptr,
                                    args[i].n_q > 0});
@@ -103,6 +204,13 @@ extern "C" knn_status knn_batch_tick(int32_t n_worlds, const knn_world *worlds,
         reuse = g.worlds[i] == worlds[i] && same_args(g.args[i], args[i]);
 
     if (!reuse) {
+        // a failed record below must not leave an older recording replayable
+        g.worlds.clear();
+        g.shape.clear();
+        std::vector<ExpandClass> classes;
+        std::vector<char> batched;
+        st = build_expand_table(g, n_worlds, worlds, args, plans, classes, batched);
+        if (st != KNN_OK) return st;
         cudaGraph_t graph = nullptr;
         cudaStream_t origin = g.streams[0];
         cudaError_t e = cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal);
@@ -112,12 +220,41 @@ extern "C" knn_status knn_batch_tick(int32_t n_worlds, const knn_world *worlds,
         for (int i = 1; i < ns; ++i) cudaStreamWaitEvent(g.streams[i], g.fork, 0);
         int64_t launches0 = 0, launches1 = 0;
         for (int32_t i = 0; i < n_worlds; ++i) launches0 += worlds[i]->w.launches;
+        // every world's index stages (and the expansion of the worlds that
+        // are not batched) as independent chains
         for (int32_t i = 0; i < n_worlds; ++i)
-            knnq::enqueue_tick(worlds[i]->w, args[i], g.streams[i % ns], false);
+            knnq::enqueue_tick(worlds[i]->w, args[i], g.streams[i % ns], false, !batched[i]);
         for (int32_t i = 0; i < n_worlds; ++i) launches1 += worlds[i]->w.launches;
         for (int i = 1; i < ns; ++i) {
             cudaEventRecord(g.join[i], g.streams[i]);
             cudaStreamWaitEvent(origin, g.join[i], 0);
+        }
+        // then per list size one gathered-expansion grid over the packets of
+        // all its worlds and one packet-walk grid over what they handed back,
+        // and one packet-walk grid over the worlds that run the walk (the
+        // classes side by side)
+        char *tb = static_cast<char *>(g.table);
+        cudaEventRecord(g.fork2, origin);
+        for (size_t c = 0; c < classes.size(); ++c) {
+            const ExpandClass &x = classes[c];
+            cudaStream_t cs = g.streams[c];
+            if (c > 0) cudaStreamWaitEvent(cs, g.fork2, 0);
+            const int n = (int)x.members.size();
+            unsigned long long *ctr = reinterpret_cast<unsigned long long *>(tb + x.ctr_off);
+            if (!x.walk) {
+                knnq::launch_gather_batch(x.kc, tb + x.gather_off, n,
+                                          reinterpret_cast<long long *>(tb + x.pfx_g_off), ctr,
+                                          dev, cs);
+                launches1 += 2;
+            }
+            knnq::launch_walk_batch(x.kc, tb + x.walk_off, n,
+                                    reinterpret_cast<long long *>(tb + x.pfx_w_off), ctr + 1, dev,
+                                    cs);
+            launches1 += 2;
+        }
+        for (size_t c = 1; c < classes.size(); ++c) {
+            cudaEventRecord(g.join2[c], g.streams[c]);
+            cudaStreamWaitEvent(origin, g.join2[c], 0);
         }
         e = cudaStreamEndCapture(origin, &graph);
         if (e != cudaSuccess) {
@@ -150,6 +287,7 @@ extern "C" knn_status knn_batch_tick(int32_t n_worlds, const knn_world *worlds,
     }
     const cudaError_t e = cudaGraphLaunch(g.exec, s);
     if (e != cudaSuccess) return bad(KNN_ERR_CUDA, cudaGetErrorString(e));
+    if (cudaEventRecord(g.done, s) == cudaSuccess) g.pending = true;
     int64_t per_world = g.nodes / (n_worlds ? n_worlds : 1);
     for (int32_t i = 0; i < n_worlds; ++i) {
         worlds[i]->w.last_stream = s;
@@ -285,4 +423,121 @@ extern "C" knn_status knn_world_autotune(knn_world h, const int32_t *q_id_dev,
     w.tuning = best_t;
     if (chosen) *chosen = best_t;
     return finish(KNN_OK);
+}
+
+// ---------------------------------------------------------------------------
+// Batch autotuner: the settings of a batch's worlds chosen by timing the whole
+// batch (a world's best setting alone is not its best inside a batch, where
+// the batched expansion already fills the GPU with many worlds' packets).
+// Worlds are grouped by list size class; per class (largest query count
+// first) the expansion form is tried (gathered packets, packet walk, one warp
+// per query), then half and twice the leaf capacity; a change is kept only if
+// the batch gets clearly (3 %) faster.  Ticks run without updates, so the
+// worlds' positions are unchanged.
+
+extern "C" knn_status knn_batch_autotune(int32_t n_worlds, const knn_world *worlds,
+                                         const knn_tick_args *args, int32_t trials,
+                                         knn_tuning *chosen, void *stream) {
+    if (n_worlds < 0 || (n_worlds > 0 && (!worlds || !args)))
+        return bad(KNN_ERR_INVALID, "knn_batch_autotune: bad world list");
+    if (n_worlds == 0) return KNN_OK;
+    for (int32_t i = 0; i < n_worlds; ++i)
+        if (!worlds[i]) return bad(KNN_ERR_INVALID, "knn_batch_autotune: NULL world");
+    if (trials < 1) trials = 1;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<knn_tick_args> a(args, args + n_worlds);
+    for (knn_tick_args &x : a) {
+        x.upd_id_dev = nullptr;
+        x.upd_x_dev = nullptr;
+        x.upd_y_dev = nullptr;
+        x.n_upd = 0;
+    }
+    std::vector<knn_tuning> saved(n_worlds), cur(n_worlds);
+    for (int32_t i = 0; i < n_worlds; ++i) {
+        saved[i] = worlds[i]->w.tuning;
+        cur[i] = knn_tuning{saved[i].leaf_capacity, 0, 0, 0};  // a capacity fixed at creation stays
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    auto restore = [&](knn_status st) {
+        for (int32_t i = 0; i < n_worlds; ++i) worlds[i]->w.tuning = saved[i];
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return st;
+    };
+    // device time of one batch tick with the settings t (recorded, one warm
+    // replay, then `trials` timed replays)
+    auto time_batch = [&](const std::vector<knn_tuning> &t, float *ms) -> knn_status {
+        for (int32_t i = 0; i < n_worlds; ++i) worlds[i]->w.tuning = t[i];
+        for (int r = 0; r < 2; ++r) {
+            const knn_status st = knn_batch_tick(n_worlds, worlds, a.data(), stream);
+            if (st != KNN_OK) return st;
+        }
+        if (cudaEventRecord(e0, s) != cudaSuccess)
+            return bad(KNN_ERR_CUDA, "knn_batch_autotune: event record failed");
+        for (int r = 0; r < trials; ++r) {
+            const knn_status st = knn_batch_tick(n_worlds, worlds, a.data(), stream);
+            if (st != KNN_OK) return st;
+        }
+        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+            return bad(KNN_ERR_CUDA, "knn_batch_autotune: a timed batch failed");
+        cudaEventElapsedTime(ms, e0, e1);
+        *ms /= (float)trials;
+        return KNN_OK;
+    };
+    float best = 0.f;
+    knn_status st = time_batch(cur, &best);
+    if (st != KNN_OK) return restore(st);
+
+    // classes: the packet list sizes, then the lists above them (one warp per query only)
+    std::vector<std::vector<int32_t>> members(6);
+    std::vector<int64_t> queries(6, 0);
+    for (int32_t i = 0; i < n_worlds; ++i) {
+        const int c = a[i].k > knnq::kMaxPacketK ? 5 : class_of(a[i].k);
+        members[c].push_back(i);
+        queries[c] += a[i].n_q;
+    }
+    std::vector<int> order;
+    for (int c = 0; c < 5; ++c)
+        if (!members[c].empty() && queries[c] > 0) order.push_back(c);
+    std::sort(order.begin(), order.end(), [&](int x, int y) { return queries[x] > queries[y]; });
+    auto try_setting = [&](const std::vector<knn_tuning> &t) -> knn_status {
+        float ms = 0.f;
+        const knn_status r = time_batch(t, &ms);
+        if (r != KNN_OK) return r;
+        if (ms < 0.97f * best) {
+            best = ms;
+            cur = t;
+        }
+        return KNN_OK;
+    };
+    for (int c : order) {
+        // the expansion form
+        for (int form : {1, 2, 4}) {
+            std::vector<knn_tuning> t = cur;
+            for (int32_t i : members[c]) t[i].expansion = form;
+            if ((st = try_setting(t)) != KNN_OK) return restore(st);
+        }
+        // the leaf capacity (with the cell-map and packet levels that follow from it)
+        for (int scale : {-1, 1}) {
+            std::vector<knn_tuning> t = cur;
+            for (int32_t i : members[c]) {
+                worlds[i]->w.tuning = cur[i];
+                const int th = knnq::plan_for(worlds[i]->w, a[i].n_q, a[i].k).th;
+                const int th2 = scale < 0 ? th / 2 : th * 2;
+                t[i].leaf_capacity = th2 < 4 ? 4 : (th2 > 4096 ? 4096 : th2);
+                t[i].grid_level = 0;
+                t[i].packet_level = 0;
+            }
+            if ((st = try_setting(t)) != KNN_OK) return restore(st);
+        }
+    }
+    for (int32_t i = 0; i < n_worlds; ++i) {
+        worlds[i]->w.tuning = cur[i];
+        if (chosen) chosen[i] = cur[i];
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return KNN_OK;
 }

@@ -402,7 +402,7 @@ knn_status check_tick_args(const World &w, const knn_tick_args &a, const char *w
 }
 
 // The stages of one tick, in order, on stream s (no synchronisation, no allocation).
-void enqueue_tick(World &w, const knn_tick_args &a, cudaStream_t s, bool marks) {
+void enqueue_tick(World &w, const knn_tick_args &a, cudaStream_t s, bool marks, bool expand) {
     const Plan p = make_plan(w, a.n_q, a.k);
     const bool m = marks && w.profiling;
     launch_tick_begin(w, p, s);
@@ -425,7 +425,7 @@ void enqueue_tick(World &w, const knn_tick_args &a, cudaStream_t s, bool marks) 
     if (m) mark(w, 4, s);
     if (a.n_q > 0 && !p.wide && !p.iterative) launch_packets(w, p, a.n_q, s);
     if (m) mark(w, 5, s);
-    if (a.n_q > 0) {
+    if (a.n_q > 0 && expand) {
         if (p.gather)
             launch_expand_gather(w, p, a.k, a.n_q, a.out_ids_dev, a.out_d2_dev, a.q_k_dev, s);
         else if (p.iterative)

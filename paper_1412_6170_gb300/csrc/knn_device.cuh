@@ -368,4 +368,44 @@ __device__ __forceinline__ uint32_t block_excl_scan_256(uint32_t v, uint32_t *tm
     return wpre + x - v;
 }
 
+// Exclusive prefix of count(0) .. count(n - 1) into out[0 .. n - 1] and the
+// total into out[n], by one block of exactly 1024 threads (all of them call
+// it); n may exceed the block, the counts are taken 1024 at a time.
+template <class Count>
+__device__ void block_prefix_1024(int n, const Count &count, long long *out) {
+    __shared__ long long wsum[32];
+    __shared__ long long carry;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += 1024) {
+        const int i = base + tid;
+        const long long v = i < n ? count(i) : 0;
+        long long x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            long long t = wsum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long y = __shfl_up_sync(kFull, t, o);
+                if (lane >= o) t += y;
+            }
+            wsum[lane] = t;
+        }
+        __syncthreads();
+        const long long excl = carry + (wid > 0 ? wsum[wid - 1] : 0) + x - v;
+        if (i < n) out[i] = excl;
+        __syncthreads();  // every thread has read carry and wsum
+        if (tid == 1023) carry = excl + v;
+        __syncthreads();
+    }
+    if (tid == 0) out[n] = carry;
+}
+
 }  // namespace knnq

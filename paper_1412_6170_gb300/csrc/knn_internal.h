@@ -226,6 +226,27 @@ void launch_expand_handed_back(World &w, const Plan &p, int32_t k, int64_t n_q,
 void launch_expand_gather(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t *out_ids,
                           float *out_d2, const int32_t *q_k, cudaStream_t s);
 
+// ---- batched expansion over many worlds (knn_expand_gather.cu, knn_expand.cu)
+// A batch table holds one entry per world (the world's expansion arguments,
+// filled on the host and copied to the device once per recorded batch).  One
+// launch per list size then expands the packets of every world of the table:
+// a one-block prefix kernel counts each world's packets on the device (pfx,
+// n + 1 entries) and resets the ticket counter, and a persistent grid takes
+// tickets across all worlds.  The walk form does the same over the packets
+// the gathered form handed back, or over the packets of the worlds that run
+// the packet walk.  kc: the list size class (4, 8, 16, 32, 64).
+size_t gather_batch_entry_bytes();
+void gather_batch_entry(World &w, const Plan &p, const knn_tick_args &t, void *dst);
+void launch_gather_batch(int kc, const void *table, int n, long long *pfx,
+                         unsigned long long *counter, int device, cudaStream_t s);
+size_t walk_batch_entry_bytes();
+// handed_back: the entry covers the packets the gathered form handed back
+// (else the world's own packet list, for worlds on the packet walk)
+void walk_batch_entry(World &w, const Plan &p, const knn_tick_args &t, bool handed_back,
+                      void *dst);
+void launch_walk_batch(int kc, const void *table, int n, long long *pfx,
+                       unsigned long long *counter, int device, cudaStream_t s);
+
 int num_sms(int device);
 // One-time kernel attributes and cached device queries (called outside any
 // stream capture).
@@ -250,8 +271,10 @@ void set_last_error(const char *msg);
 // Host-side argument checks of one tick (sets the error message).
 knn_status check_tick_args(const World &w, const knn_tick_args &a, const char *who);
 // Enqueue every stage of one tick on s; `marks` records stage events when
-// the world's profiling is on.
-void enqueue_tick(World &w, const knn_tick_args &a, cudaStream_t s, bool marks);
+// the world's profiling is on.  expand == false stops after the packets are
+// cut (a batch expands them).
+void enqueue_tick(World &w, const knn_tick_args &a, cudaStream_t s, bool marks,
+                  bool expand = true);
 // One tick through the world's graph cache when graphs are on (else direct).
 knn_status tick_launch(World &w, const knn_tick_args &a, cudaStream_t s);
 // The index / expansion parameters a tick with n_q queries and this k uses.

@@ -110,6 +110,8 @@ _SIGNATURES = {
                        ctypes.c_int),
     "knn_world_autotune": ([_vp, _vp, _vp, _vp, _i64, _i32, _vp, _vp, _i32,
                             ctypes.POINTER(knn_tuning), _vp], ctypes.c_int),
+    "knn_batch_autotune": ([_i32, ctypes.POINTER(_vp), ctypes.POINTER(knn_tick_args), _i32,
+                            ctypes.POINTER(knn_tuning), _vp], ctypes.c_int),
     "knn_server_create": ([ctypes.POINTER(knn_server_desc), ctypes.POINTER(_vp)], ctypes.c_int),
     "knn_server_add_world": ([_vp, ctypes.POINTER(knn_world_desc), _vp, _vp, _i64,
                               ctypes.POINTER(_i32)], ctypes.c_int),
@@ -331,6 +333,18 @@ def knn_world_autotune(w: int, q_id, q_x, q_y, n_q: int, k: int, out_ids, out_d2
                                     ctypes.byref(t), stream))
     return {"leaf_capacity": t.leaf_capacity, "grid_level": t.grid_level,
             "packet_level": t.packet_level, "expansion": t.expansion}
+
+
+def knn_batch_autotune(worlds, args, trials: int = 2, stream: int = 0) -> list:
+    """Settings for the batch's worlds chosen by timing whole batch ticks; returns
+    one tuning dict per world (the settings stay in the worlds)."""
+    n = len(worlds)
+    wa = (_vp * n)(*worlds)
+    aa = (knn_tick_args * n)(*args)
+    ts = (knn_tuning * n)()
+    _check(lib().knn_batch_autotune(n, wa, aa, trials, ts, stream))
+    return [{"leaf_capacity": t.leaf_capacity, "grid_level": t.grid_level,
+             "packet_level": t.packet_level, "expansion": t.expansion} for t in ts]
 
 
 def tick_args(k: int, q_id=None, upd_id=None, upd_x=None, upd_y=None, q_x=None, q_y=None,
