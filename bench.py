@@ -812,6 +812,21 @@ def run_gpu(args):
     if dist is not None:
         dist.barrier()
     knnq.lib()
+    if args.only:
+        # one comparison leg alone (its own JSON line), e.g. for a profiler
+        legs = {"serving": lambda: serving_config5(dev, check=not args.no_check),
+                "skewed": lambda: skewed_config3(dev, check=not args.no_check),
+                "batching": lambda: batched_vs_plain(dev),
+                "k_sweep": lambda: k_sweep(dev),
+                "index_reuse": lambda: index_reuse_vs_rebuild(dev),
+                "brute_force": lambda: brute_vs_indexed(dev),
+                "expansion_ablation": lambda: expansion_ablation(dev)}
+        if rank == 0:
+            print(json.dumps({"leg": args.only, **legs[args.only]()}, default=_json_default),
+                  flush=True)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
 
     wl = synth.plain_uniform_moving(n=N_OBJ, k=K, ticks=N_TICKS, seed=0)
     stream = torch.cuda.current_stream()
@@ -1069,6 +1084,10 @@ def main():
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-patterns", action="store_true",
                     help="skip the serving, skewed, batching and other comparison legs")
+    ap.add_argument("--only", default=None,
+                    choices=["serving", "skewed", "batching", "k_sweep", "index_reuse",
+                             "brute_force", "expansion_ablation"],
+                    help="run one comparison leg alone and print its JSON line")
     ap.add_argument("--latency-ticks", type=int, default=200,
                     help="ticks timed one by one for p50/p99 tick latency")
     args = ap.parse_args()
