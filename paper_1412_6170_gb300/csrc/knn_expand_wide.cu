@@ -12,7 +12,10 @@
 // keys, then sorted, and the first k keys are the row, written by the whole
 // warp (coalesced).  (Measured on 1M uniform objects: the select halves the
 // expansion at k = 256 and 512 and saves 31 % at k = 128; at k <= 64 the
-// sort of at most 128 keys is the cheaper cut.)
+// sort of at most 128 keys is the cheaper cut.)  Sorts of up to 128 keys run
+// in registers, four keys per lane with shuffles between lanes (k = 64: 2.99
+// -> 2.58 ms per tick, k = 128: 4.68 -> 4.43 ms, against the sort through
+// shared memory, which longer sorts keep).
 //
 // The walk is the packet kernel's, for a single point: the query's level-G
 // cell and the rings around it, gathered 32 cells at a time, every leaf whose
@@ -74,6 +77,66 @@ __device__ __forceinline__ void warp_sort_keys(unsigned long long *buf, int coun
             __syncwarp();
         }
     }
+}
+
+// The same sort in registers for 32 R keys (entries from count on padded with
+// kPad): lane i holds the keys i R .. i R + R - 1, a compare-exchange between
+// two keys of one lane stays in registers and one between lanes goes through
+// a shuffle; no shared-memory round trip per stage.
+template <int R>
+__device__ __forceinline__ void warp_sort_regs(unsigned long long *buf, int count, int lane) {
+    constexpr int P = 32 * R;
+    __syncwarp();
+    unsigned long long x[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        const int e = lane * R + j;
+        x[j] = e < count ? buf[e] : kPad;
+    }
+#pragma unroll
+    for (int size = 2; size <= P; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride < R) {
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    const int pj = j ^ stride;
+                    if (pj > j) {
+                        const bool asc = ((lane * R + j) & size) == 0;
+                        const unsigned long long a = x[j], b = x[pj];
+                        const bool sw = asc ? b < a : a < b;
+                        x[j] = sw ? b : a;
+                        x[pj] = sw ? a : b;
+                    }
+                }
+            } else {
+                const int ls = stride / R;
+                const bool lower = (lane & ls) == 0;
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    const unsigned long long y = __shfl_xor_sync(kFull, x[j], ls);
+                    const bool asc = ((lane * R + j) & size) == 0;
+                    const bool ylo = y < x[j];
+                    x[j] = (lower == asc) == ylo ? y : x[j];
+                }
+            }
+        }
+    }
+    __syncwarp();  // every lane has read its keys
+#pragma unroll
+    for (int j = 0; j < R; ++j) buf[lane * R + j] = x[j];
+    __syncwarp();
+}
+
+// Ascending sort of buf[0, count) (count <= cap): in registers up to 32 RMAX
+// keys, else in shared memory.
+template <int RMAX>
+__device__ __forceinline__ void warp_sort(unsigned long long *buf, int count, int cap, int lane) {
+    if (count <= 32) warp_sort_regs<1>(buf, count, lane);
+    else if (count <= 64) warp_sort_regs<2>(buf, count, lane);
+    else if (RMAX >= 4 && count <= 128) warp_sort_regs<(RMAX >= 4 ? 4 : 1)>(buf, count, lane);
+    else if (RMAX >= 8 && count <= 256) warp_sort_regs<(RMAX >= 8 ? 8 : 1)>(buf, count, lane);
+    else warp_sort_keys(buf, count, cap, lane);
 }
 
 // Moves the keys of buf[0, count) whose d^2 is at most the kq-th smallest d^2
@@ -299,7 +362,7 @@ __global__ void __launch_bounds__(kWideWarps * 32) k_expand_wide(const WideArgs 
                                     thr = fminf(thr, warp_max(mx));
                                     count = kept;
                                 } else {
-                                    warp_sort_keys(buf, count, B, lane);
+                                    warp_sort<(B >= 128 ? 4 : B / 32)>(buf, count, B, lane);
                                     if (count > kq) count = kq;
                                     thr = fminf(thr, __uint_as_float((uint32_t)(buf[kq - 1] >> 32)));
                                 }
@@ -322,7 +385,7 @@ __global__ void __launch_bounds__(kWideWarps * 32) k_expand_wide(const WideArgs 
         // a8: the row, in caller order, written by the whole warp
         if (KW >= 128 && count > KW)
             count = warp_select_front(buf, count, kq, s_hist[wid], lane);
-        warp_sort_keys(buf, count, B, lane);
+        warp_sort<(B >= 128 ? 4 : B / 32)>(buf, count, B, lane);
         int32_t *oi = g.out_ids + (int64_t)orig * k;
         float *od = g.out_d2 + (int64_t)orig * k;
         for (int r = lane; r < k; r += 32) {
