@@ -1,10 +1,12 @@
 // Batched ticks over many worlds, and the per-world autotuner.
 //
 // knn_batch_tick records the tick of every world of a batch into one CUDA
-// graph: each world's stages form an independent chain, the chains are spread
-// over internal streams between a fork and a join on the caller's stream, so
-// the GPU runs small worlds side by side and the whole batch costs one graph
-// launch.  The executable graph is kept and replayed while the batch keeps the
+// graph: each world's index stages form an independent chain, the chains are
+// spread over internal streams between a fork and a join on the caller's
+// stream, so the GPU runs small worlds side by side and the whole batch costs
+// one graph launch.  The expansion runs batched: per form and list size one
+// persistent grid over the packets of all the class's worlds, started as soon
+// as that class's chains are done.  The executable graph is kept and replayed while the batch keeps the
 // same worlds, sizes and pointers (a steady serving or simulation loop); any
 // change records the batch again and updates the graph in place.  Every tick
 // takes its look-back epochs and update stamps from device counters, so a
@@ -43,7 +45,11 @@ struct BatchGraph {
     void *table = nullptr;
     size_t table_bytes = 0;
     std::vector<char> host;
-    cudaEvent_t fork2 = nullptr, join2[kMaxStreams] = {};
+    // one stream per expansion class; cls_done[c][i]: stream i has finished
+    // the index chains of class c's worlds (and of every world before them)
+    cudaStream_t cstreams[10] = {};
+    cudaEvent_t cls_done[10][kMaxStreams] = {};
+    cudaEvent_t cjoin[10] = {};
     cudaEvent_t done = nullptr;  // after the last launch of the graph
     bool pending = false;
 };
@@ -82,14 +88,20 @@ bool same_args(const knn_tick_args &a, const knn_tick_args &b) {
 knn_status ensure_streams(BatchGraph &g) {
     if (g.fork) return KNN_OK;
     if (cudaEventCreateWithFlags(&g.fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&g.fork2, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming) != cudaSuccess)
         return bad(KNN_ERR_CUDA, "knn_batch_tick: event creation failed");
     for (int i = 0; i < kMaxStreams; ++i) {
         if (cudaStreamCreateWithFlags(&g.streams[i], cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&g.join[i], cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&g.join2[i], cudaEventDisableTiming) != cudaSuccess)
+            cudaEventCreateWithFlags(&g.join[i], cudaEventDisableTiming) != cudaSuccess)
             return bad(KNN_ERR_CUDA, "knn_batch_tick: stream creation failed");
+    }
+    for (int c = 0; c < 10; ++c) {
+        if (cudaStreamCreateWithFlags(&g.cstreams[c], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&g.cjoin[c], cudaEventDisableTiming) != cudaSuccess)
+            return bad(KNN_ERR_CUDA, "knn_batch_tick: stream creation failed");
+        for (int i = 0; i < kMaxStreams; ++i)
+            if (cudaEventCreateWithFlags(&g.cls_done[c][i], cudaEventDisableTiming) != cudaSuccess)
+                return bad(KNN_ERR_CUDA, "knn_batch_tick: event creation failed");
     }
     return KNN_OK;
 }
@@ -218,44 +230,61 @@ extern "C" knn_status knn_batch_tick(int32_t n_worlds, const knn_world *worlds,
         const int ns = n_worlds < kMaxStreams ? n_worlds : kMaxStreams;
         cudaEventRecord(g.fork, origin);
         for (int i = 1; i < ns; ++i) cudaStreamWaitEvent(g.streams[i], g.fork, 0);
-        int64_t launches0 = 0, launches1 = 0;
+        int64_t launches0 = 0, launches1 = 0, batch_launches = 0;
         for (int32_t i = 0; i < n_worlds; ++i) launches0 += worlds[i]->w.launches;
-        // every world's index stages (and the expansion of the worlds that
-        // are not batched) as independent chains
-        for (int32_t i = 0; i < n_worlds; ++i)
-            knnq::enqueue_tick(worlds[i]->w, args[i], g.streams[i % ns], false, !batched[i]);
-        for (int32_t i = 0; i < n_worlds; ++i) launches1 += worlds[i]->w.launches;
-        for (int i = 1; i < ns; ++i) {
-            cudaEventRecord(g.join[i], g.streams[i]);
-            cudaStreamWaitEvent(origin, g.join[i], 0);
-        }
-        // then per list size one gathered-expansion grid over the packets of
-        // all its worlds and one packet-walk grid over what they handed back,
-        // and one packet-walk grid over the worlds that run the walk (the
-        // classes side by side)
+        // Every world's index stages (and the expansion of the worlds that are
+        // not batched) as independent chains, round robin over the streams,
+        // class by class with the costliest expansion class first (query
+        // count x list size).  Once a class's chains are done on every
+        // stream, its own stream runs one gathered-expansion grid over the
+        // packets of all its worlds and one packet-walk grid over what they
+        // handed back (a walk class: one walk grid), so the expansion of the
+        // first classes overlaps the index stages of the later ones.
+        std::vector<size_t> corder(classes.size());
+        for (size_t c = 0; c < classes.size(); ++c) corder[c] = c;
+        auto cost = [&](size_t c) {
+            double q = 0.0;
+            for (int32_t i : classes[c].members) q += (double)args[i].n_q;
+            return q * classes[c].kc;
+        };
+        std::sort(corder.begin(), corder.end(),
+                  [&](size_t a0, size_t b0) { return cost(a0) > cost(b0); });
         char *tb = static_cast<char *>(g.table);
-        cudaEventRecord(g.fork2, origin);
-        for (size_t c = 0; c < classes.size(); ++c) {
+        int32_t pos = 0;
+        for (size_t r = 0; r < corder.size(); ++r) {
+            const size_t c = corder[r];
             const ExpandClass &x = classes[c];
-            cudaStream_t cs = g.streams[c];
-            if (c > 0) cudaStreamWaitEvent(cs, g.fork2, 0);
+            for (int32_t i : x.members)
+                knnq::enqueue_tick(worlds[i]->w, args[i], g.streams[pos++ % ns], false, false);
+            cudaStream_t cs = g.cstreams[r];
+            for (int i = 0; i < ns; ++i) {
+                cudaEventRecord(g.cls_done[r][i], g.streams[i]);
+                cudaStreamWaitEvent(cs, g.cls_done[r][i], 0);
+            }
             const int n = (int)x.members.size();
             unsigned long long *ctr = reinterpret_cast<unsigned long long *>(tb + x.ctr_off);
             if (!x.walk) {
                 knnq::launch_gather_batch(x.kc, tb + x.gather_off, n,
                                           reinterpret_cast<long long *>(tb + x.pfx_g_off), ctr,
                                           dev, cs);
-                launches1 += 2;
+                batch_launches += 2;
             }
             knnq::launch_walk_batch(x.kc, tb + x.walk_off, n,
                                     reinterpret_cast<long long *>(tb + x.pfx_w_off), ctr + 1, dev,
                                     cs);
-            launches1 += 2;
+            batch_launches += 2;
+            cudaEventRecord(g.cjoin[r], cs);
         }
-        for (size_t c = 1; c < classes.size(); ++c) {
-            cudaEventRecord(g.join2[c], g.streams[c]);
-            cudaStreamWaitEvent(origin, g.join2[c], 0);
+        for (int32_t i = 0; i < n_worlds; ++i)
+            if (!batched[i])
+                knnq::enqueue_tick(worlds[i]->w, args[i], g.streams[pos++ % ns], false, true);
+        for (int32_t i = 0; i < n_worlds; ++i) launches1 += worlds[i]->w.launches;
+        launches1 += batch_launches;
+        for (int i = 1; i < ns; ++i) {
+            cudaEventRecord(g.join[i], g.streams[i]);
+            cudaStreamWaitEvent(origin, g.join[i], 0);
         }
+        for (size_t r = 0; r < corder.size(); ++r) cudaStreamWaitEvent(origin, g.cjoin[r], 0);
         e = cudaStreamEndCapture(origin, &graph);
         if (e != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
