@@ -687,9 +687,10 @@ __global__ void __launch_bounds__(256) k_scan_excl(const int32_t *in, const int3
                                                    uint32_t *ticket,
                                                    const uint32_t *__restrict__ tickinfo,
                                                    uint32_t site, uint32_t *err,
-                                                   const int32_t *skip_if,
+                                                   const int32_t *skip_if, int skip_on_zero,
                                                    const int32_t *len_minus_1) {
-    if (skip_if && *skip_if != 0) return;  // the same for every block of the launch
+    // the same for every block of the launch
+    if (skip_if && (*skip_if != 0) != (skip_on_zero != 0)) return;
     if (len_minus_1) {  // the length is known on the device only: *len_minus_1 + 1 <= len
         const int64_t l = (int64_t)*len_minus_1 + 1;
         len = l < len ? (l > 0 ? l : 0) : len;
@@ -748,21 +749,23 @@ __global__ void __launch_bounds__(256) k_scan_excl(const int32_t *in, const int3
     if ((int64_t)(tile + 1) * kScanTile >= len && tid == 255 && total) *total = (int32_t)run;
 }
 
-// skip_if: when non-null and nonzero on the device, the launch does nothing.
+// skip_if: when non-null and nonzero on the device (zero, with skip_on_zero),
+// the launch does nothing.
 // len_minus_1: when non-null, the device value + 1 (at most len) is the length.
 // gather_idx: when non-null, entry c is in[gather_idx[c]] (and the last entry 0).
 static void scan_excl(World &w, const int32_t *in, int32_t *out, int64_t len, int32_t *total,
                       int counter, cudaStream_t s, const int32_t *gather_idx = nullptr,
-                      const int32_t *skip_if = nullptr, const int32_t *len_minus_1 = nullptr) {
+                      const int32_t *skip_if = nullptr, const int32_t *len_minus_1 = nullptr,
+                      bool skip_on_zero = false) {
     const int tiles = (int)((len + kScanTile - 1) / kScanTile);
     if (gather_idx)
         k_scan_excl<true><<<tiles, 256, 0, s>>>(in, gather_idx, out, len, total, w.status,
                                                 w.counters + counter, w.tickinfo, w.site++,
-                                                w.err, skip_if, len_minus_1);
+                                                w.err, skip_if, skip_on_zero, len_minus_1);
     else
         k_scan_excl<false><<<tiles, 256, 0, s>>>(in, nullptr, out, len, total, w.status,
                                                  w.counters + counter, w.tickinfo, w.site++,
-                                                 w.err, skip_if, len_minus_1);
+                                                 w.err, skip_if, skip_on_zero, len_minus_1);
     ++w.launches;
 }
 
@@ -822,7 +825,10 @@ __global__ void k_query_place(int64_t n_q, int64_t n, const int32_t *__restrict_
 // By issuer id, first half: every valid query counts one more query at its
 // issuer and keeps its rank among that issuer's queries and, in qidx[issuer],
 // its own index (the only one there when the issuer has a single query).  A
-// second query at one issuer raises qcnt[n], which makes k_query_place_id run.
+// second query at one issuer sets bit 0 of qcnt[n], which makes
+// k_query_place_id run; an invalid issuer sets bit 1.  With as many queries as
+// objects, qcnt[n] == 0 means one query per object: the query offsets are the
+// identity and their scan is skipped.
 __global__ void k_query_count_id(const int32_t *__restrict__ q_id, int64_t n_q, int64_t n,
                                  int32_t *qcnt, int k, int32_t *out_ids, float *out_d2,
                                  uint32_t *err, int32_t *__restrict__ qrank,
@@ -832,6 +838,7 @@ __global__ void k_query_count_id(const int32_t *__restrict__ q_id, int64_t n_q, 
         const int32_t s = q_id[i];
         if (s < 0 || s >= n) {
             atomicOr(err, kErrBadQuery);
+            atomicOr(&qcnt[n], 2);
             for (int r = 0; r < k; ++r) {
                 out_ids[i * k + r] = -1;
                 out_d2[i * k + r] = __int_as_float(0x7f800000);
@@ -841,7 +848,7 @@ __global__ void k_query_count_id(const int32_t *__restrict__ q_id, int64_t n_q, 
         const int32_t r = atomicAdd(&qcnt[s], 1);
         qrank[i] = r;
         qidx[s] = (int32_t)i;
-        if (r == 1) qcnt[n] = 1;
+        if (r == 1) atomicOr(&qcnt[n], 1);
     }
 }
 
@@ -854,7 +861,7 @@ __global__ void k_query_place_id(const int32_t *__restrict__ q_id, int64_t n_q, 
                                  const int32_t *__restrict__ qrank,
                                  const int32_t *__restrict__ qoff,
                                  const int32_t *__restrict__ qcnt, int32_t *qs_orig) {
-    if (qcnt[n] == 0) return;  // the same for every block of the launch
+    if ((qcnt[n] & 1) == 0) return;  // the same for every block of the launch
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_q;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t s = q_id[i];
@@ -877,10 +884,16 @@ __global__ void k_query_fill(int64_t n, int64_t n_q, const int32_t *__restrict__
                              const int32_t *__restrict__ obj_leaf,
                              const int32_t *__restrict__ qidx, float *qs_x, float *qs_y,
                              int32_t *qs_id, uint32_t *qs_key, int32_t *qs_leaf,
-                             int32_t *qs_orig, int32_t *inv) {
+                             int32_t *qs_orig, int32_t *inv, const int32_t *ident,
+                             int32_t *scalars) {
+    // one query per object (ident: the flag word of k_query_count_id, zero):
+    // object p's query is slot p, the offsets were not scanned
+    const bool identity = ident && *ident == 0;
+    if (identity && blockIdx.x == 0 && threadIdx.x == 0) scalars[kScalarValidQueries] = (int32_t)n;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
-        int32_t a = qoff[p], b = qoff[p + 1];
+        int32_t a = identity ? (int32_t)p : qoff[p];
+        int32_t b = identity ? (int32_t)p + 1 : qoff[p + 1];
         if (a >= b) continue;
         const bool single = b - a == 1;
         if (a < 0) a = 0;
@@ -918,11 +931,14 @@ void launch_queries_at_issuers(World &w, const Plan &p, const int32_t *q_id, int
         // aux: each issuer's last query
         k_query_count_id<<<g, 256, 0, s>>>(q_id, n_q, w.n, w.qcnt, k, out_ids, out_d2, w.err,
                                            qrank, aux);
+        // counts taken in sorted-object order; with as many queries as
+        // objects the scan is skipped when each object has exactly one
+        const int32_t *ident = n_q == w.n ? w.qcnt + w.n : nullptr;
         scan_excl(w, w.qcnt, w.qoff, w.n + 1, w.scalars + kScalarValidQueries, kCtrQueryScan,
-                  s, w.sid);  // counts taken in sorted-object order
+                  s, w.sid, ident, nullptr, true);
         k_query_fill<<<gf, 256, 0, s>>>(w.n, n_q, w.qoff, w.xs, w.ys, w.sid, skey, w.obj_leaf,
                                         aux, w.qs_x, w.qs_y, w.qs_id, w.qs_key, w.qs_leaf,
-                                        w.qs_orig, w.inv);
+                                        w.qs_orig, w.inv, ident, w.scalars);
         k_query_place_id<<<g, 256, 0, s>>>(q_id, n_q, w.n, w.inv, qrank, w.qoff, w.qcnt,
                                            w.qs_orig);
     } else {
@@ -934,7 +950,7 @@ void launch_queries_at_issuers(World &w, const Plan &p, const int32_t *q_id, int
         k_query_place<<<g, 256, 0, s>>>(n_q, w.n, aux, qrank, w.qoff, w.qs_orig);
         k_query_fill<<<gf, 256, 0, s>>>(w.n, n_q, w.qoff, w.xs, w.ys, w.sid, skey, w.obj_leaf,
                                         nullptr, w.qs_x, w.qs_y, w.qs_id, w.qs_key, w.qs_leaf,
-                                        w.qs_orig, w.inv);
+                                        w.qs_orig, w.inv, nullptr, w.scalars);
     }
     w.launches += 3;  // and one counted by scan_excl
 }

@@ -279,6 +279,27 @@ def test_repeated_query_ids_both_counting_sorts(nq):
     compare_ticks(x, y, [tick(q, 9), tick(r.permutation(n)[:nq].astype(np.int32), 6)])
 
 
+def test_one_query_per_object_and_near_misses():
+    # as many queries as objects, counted by issuer id: a permutation of the
+    # objects (each queries once: the query offsets are the identity and their
+    # scan is skipped), then the cases that look alike but are not -- one
+    # issuer twice and another never, one invalid issuer -- which take the scan
+    r = np.random.default_rng(19)
+    n = 20000
+    x, y = r.random(n).astype(np.float32), r.random(n).astype(np.float32)
+    perm = r.permutation(n).astype(np.int32)
+    dup = perm.copy()
+    dup[100] = dup[200]
+    moved = (r.random(n) < 0.5).astype(bool)
+    uid = np.flatnonzero(moved).astype(np.int32)
+    upd = (uid, np.clip(x[uid] + 1e-3, 0, 1), np.clip(y[uid] - 1e-3, 0, 1))
+    compare_ticks(x, y, [tick(perm, 16), tick(dup, 16, upd), tick(perm, 8), tick(perm[::-1], 16)])
+    bad = perm.copy()
+    bad[5] = -7
+    compare_ticks(x, y, [tick(perm, 16), tick(bad, 16), tick(perm, 16)],
+                  expect_status=knnq.KNN_ERR_DEVICE_INPUT)
+
+
 def test_domain_offset_and_scale():
     r = np.random.default_rng(8)
     n = 20000
