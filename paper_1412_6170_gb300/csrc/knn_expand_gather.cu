@@ -40,11 +40,19 @@ constexpr int kDensityCells = 64;      // cells counted around a packet for per-
 
 template <int KC>
 struct GatherShape {
-    // buffer slots per lane (lists of 64 need 36: the row write reuses the
-    // buffer for 32 rows of KC + 4 words)
-    static constexpr int kCap = KC <= 32 ? 32 : 36;
+    // Buffer slots per lane.  A merge is forced for every lane as soon as one
+    // lane's buffer is kBatch short of full, and then every lane merges its
+    // newest kBatch (most of them padding when only a few lanes were near
+    // full), so a longer buffer means fewer, fuller merges.  Lists of 32 take
+    // 56 slots at 3 blocks per SM (4M clustered objects, a quarter querying:
+    // 16 merges per packet with 32 slots, expansion 1.53 -> 1.41 ms; 1M
+    // uniform, all querying: 0.87 -> 0.84 ms); shorter lists keep 32 slots and
+    // 5 blocks per SM (40 or 44 slots at 4 blocks: clustered k = 16 4 %
+    // faster, uniform k = 16 0.5 % slower).  Lists of 64 need 36: the row
+    // write reuses the buffer for 32 rows of KC + 4 words.
+    static constexpr int kCap = KC <= 16 ? 32 : (KC <= 32 ? 56 : 36);
     static constexpr int kFlushAt = kCap - kBatch;
-    static constexpr int kMinBlocks = KC <= 16 ? 5 : (KC <= 32 ? 4 : 2);  // 20, 16 or 8 warps per SM
+    static constexpr int kMinBlocks = KC <= 16 ? 5 : (KC <= 32 ? 3 : 2);  // 20, 12 or 8 warps per SM
 };
 
 struct GatherArgs {
