@@ -73,7 +73,8 @@ typedef enum {
 typedef struct {
     float x0, y0, side;      /* side > 0 and finite */
     int32_t leaf_capacity;   /* th_quad: max objects per leaf; 0 = automatic; <= 4096 */
-    int32_t max_depth;       /* l_max in [1, 16]; 0 = 16 */
+    int32_t max_depth;       /* l_max in [1, 16]; 0 = automatic: 12 for n <= 2^20
+                                objects (24-bit keys, a 3-pass sort), else 16 */
     int32_t k_max;           /* largest k a tick may ask for, in [1, 512] */
     int64_t max_queries;     /* largest n_q a tick may pass, >= 0 */
 } knn_world_desc;

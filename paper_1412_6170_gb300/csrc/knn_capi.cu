@@ -193,7 +193,7 @@ knn_status world_init_resident(World &w, const knn_world_desc *desc, const float
     cudaGetDevice(&w.device);
     w.desc = *desc;
     w.n = n;
-    w.L = desc->max_depth > 0 ? desc->max_depth : 16;
+    w.L = desc->max_depth > 0 ? desc->max_depth : knnq::default_max_depth(n);
     // a cell map with more than ~4 cells per object never pays off
     int g = 1;
     while (g < kMaxGridLevel && g < w.L && (1ll << (2 * g)) < 4 * n) ++g;

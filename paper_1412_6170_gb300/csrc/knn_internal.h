@@ -177,6 +177,14 @@ inline int default_leaf_capacity(int k) {
     return th < 8 ? 8 : (th > 256 ? 256 : th);
 }
 
+// l_max when the world's descriptor leaves it to the library (Section 4.1.1
+// fixes l_max without a value): 12 while a uniform world would hold at most
+// one object per 16 level-12 cells (n <= 4^12 / 16), so that the Morton keys
+// have 24 bits and the radix sort three 8-bit passes; 16 (32-bit keys, four
+// passes) for larger worlds.  Rows do not depend on it: a leaf at l_max may
+// hold more than th_quad objects and is searched like any other.
+inline int default_max_depth(int64_t n) { return n <= (int64_t(1) << 20) ? 12 : 16; }
+
 // Packets never exceed n_q/32 + (non-empty packet cells) <= n_q + n_q/32 + 1.
 inline int64_t packet_capacity(const World &w) {
     return w.desc.max_queries + w.desc.max_queries / 32 + 2;

@@ -173,7 +173,7 @@ extern "C" knn_status knn_query_static(const knn_world_desc *desc, const float *
     w.desc.k_max = knnq::kMaxK;
     w.desc.max_queries = n_q;
     w.n = n;
-    w.L = desc->max_depth > 0 ? desc->max_depth : 16;
+    w.L = desc->max_depth > 0 ? desc->max_depth : knnq::default_max_depth(n);
     w.gmax = w.L < kStaticMaxGridLevel ? w.L : kStaticMaxGridLevel;
     w.scale = (float)(1u << w.L) / desc->side;
     w.tuning.leaf_capacity = desc->leaf_capacity;

@@ -55,6 +55,27 @@ def test_leaves_match_oracle(dist, n, th, G, L):
         assert np.array_equal(got[key].astype(np.int64), want[key].astype(np.int64)), key
 
 
+@pytest.mark.parametrize("n,L", [(100_000, 12), (1 << 20, 12), ((1 << 20) + 1, 16)])
+def test_automatic_depth(n, L):
+    # a world created without max_depth takes l_max = 12 up to 2^20 objects and
+    # 16 above; its leaves are the oracle's at that depth
+    x, y = synth.clustered_positions(n, 6)
+    world = make_world(x, y, k_max=8)
+    try:
+        world.set_tuning(leaf_capacity=16, grid_level=7, packet_level=4)
+        t = synth.Tick(np.zeros(0, np.int32), np.zeros(0, np.float32), np.zeros(0, np.float32),
+                       np.arange(100, dtype=np.int32), 4)
+        gpu_tick(world, t)
+        got = {k: v.cpu().numpy() for k, v in world.leaves().items()}
+    finally:
+        world.close()
+    got["z"] = got["z"].view(np.uint32)
+    want = oracle.pr_quadtree(x, y, L, 16, min_level=7)
+    assert np.array_equal(got["order"], want["order"])
+    for key in ("level", "z", "start", "count"):
+        assert np.array_equal(got[key].astype(np.int64), want[key].astype(np.int64)), key
+
+
 @pytest.mark.parametrize("dist,n,th,G", [("clustered", 100000, 16, 8), ("half", 30000, 8, 6)])
 def test_reuse_leaves_cover_every_cell(dist, n, th, G):
     # with index reuse on, the leaves are the oracle's plus one empty leaf at
@@ -65,7 +86,7 @@ def test_reuse_leaves_cover_every_cell(dist, n, th, G):
     else:
         x, y = synth.uniform_positions(n, 4)
         x = (x * 0.5).astype(np.float32)
-    world = make_world(x, y, k_max=8)
+    world = make_world(x, y, k_max=8, max_depth=L)
     try:
         world.set_tuning(leaf_capacity=th, grid_level=G, packet_level=min(G, 4))
         world.set_index_reuse(4)
