@@ -279,6 +279,42 @@ def test_repeated_query_ids_both_counting_sorts(nq):
     compare_ticks(x, y, [tick(q, 9), tick(r.permutation(n)[:nq].astype(np.int32), 6)])
 
 
+def test_updates_aligned_and_offset_arrays():
+    # the same updates (repeated ids, ids out of range, non-finite positions, a
+    # length that is not a multiple of 4) through 16-byte aligned caller arrays
+    # and through arrays one element off
+    torch, dev = torch_dev()
+    r = np.random.default_rng(23)
+    n = 5000
+    x, y = r.random(n).astype(np.float32), r.random(n).astype(np.float32)
+    m = 4003
+    uid = r.integers(-3, n + 3, m).astype(np.int32)
+    uid[100:140] = 77
+    ux = r.random(m).astype(np.float32)
+    uy = r.random(m).astype(np.float32)
+    ux[5] = np.nan
+    uy[9] = np.inf
+    q = np.arange(n, dtype=np.int32)
+    xe, ye, _ = oracle.apply_updates(x, y, uid, ux, uy)
+    rid, rd2, _ = oracle.knn(xe, ye, q, 8)
+    for off in (0, 1):
+        bufs = []
+        for a in (uid, ux, uy):
+            t = torch.zeros(m + off, dtype=torch.from_numpy(a).dtype, device=dev)
+            t[off:] = torch.from_numpy(a).to(dev)
+            bufs.append(t[off:])
+        world = make_world(x, y, k_max=8, max_queries=n)
+        try:
+            ids, d2 = world.tick(8, to_dev(q), *bufs)
+            torch.cuda.synchronize()
+            assert_rows_equal(ids.cpu().numpy(), d2.cpu().numpy(), rid, rd2, what=f"offset {off}")
+            st, bits = world.status()
+            assert st == knnq.KNN_ERR_DEVICE_INPUT, (st, bits)
+            assert bits & knnq.ERR_BAD_UPDATE_ID and bits & knnq.ERR_NONFINITE_UPDATE
+        finally:
+            world.close()
+
+
 def test_one_query_per_object_and_near_misses():
     # as many queries as objects, counted by issuer id: a permutation of the
     # objects (each queries once: the query offsets are the identity and their
