@@ -199,17 +199,22 @@ extern "C" knn_status knn_batch_tick(int32_t n_worlds, const knn_world *worlds,
     if (st != KNN_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
 
-    // Shape: the plan of every world (and whether updates run) fixes the graph's nodes.
+    // Shape: the plan of every world (and whether updates run) fixes the graph's
+    // nodes; the world's uid and scratch generation pin the pointers recorded
+    // in it (a world destroyed and created again at the same handle address,
+    // or whose scratch moved, is recorded again).
     std::vector<int> shape;
     std::vector<knnq::Plan> plans;
-    shape.reserve(8 * n_worlds);
+    shape.reserve(11 * n_worlds);
     plans.reserve(n_worlds);
     for (int32_t i = 0; i < n_worlds; ++i) {
         const knnq::Plan p = knnq::plan_for(worlds[i]->w, args[i].n_q, args[i].k);
         plans.push_back(p);
+        const knnq::World &wi = worlds[i]->w;
         shape.insert(shape.end(), {p.th, p.G, p.Gp, (int)p.wide, (int)p.gather,
                                    args[i].n_upd > 0, args[i].q_x_dev != nullptr,
-                                   args[i].n_q > 0});
+                                   args[i].n_q > 0, (int)(wi.uid & 0x7fffffffu),
+                                   (int)(wi.uid >> 31), (int)wi.scratch_gen});
     }
     bool reuse = g.exec && (int32_t)g.worlds.size() == n_worlds && g.shape == shape;
     for (int32_t i = 0; reuse && i < n_worlds; ++i)

@@ -1,5 +1,6 @@
 // C ABI (include/knn.h): argument validation, the world's device arena, the
 // order of the per-tick stages, host-buffer ticks, status and introspection.
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -166,6 +167,7 @@ void world_attach_scratch(World &w, void *base, cudaStream_t s) {
         t.exec = nullptr;
     }
     w.arena = base;
+    ++w.scratch_gen;
     carve_scratch(w, static_cast<char *>(base));
     cudaMemsetAsync(w.scalars, 0, sizeof(int32_t) * kNumScalars, s);
     // look-back status words must not hold anything that could match a live epoch
@@ -191,6 +193,8 @@ knn_status world_init_resident(World &w, const knn_world_desc *desc, const float
         return fail(KNN_ERR_INVALID, "world: max_queries outside [0, 2^30]");
     if (!x_dev || !y_dev) return fail(KNN_ERR_INVALID, "world: NULL positions");
     cudaGetDevice(&w.device);
+    static std::atomic<uint64_t> next_uid{0};
+    w.uid = ++next_uid;
     w.desc = *desc;
     w.n = n;
     w.L = desc->max_depth > 0 ? desc->max_depth : knnq::default_max_depth(n);

@@ -67,6 +67,11 @@ struct TickGraph {
 constexpr int kTickGraphs = 16;
 
 struct World {
+    // unique per world created in this process, and bumped whenever the tick
+    // scratch moves: a recorded batch that holds the world's pointers is valid
+    // only for the (uid, scratch_gen) it was recorded with
+    uint64_t uid = 0;
+    uint32_t scratch_gen = 0;
     int device = 0;
     knn_world_desc desc{};
     int64_t n = 0;

@@ -209,3 +209,36 @@ def test_batch_autotune_keeps_rows_exact_and_settings():
     finally:
         for w in worlds:
             w.close()
+
+
+def test_batch_after_a_world_is_replaced():
+    # a batch recorded with world B, then B destroyed and a new world of the
+    # same size created (possibly at the same handle address) and batched with
+    # the same argument buffers: the batch is recorded again, rows stay exact
+    torch, dev = torch_dev()
+    r = np.random.default_rng(31)
+    n = 20_000
+    xa, ya = r.random(n).astype(np.float32), r.random(n).astype(np.float32)
+    xb, yb = r.random(n).astype(np.float32), r.random(n).astype(np.float32)
+    q = to_dev(np.arange(n, dtype=np.int32))
+    out = [(torch.empty((n, 8), dtype=torch.int32, device=dev),
+            torch.empty((n, 8), dtype=torch.float32, device=dev)) for _ in range(2)]
+    args = [knnq.tick_args(8, q, out_ids=o[0], out_d2=o[1]) for o in out]
+    a = knnq.World(to_dev(xa), to_dev(ya), k_max=8, max_queries=n)
+    b = knnq.World(to_dev(xb), to_dev(yb), k_max=8, max_queries=n)
+    try:
+        s = torch.cuda.current_stream().cuda_stream
+        knnq.knn_batch_tick([a.handle, b.handle], args, s)
+        torch.cuda.synchronize()
+        b.close()
+        xc, yc = r.random(n).astype(np.float32), r.random(n).astype(np.float32)
+        b = knnq.World(to_dev(xc), to_dev(yc), k_max=8, max_queries=n)
+        for _ in range(2):
+            knnq.knn_batch_tick([a.handle, b.handle], args, s)
+            torch.cuda.synchronize()
+            for (x, y), (oi, od) in zip(((xa, ya), (xc, yc)), out):
+                rid, rd2, _ = oracle.knn(x, y, np.arange(n, dtype=np.int32), 8)
+                assert_rows_equal(oi.cpu().numpy(), od.cpu().numpy(), rid, rd2)
+    finally:
+        a.close()
+        b.close()
