@@ -242,3 +242,32 @@ def test_batch_after_a_world_is_replaced():
     finally:
         a.close()
         b.close()
+
+
+def test_batch_of_more_than_1024_worlds_in_one_class():
+    # the device prefix over a class's worlds runs 1024 worlds at a time: 1100
+    # small worlds of one list size, every row against the oracle
+    torch, dev = torch_dev()
+    r = np.random.default_rng(41)
+    nw = 1100
+    sizes = r.integers(20, 120, nw)
+    worlds, data = [], []
+    try:
+        for i, n in enumerate(sizes):
+            x, y = r.random(n).astype(np.float32), r.random(n).astype(np.float32)
+            q = np.arange(n, dtype=np.int32)
+            oi = torch.empty((n, 4), dtype=torch.int32, device=dev)
+            od = torch.empty((n, 4), dtype=torch.float32, device=dev)
+            worlds.append(knnq.World(to_dev(x), to_dev(y), k_max=4, max_queries=int(n)))
+            data.append((x, y, q, to_dev(q), oi, od))
+        args = [knnq.tick_args(4, dq, out_ids=oi, out_d2=od) for (_, _, _, dq, oi, od) in data]
+        s = torch.cuda.current_stream().cuda_stream
+        for _ in range(2):  # recorded, then replayed
+            knnq.knn_batch_tick([w.handle for w in worlds], args, s)
+            torch.cuda.synchronize()
+        for i, (x, y, q, _, oi, od) in enumerate(data):
+            rid, rd2, _ = oracle.knn(x, y, q, 4)
+            assert_rows_equal(oi.cpu().numpy(), od.cpu().numpy(), rid, rd2, what=f"world {i}")
+    finally:
+        for w in worlds:
+            w.close()
