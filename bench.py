@@ -211,7 +211,7 @@ def rows_vs_oracle(x, y, q_id, k, ids, d2, count=256, seed=0):
                 and np.array_equal(d2[rows].view(np.uint32), rd2.view(np.uint32)))
 
 
-def serving_config5(dev, n_worlds=64, loads=(0.5, 0.8, 0.95), n_req=1000, n_slots=4, seed=5,
+def serving_config5(dev, n_worlds=64, loads=(0.5, 0.8, 0.95), n_req=1000, n_slots=8, seed=5,
                     check=True):
     """The serving workload: a Poisson stream of tick requests over 64 resident
     clustered worlds (10k-4M objects, k up to 64, 10-100 % of the objects query),
