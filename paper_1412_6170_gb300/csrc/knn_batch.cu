@@ -179,6 +179,7 @@ extern "C" knn_status knn_batch_tick(int32_t n_worlds, const knn_world *worlds,
     if (n_worlds < 0 || (n_worlds > 0 && (!worlds || !args)))
         return bad(KNN_ERR_INVALID, "knn_batch_tick: bad world list");
     if (n_worlds == 0) return KNN_OK;
+    knnq::NvtxRange range("knnq batch_tick");
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) return bad(KNN_ERR_CUDA, "knn_batch_tick: bad device");
@@ -221,6 +222,7 @@ extern "C" knn_status knn_batch_tick(int32_t n_worlds, const knn_world *worlds,
         reuse = g.worlds[i] == worlds[i] && same_args(g.args[i], args[i]);
 
     if (!reuse) {
+        knnq::NvtxRange rec("knnq batch record");
         // a failed record below must not leave an older recording replayable
         g.worlds.clear();
         g.shape.clear();
@@ -341,6 +343,7 @@ extern "C" knn_status knn_world_autotune(knn_world h, const int32_t *q_id_dev,
                                          float *out_d2_dev, int32_t trials, knn_tuning *chosen,
                                          void *stream) {
     if (!h) return bad(KNN_ERR_INVALID, "knn_world_autotune: NULL world");
+    knnq::NvtxRange range("knnq world_autotune");
     World &w = h->w;
     knn_tick_args a{nullptr, nullptr, nullptr, 0, q_id_dev, q_x_dev, q_y_dev, n_q, k,
                     out_ids_dev, out_d2_dev, nullptr};
@@ -477,6 +480,7 @@ extern "C" knn_status knn_batch_autotune(int32_t n_worlds, const knn_world *worl
     if (n_worlds == 0) return KNN_OK;
     for (int32_t i = 0; i < n_worlds; ++i)
         if (!worlds[i]) return bad(KNN_ERR_INVALID, "knn_batch_autotune: NULL world");
+    knnq::NvtxRange range("knnq batch_autotune");
     if (trials < 1) trials = 1;
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<knn_tick_args> a(args, args + n_worlds);

@@ -411,13 +411,23 @@ void enqueue_tick(World &w, const knn_tick_args &a, cudaStream_t s, bool marks, 
     const bool m = marks && w.profiling;
     launch_tick_begin(w, p, s);
     if (m) mark(w, 0, s);
-    launch_updates(w, a.upd_id_dev, a.upd_x_dev, a.upd_y_dev, a.n_upd, s);
+    {
+        NvtxRange r("knnq a1 updates");
+        launch_updates(w, a.upd_id_dev, a.upd_x_dev, a.upd_y_dev, a.n_upd, s);
+    }
     if (m) mark(w, 1, s);
-    if (p.reuse_age > 0) launch_index_reuse(w, p, s);  // on reuse ticks; else the sort runs
-    launch_object_sort(w, p, s);
+    {
+        NvtxRange r("knnq a2-a3 keys + sort");
+        if (p.reuse_age > 0) launch_index_reuse(w, p, s);  // on reuse ticks; else the sort runs
+        launch_object_sort(w, p, s);
+    }
     if (m) mark(w, 2, s);
-    launch_leaves(w, p, s);
+    {
+        NvtxRange r("knnq a4-a5 leaves");
+        launch_leaves(w, p, s);
+    }
     if (m) mark(w, 3, s);
+    NvtxRange rq("knnq a6 query order, a7-a8 expansion");
     if (a.n_q > 0) {
         if (a.q_x_dev == nullptr)
             launch_queries_at_issuers(w, p, a.q_id_dev, a.n_q, a.k, a.out_ids_dev,
@@ -529,6 +539,7 @@ knn_status knn_tick(knn_world h, const int32_t *upd_id, const float *upd_x, cons
                     int64_t n_upd, const int32_t *q_id, const float *q_x, const float *q_y,
                     int64_t n_q, int32_t k, int32_t *out_ids, float *out_d2, void *stream) {
     if (!h) return fail(KNN_ERR_INVALID, "knn_tick: NULL world");
+    knnq::NvtxRange range("knnq tick");
     knn_tick_args a{upd_id, upd_x, upd_y, n_upd, q_id, q_x, q_y, n_q, k, out_ids, out_d2,
                     nullptr};
     const knn_status st = knnq::check_tick_args(h->w, a, "knn_tick");
@@ -540,6 +551,7 @@ knn_status knn_tick(knn_world h, const int32_t *upd_id, const float *upd_x, cons
 
 knn_status knn_tick_ex(knn_world h, const knn_tick_args *args, void *stream) {
     if (!h || !args) return fail(KNN_ERR_INVALID, "knn_tick_ex: NULL argument");
+    knnq::NvtxRange range("knnq tick");
     const knn_status st = knnq::check_tick_args(h->w, *args, "knn_tick_ex");
     if (st != KNN_OK) return st;
     World &w = h->w;
@@ -676,6 +688,7 @@ knn_status knn_tick_host_submit(knn_world h, const int32_t *upd_id, const float 
                                 int32_t *out_ids, float *out_d2, void *stream,
                                 int64_t *ticket) {
     if (!h || !ticket) return fail(KNN_ERR_INVALID, "knn_tick_host_submit: NULL argument");
+    knnq::NvtxRange range("knnq tick_host_submit");
     World &w = h->w;
     const bool explicit_q = q_x != nullptr;
     if (n_upd > 0 && (!upd_id || !upd_x || !upd_y))

@@ -3,10 +3,21 @@
 
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "knn.h"
 
 namespace knnq {
+
+// A named range on the host timeline for profilers that read NVTX (a push at
+// construction, a pop at destruction; without a profiler attached each is a
+// test of one function pointer).  The library's ranges are named "knnq ...".
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 constexpr int kMaxK = 512;        // largest k of any tick
 constexpr int kMaxPacketK = 64;   // largest k of the packet expansion kernel

@@ -154,6 +154,7 @@ struct knn_server_s {
                 Slot &sl = slots[free_slot];
                 if (!ensure_scratch(*pick, sl.stream)) break;  // wait for memory
                 Request &r = requests[pick_id];
+                knnq::NvtxRange range("knnq serve tick");
                 knnq::tick_launch(pick->h.w, r.args, sl.stream);  // replays a recorded tick
                 cudaEventRecord(sl.done, sl.stream);
                 sl.request = pick_id;

@@ -136,6 +136,7 @@ extern "C" knn_status knn_query_static(const knn_world_desc *desc, const float *
                                        const float *q_x_dev, const float *q_y_dev, int64_t n_q,
                                        int32_t k, int32_t *out_ids_dev, float *out_d2_dev,
                                        void *stream) {
+    knnq::NvtxRange range("knnq query_static");
     if (!desc) return bad(KNN_ERR_INVALID, "NULL desc");
     if (!(desc->side > 0.f) || !std::isfinite(desc->side) || !std::isfinite(desc->x0) ||
         !std::isfinite(desc->y0))
