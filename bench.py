@@ -930,7 +930,7 @@ def run_gpu(args):
     h_oid = torch.empty((N_OBJ, K), dtype=torch.int32).pin_memory()
     h_od = torch.empty((N_OBJ, K), dtype=torch.float32).pin_memory()
     vp = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
-    e2e_steps = max(3, min(args.steps, 10))
+    e2e_steps = max(3, min(args.steps, 20))
 
     def e2e_run(mode):
         # mode: how knn_tick_host uses the pinned arrays (bit 0 rows written in
@@ -973,10 +973,15 @@ def run_gpu(args):
         knnq.knn_tick_host_wait(world.handle, prev)
 
     e2e_pipelined(3)  # warm-up (allocates the two staging slots, records the graphs)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    e2e_pipelined(e2e_steps)
-    e2e_total = max_over_ranks([time.perf_counter() - t0], dist, dev)[0]
+    # three timed runs (fill and drain inside each); the median is reported, so
+    # one host-side hiccup in a run of a few milliseconds does not decide it
+    e2e_runs = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_pipelined(e2e_steps)
+        e2e_runs.append(max_over_ranks([time.perf_counter() - t0], dist, dev)[0])
+    e2e_total = sorted(e2e_runs)[1]
     e2e_modes = {"pipelined": e2e_total, **e2e_modes}
     # the rows that reached host memory in the last pipelined step, against
     # the oracle (every object moves every tick, so that tick's inputs alone
@@ -1049,8 +1054,10 @@ def run_gpu(args):
                 "d2h_bytes_per_step": N_OBJ * K * 8,
                 "api": "knn_tick_host_submit + knn_tick_host_wait (pinned host buffers, "
                        "two ticks in flight: each step's inputs copied in and rows copied "
-                       "out inside the timed region, overlapping the next step's search); "
+                       "out inside the timed region, overlapping the next step's search; "
+                       "the median of three timed runs of the same steps); "
                        "by_mode adds the synchronous knn_tick_host",
+                "pipelined_runs_s": e2e_runs,
                 "by_mode": {m: replicas_value(n_gpus, N_OBJ * e2e_steps, t)
                             for m, t in e2e_modes.items()},
                 "exact_spot_check": e2e_spot},
