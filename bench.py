@@ -460,7 +460,8 @@ def skewed_config3(dev, ticks=10, rounds=3, seed=0, check=True):
                 b.record(stream)
                 b.synchronize()
                 ms.append(a.elapsed_time(b))
-                exp_ms.append(world.stage_times()["expand"])
+                st_k = world.stage_times()
+                exp_ms.append(st_k["expand"] + st_k["pass-on"])
         ok = None
         if check:
             t = w.ticks[ticks - 1]
@@ -529,9 +530,11 @@ def index_reuse_vs_rebuild(dev, ticks=20, max_age=8):
 
 
 def expansion_ablation(dev, ticks=3):
-    """The headline workload's expansion in each form: gathered packets (the
-    default for k = 16), packets walking the quadtree, one warp per query, and
-    the paper's multi-pass iterative form; tick times and whether the rows agree."""
+    """The headline workload's expansion in each form: tiles (the default for
+    k = 16), gathered packets, packets walking the quadtree, one warp per query,
+    and the paper's multi-pass iterative form; tick times, the first expansion
+    kernel's time and the time of what finishes the packets it passed on, and
+    whether the rows agree."""
     import torch
 
     from paper_1412_6170_gb300 import knnq, synth
@@ -541,8 +544,8 @@ def expansion_ablation(dev, ticks=3):
     uy = [torch.from_numpy(t.upd_y).to(dev) for t in wl.ticks]
     stream = torch.cuda.current_stream()
     out, rows = {}, {}
-    for name, exp in (("gathered packets", 4), ("packets", 1), ("warp per query", 2),
-                      ("multi-pass iterative", 3)):
+    for name, exp in (("tiles", 5), ("gathered packets", 4), ("packets", 1),
+                      ("warp per query", 2), ("multi-pass iterative", 3)):
         x0, y0 = torch.from_numpy(wl.x0).to(dev), torch.from_numpy(wl.y0).to(dev)
         world = knnq.World(x0, y0, k_max=K, max_queries=N_OBJ)
         world.set_tuning(expansion=exp)
@@ -551,13 +554,15 @@ def expansion_ablation(dev, ticks=3):
         od = torch.empty((N_OBJ, K), dtype=torch.float32, device=dev)
         try:
             world.tick(K, ids, ids, ux[0], uy[0], out_ids=oi, out_d2=od)
-            tick_ms, exp_ms = [], []
+            tick_ms, exp_ms, pass_ms = [], [], []
             for i in range(ticks):
                 world.tick(K, ids, ids, ux[1 - i % 2], uy[1 - i % 2], out_ids=oi, out_d2=od)
                 st = world.stage_times()
                 tick_ms.append(sum(st.values()))
                 exp_ms.append(st["expand"])
-            out[name] = {"tick_ms": min(tick_ms), "expand_ms": min(exp_ms)}
+                pass_ms.append(st["pass-on"])
+            out[name] = {"tick_ms": min(tick_ms), "expand_ms": min(exp_ms),
+                         "pass_on_ms": min(pass_ms)}
             rows[name] = (oi.cpu(), od.cpu())
         finally:
             world.close()
@@ -1011,8 +1016,9 @@ def run_gpu(args):
     exp_ms = stage_sums["expand"] / args.steps
     hbm, hbm_kind = peaks()
     achieved = ALGO_BYTES_PER_QUERY * N_OBJ / (exp_ms / 1e3) / 1e9
-    kernel, source = ("k_expand_gather", "knn_expand_gather.cu") if form == 4 else \
-        ("k_expand", "knn_expand.cu")
+    kernel, source = {5: ("k_expand_tile", "knn_expand_tile.cu"),
+                      4: ("k_expand_gather", "knn_expand_gather.cu")}.get(
+                          form, ("k_expand", "knn_expand.cu"))
     prof = expand_profile(kernel, source)
     traffic = None if prof is None else prof["traffic"]
     n_sms = torch.cuda.get_device_properties(dev).multi_processor_count

@@ -302,7 +302,15 @@ knn_status knn_brute_force(const float *x_dev, const float *y_dev, int64_t n,
  *   the paper's multi-pass form (Section 4.2: first iteration on the query's
  *   own cell, then alternating left/right Morton sub-visits, one cell per
  *   iteration; k <= 64), an ablation with the same rows, never recorded in a
- *   tick graph.  The automatic choice is 4 for k <= 32 and 2 above.
+ *   tick graph; 5 = tiles (9 <= k <= 32, queries at their issuers; other
+ *   ticks run form 4): one thread block per packet-level cell of the sorted
+ *   queries stages the objects around the cell in shared memory once
+ *   (counting-sorted into a fine grid) and each lane scans only its own
+ *   query's search box, nearest rows first, shrinking it as its k-th
+ *   distance tightens (Alg. 1's per-cell scan); packets it cannot finish
+ *   exactly (equal distances, a cell too full to stage) go to form 4, which
+ *   finishes them.  The automatic choice is 4 for k <= 8, 5 for 9 <= k <= 32
+ *   and 2 above.
  * Any field set to 0 keeps (or restores) the automatic choice. */
 typedef struct {
     int32_t leaf_capacity;
@@ -419,7 +427,9 @@ knn_status knn_world_set_graphs(knn_world w, int32_t enable);
  * finished, *handed_back = packets it handed to the packet walk (no object
  * near the packet, a search box of more than 4096 cells, or queries still
  * short of k objects after two thresholds); both 0 unless the tick used the
- * gathered form.  Either may be NULL.  Rows are identical either way. */
+ * gathered form.  After the tiled form the gathered form only sees the
+ * packets the tiles passed on, so the two counts add up to those.  Either may
+ * be NULL.  Rows are identical either way. */
 knn_status knn_world_expand_info(knn_world w, int64_t *gathered, int64_t *handed_back);
 
 /* Records the graph of a tick with these arguments without running it, so
@@ -433,7 +443,10 @@ knn_status knn_world_record_tick(knn_world w, const knn_tick_args *args);
 /* Per-stage device times of ticks.  When enabled, each tick records CUDA
  * events around its stages on its stream; knn_world_stage_times synchronizes
  * and writes up to n_stages milliseconds for the last tick.  Stage names come
- * from knn_stage_name (NULL past the last stage). */
+ * from knn_stage_name (NULL past the last stage): update, keys+sort, leaves,
+ * query order, packets, expand (the tick's first expansion kernel) and
+ * pass-on (the kernels that finish the packets it passed on: the gathered
+ * form after the tiled one, the packet walk after the gathered one). */
 knn_status knn_world_set_profiling(knn_world w, int32_t enable);
 knn_status knn_world_stage_times(knn_world w, float *ms_host, int32_t n_stages);
 const char *knn_stage_name(int32_t i);

@@ -21,7 +21,8 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libknnq.so")
 DEBUG_DIR = os.path.join(HERE, "_build_debug")
 DEBUG_LIB = os.path.join(DEBUG_DIR, "libknnq.so")
-SOURCES = ["knn_index.cu", "knn_expand.cu", "knn_expand_gather.cu", "knn_expand_wide.cu",
+SOURCES = ["knn_index.cu", "knn_expand.cu", "knn_expand_gather.cu", "knn_expand_tile.cu",
+           "knn_expand_wide.cu",
            "knn_expand_iter.cu",
            "knn_brute.cu", "knn_capi.cu", "knn_static.cu", "knn_batch.cu", "knn_server.cu"]
 HEADERS = ["knn_device.cuh", "knn_internal.h"]

@@ -29,9 +29,12 @@ knn_status cuda_fail(cudaError_t e, const char *what) {
     return fail(KNN_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+// "expand" is the tick's first expansion kernel; "pass-on" the kernels that
+// finish what it passed on (the gathered form after the tiled one, the packet
+// walk after the gathered one; empty for the other forms).
 const char *kStageNames[] = {"update", "keys+sort", "leaves", "query order", "packets",
-                             "expand"};
-constexpr int kNumStages = 6;
+                             "expand", "pass-on"};
+constexpr int kNumStages = 7;
 
 int round_log4(double v) {
     if (v <= 1.0) return 0;
@@ -71,7 +74,14 @@ Plan make_plan(const World &w, int64_t n_q, int k) {
     // ms for the walk; 4M clustered objects, a quarter querying, k = 32: 1.53
     // against 1.58 ms)
     p.gather = !p.iterative && !p.wide && k <= knnq::kMaxPacketK &&
-               (w.tuning.expansion == 4 || (w.tuning.expansion == 0 && k <= 32));
+               (w.tuning.expansion == 4 || w.tuning.expansion == 5 ||
+                (w.tuning.expansion == 0 && k <= 32));
+    // the tiled form (queries at issuers; the gathered form finishes what it
+    // passes on) for 9 <= k <= 32, with about 200 queries per tile
+    p.tile = p.gather && k >= 9 && k <= 32 &&
+             (w.tuning.expansion == 5 || w.tuning.expansion == 0);
+    if (p.tile && w.tuning.packet_level <= 0)
+        p.Gp = clampi(round_log4((double)(n_q > 0 ? n_q : 1) / 200.0), 0, p.G);
     p.by_id = 2 * n_q >= w.n;
     p.reuse_age = w.reuse_age;
     p.reuse_f16 = w.reuse_factor > 0.f ? (int)std::lround(w.reuse_factor * 16.f) : 0;
@@ -437,19 +447,41 @@ void enqueue_tick(World &w, const knn_tick_args &a, cudaStream_t s, bool marks, 
                                     a.out_ids_dev, a.out_d2_dev, s);
     }
     if (m) mark(w, 4, s);
-    if (a.n_q > 0 && !p.wide && !p.iterative) launch_packets(w, p, a.n_q, s);
+    // the tiled form takes the level-Gp cells of the sorted queries directly
+    // and cuts packets only for what it passes on
+    const bool tile = p.tile && expand && a.q_x_dev == nullptr;
+    if (a.n_q > 0 && !p.wide && !p.iterative) {
+        if (tile) launch_query_cells(w, p, a.n_q, s);
+        else launch_packets(w, p, a.n_q, s);
+    }
     if (m) mark(w, 5, s);
     if (a.n_q > 0 && expand) {
-        if (p.gather)
-            launch_expand_gather(w, p, a.k, a.n_q, a.out_ids_dev, a.out_d2_dev, a.q_k_dev, s);
-        else if (p.iterative)
-            launch_expand_iter(w, p, a.k, a.n_q, a.out_ids_dev, a.out_d2_dev, a.q_k_dev, s);
-        else if (p.wide)
-            launch_expand_wide(w, p, a.k, a.n_q, a.out_ids_dev, a.out_d2_dev, a.q_k_dev, s);
-        else
-            launch_expand(w, p, a.k, a.n_q, a.out_ids_dev, a.out_d2_dev, a.q_k_dev, s);
+        if (p.gather) {
+            if (tile)
+                launch_expand_tile(w, p, a.k, a.n_q, a.out_ids_dev, a.out_d2_dev, a.q_k_dev, s);
+            else
+                launch_expand_gather(w, p, a.k, a.n_q, a.out_ids_dev, a.out_d2_dev, a.q_k_dev, s,
+                                     false);
+            if (m) mark(w, 6, s);
+            if (tile)
+                launch_expand_gather(w, p, a.k, a.n_q, a.out_ids_dev, a.out_d2_dev, a.q_k_dev, s,
+                                     false);
+            launch_expand_handed_back(w, p, a.k, a.n_q, a.out_ids_dev, a.out_d2_dev, a.q_k_dev,
+                                      s);
+        }
+        else {
+            if (p.iterative)
+                launch_expand_iter(w, p, a.k, a.n_q, a.out_ids_dev, a.out_d2_dev, a.q_k_dev, s);
+            else if (p.wide)
+                launch_expand_wide(w, p, a.k, a.n_q, a.out_ids_dev, a.out_d2_dev, a.q_k_dev, s);
+            else
+                launch_expand(w, p, a.k, a.n_q, a.out_ids_dev, a.out_d2_dev, a.q_k_dev, s);
+            if (m) mark(w, 6, s);
+        }
+    } else if (m) {
+        mark(w, 6, s);
     }
-    if (m) mark(w, 6, s);
+    if (m) mark(w, 7, s);
     w.last_stream = s;
     w.last_plan = p;
 }
@@ -519,8 +551,8 @@ knn_status knn_world_set_tuning(knn_world h, const knn_tuning *t) {
         return fail(KNN_ERR_INVALID, "grid_level outside [0, %d] for this world", h->w.gmax);
     if (t->packet_level < 0 || t->packet_level > knnq::kMaxGridLevel)
         return fail(KNN_ERR_INVALID, "packet_level outside [0, 10]");
-    if (t->expansion < 0 || t->expansion > 4)
-        return fail(KNN_ERR_INVALID, "expansion outside [0, 4]");
+    if (t->expansion < 0 || t->expansion > 5)
+        return fail(KNN_ERR_INVALID, "expansion outside [0, 5]");
     h->w.tuning = *t;
     return KNN_OK;
 }
@@ -531,7 +563,7 @@ knn_status knn_world_get_tuning(knn_world h, int64_t n_q, int32_t k, knn_tuning 
     out->leaf_capacity = p.th;
     out->grid_level = p.G;
     out->packet_level = p.Gp;
-    out->expansion = p.iterative ? 3 : (p.wide ? 2 : (p.gather ? 4 : 1));
+    out->expansion = p.iterative ? 3 : (p.wide ? 2 : (p.tile ? 5 : (p.gather ? 4 : 1)));
     return KNN_OK;
 }
 

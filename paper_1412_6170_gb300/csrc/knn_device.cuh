@@ -131,6 +131,22 @@ __device__ __forceinline__ void merge_batch(unsigned long long (&a)[KC],
     }
 }
 
+// Two binary32 operations at once (sm_100 packed pairs): each half is rounded
+// to nearest on its own, like the scalar operation.
+__device__ __forceinline__ unsigned long long f2sub(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long f2mul(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long f2pack(float lo, float hi) {
+    return ((unsigned long long)__float_as_uint(hi) << 32) | __float_as_uint(lo);
+}
+
 // Level-G cell of a coordinate, with the same monotone rounding as the keys.
 __device__ __forceinline__ int cell_g(float v, float v0, float scale, int G) {
     const float t = __fmul_rn(__fsub_rn(v, v0), scale);

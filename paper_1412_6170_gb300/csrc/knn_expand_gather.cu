@@ -122,22 +122,6 @@ __device__ __forceinline__ void gmerge(GLane<KC> &L, GatherSmem<KC> &sm, int lan
     L.thr = fminf(L.thr, __uint_as_float((uint32_t)(L.lst[KC - 1] >> 32)));
 }
 
-// Two binary32 operations at once (sm_100 packed pairs): each half is rounded
-// to nearest on its own, like the scalar operation.
-__device__ __forceinline__ unsigned long long f2sub(unsigned long long a, unsigned long long b) {
-    unsigned long long r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ unsigned long long f2mul(unsigned long long a, unsigned long long b) {
-    unsigned long long r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ unsigned long long f2pack(float lo, float hi) {
-    return ((unsigned long long)__float_as_uint(hi) << 32) | __float_as_uint(lo);
-}
-
 // Float bits mapped to an unsigned key of the same order (for warp min/max by
 // one integer reduction), and back.
 __device__ __forceinline__ uint32_t ord_key(float x) {
@@ -844,7 +828,7 @@ static GatherArgs gather_args(World &w, const Plan &p, int32_t k, int64_t n_q, i
 }
 
 void launch_expand_gather(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t *out_ids,
-                          float *out_d2, const int32_t *q_k, cudaStream_t s) {
+                          float *out_d2, const int32_t *q_k, cudaStream_t s, bool then_walk) {
     if (n_q <= 0) return;
     const GatherArgs a = gather_args(w, p, k, n_q, out_ids, out_d2, q_k);
     if (k <= 4) run_gather<4>(a, w.device, s);
@@ -854,7 +838,7 @@ void launch_expand_gather(World &w, const Plan &p, int32_t k, int64_t n_q, int32
     else run_gather<64>(a, w.device, s);
     ++w.launches;
     // the packets handed back, through the packet walk
-    launch_expand_handed_back(w, p, k, n_q, out_ids, out_d2, q_k, s);
+    if (then_walk) launch_expand_handed_back(w, p, k, n_q, out_ids, out_d2, q_k, s);
 }
 
 // ---------------------------------------------------------------------------

@@ -1,0 +1,669 @@
+// a7 + a8, tiled form -- per-query expansion with top-k and the covered-disc
+// check, and the rows in caller order (Sections 4.2.1-4.2.2, Alg. 1).
+//
+// One block serves one level-Gp cell of the sorted queries (a tile; queries
+// at their issuers only).  The block first stages, once for all of the tile's
+// queries, every object of the level-G cells within a margin H of the tile's
+// queries (the paper's per-cell shared scan of Alg. 1, with the neighbouring
+// cells' objects brought in once per cell instead of once per query): the
+// objects are counting-sorted in shared memory into a row-major grid of
+// micro-cells of about one object each.  Then every lane (one query) scans
+// only its own search box, one micro-cell row at a time, its own row first
+// and then alternately the rows above and below (near objects first), and
+// shrinks the box whenever its threshold tightens (Alg. 1's "keep only what
+// is closer than dist_k").
+//
+// Selection keys are 32-bit: (code of d^2 << 11) | (staged index + 1), where
+// the code is floor(d^2 * 2^21 / t) for the lane's first threshold t, so the
+// compare-exchange networks take two integer min/max instructions.  The code
+// is monotone in d^2, so the 32-bit order is the (d^2, id) order wherever the
+// codes differ.  A lane is exact when the codes of its k keys are distinct
+// and the smallest code it dropped is above its k-th: then its keys are the k
+// nearest by (d^2, id) and in order.  Equal codes (ties or near-ties of d^2),
+// a lane that still holds fewer than k keys after its threshold reached the
+// staged margin, and tiles whose margin holds too many objects go to the
+// gathered form as packets of up to 32 consecutive queries (the packets
+// k_packets would cut), which finishes them exactly.
+//
+// Exactness of the box: every object within a lane's threshold lies in its
+// box (the box bounds round outward), every object of the box is staged, and
+// an object outside the staged margin is at least t_fit away (a bound rounded
+// like the exact distances), so a lane whose threshold stays below t_fit sees
+// every object that can enter its list.
+#include <cstdio>
+#include <cstring>
+
+#include "knn_device.cuh"
+#include "knn_internal.h"
+
+namespace knnq {
+
+namespace {
+
+constexpr int kTileThreads = 256;               // 8 warps; warp w serves packets w, w + 8, ...
+constexpr int kTileWarps = kTileThreads / 32;
+constexpr int kTileObj = 2047;                  // staged objects (index + 1 fits 11 bits)
+constexpr int kTileCells = 1024;                // micro-cells
+constexpr int kTileStage = 256;                 // level-G cells staged per tile
+constexpr int kTileMaxQ = 4096;                 // a tile with more queries goes to the gathered form
+constexpr int kTileSlots = 16;                  // candidate buffer slots per lane
+constexpr int kTileFlush = kTileSlots - kBatch; // a merge as soon as one lane holds a batch
+constexpr uint32_t kPad32 = 0xFFFFFFFFu;        // empty slot (above every real key)
+constexpr float kCodeMax = 2097150.f;           // 2^21 - 2: largest distance code
+
+struct TileArgs {
+    const float *xs, *ys;
+    const int32_t *sid;
+    const int32_t *cb;
+    const int32_t *bstart;
+    const float *qs_x, *qs_y;
+    const int32_t *qs_id, *qs_orig;
+    const int32_t *qcs;
+    int32_t *scalars;
+    uint32_t *tile_counter;
+    int32_t *pk_start, *pk_len;  // packets passed to the gathered form
+    int32_t *out_ids;
+    float *out_d2;
+    const int32_t *q_k;
+    uint32_t *err;
+    float x0, y0, side, scale_g;
+    int G, Gp, k;
+    int vec_out;
+    int64_t n, n_q, pk_cap, leaf_cap;
+};
+
+struct TileSmem {
+    float2 xy[kTileObj + 1];   // staged objects in micro-cell order
+    int32_t id[kTileObj + 1];
+    int32_t cs[kTileCells + 1];     // first staged object of each micro-cell (counts while sorting)
+    int32_t gofs[kTileStage + 1];   // first staged index of each staged level-G cell
+    int32_t goa[kTileStage];        // and its first object in the leaf-ordered store
+    uint32_t buf[kTileSlots][kTileThreads];  // candidate keys [slot][thread]
+    float red[4][kTileWarps];
+    uint32_t scan_tmp[8];
+    uint32_t scan_total;
+    uint32_t ticket;
+    float hx0, hx1, hy0, hy1;  // the staged margin (a box around the tile's queries)
+    float iw, ih;              // micro-cells per unit length
+    float rho;                 // the tile's object density
+    int nmx, nmy, ngx, ng, gx0, gy0, ok, pk_base;
+};
+
+// Micro-cell coordinate of v in a grid starting at v0 with `inv` cells per
+// unit length and n cells: monotone in v (clamped at both ends).
+__device__ __forceinline__ int mcell(float v, float v0, float inv, int n) {
+    const float t = __fmul_rn(__fsub_rn(v, v0), inv);
+    if (!(t >= 0.0f)) return 0;
+    if (t >= (float)n) return n - 1;
+    return (int)t;
+}
+
+__device__ __forceinline__ void cmpx32(uint32_t &x, uint32_t &y) {
+    const uint32_t lo = min(x, y);
+    y = max(x, y);
+    x = lo;
+}
+
+// Sort 8 keys ascending (the 19-comparator network of sort8).
+__device__ __forceinline__ void sort8_32(uint32_t (&b)[kBatch]) {
+    cmpx32(b[0], b[2]); cmpx32(b[1], b[3]); cmpx32(b[4], b[6]); cmpx32(b[5], b[7]);
+    cmpx32(b[0], b[4]); cmpx32(b[1], b[5]); cmpx32(b[2], b[6]); cmpx32(b[3], b[7]);
+    cmpx32(b[0], b[1]); cmpx32(b[2], b[3]); cmpx32(b[4], b[5]); cmpx32(b[6], b[7]);
+    cmpx32(b[2], b[4]); cmpx32(b[3], b[5]);
+    cmpx32(b[1], b[4]); cmpx32(b[3], b[6]);
+    cmpx32(b[1], b[2]); cmpx32(b[3], b[4]); cmpx32(b[5], b[6]);
+}
+
+// a (KC keys, ascending) := the KC smallest of a and b (8 keys, ascending), as
+// merge_batch does; `disc` becomes the smallest key dropped so far.
+template <int KC>
+__device__ __forceinline__ void merge32(uint32_t (&a)[KC], const uint32_t (&b)[kBatch],
+                                        uint32_t &disc) {
+    static_assert(KC >= kBatch, "lists of at least one batch");
+#pragma unroll
+    for (int i = KC - kBatch; i < KC; ++i) {
+        const uint32_t v = b[KC - 1 - i];
+        disc = min(disc, max(v, a[i]));
+        a[i] = min(v, a[i]);
+    }
+#pragma unroll
+    for (int span = KC / 2; span >= 1; span >>= 1) {
+#pragma unroll
+        for (int i = 0; i < KC; ++i)
+            if ((i & span) == 0) cmpx32(a[i], a[i + span]);
+    }
+}
+
+// Exact squared distance from the query (packed qx, qy) to a staged object.
+__device__ __forceinline__ float tile_d2(unsigned long long qq, float2 v) {
+    const unsigned long long o = f2pack(v.x, v.y);
+    const unsigned long long dxy = f2sub(qq, o);
+    const unsigned long long sq = f2mul(dxy, dxy);
+    return __fadd_rn(__uint_as_float((uint32_t)sq), __uint_as_float((uint32_t)(sq >> 32)));
+}
+
+// One packet: the sorted queries q0 .. q0 + ql - 1 of the current tile, lane
+// i owning query q0 + i.  Returns nothing; rows are written, or the packet is
+// passed to the gathered form.
+template <int KC>
+__device__ __forceinline__ void tile_packet(const TileArgs &g, TileSmem &s, int32_t q0, int32_t ql,
+                                            int tid) {
+    const int lane = tid & 31;
+    const float kInf = __int_as_float(0x7f800000);
+    const bool has = lane < ql;
+    const int32_t j = q0 + (has ? lane : 0);
+    const int32_t orig = has ? g.qs_orig[j] : -1;
+    const bool active = has && orig >= 0;
+    const float qx = active ? g.qs_x[j] : 0.f;
+    const float qy = active ? g.qs_y[j] : 0.f;
+    int kq = g.k;
+    if (g.q_k && active) {
+        kq = g.q_k[orig];
+        if (kq < 0 || kq > g.k) {
+            atomicOr(g.err, kErrBadQuery);
+            kq = 0;
+        }
+    }
+    const bool want = active && kq > 0;
+    const float hx0 = s.hx0, hy0 = s.hy0, iw = s.iw, ih = s.ih;
+    const int nmx = s.nmx, nmy = s.nmy;
+    const int mxq = mcell(qx, hx0, iw, nmx), myq = mcell(qy, hy0, ih, nmy);
+
+    bool fail = false;
+    // the issuer's own staged object (its position is the query's, so it sits
+    // in the query's micro-cell); it never enters the list
+    int selfp = -1;
+    if (want) {
+        const int32_t me = g.qs_id[j];
+        const int c = myq * nmx + mxq;
+        const int pe = s.cs[c + 1];
+        for (int p = s.cs[c]; p < pe; ++p)
+            if (s.id[p] == me) selfp = p;
+        if (me >= 0 && selfp < 0) fail = true;
+    }
+    // first threshold: the squared radius holding about k + 4 sqrt(k) + 4
+    // objects at the density of the 7 x 7 micro-cells around the query
+    float t0 = kInf;
+    if (want) {
+        const int xa = max(mxq - 3, 0), xb = min(mxq + 3, nmx - 1);
+        const int ya = max(myq - 3, 0), yb = min(myq + 3, nmy - 1);
+        int cnt = 0;
+        for (int r = ya; r <= yb; ++r) cnt += s.cs[r * nmx + xb + 1] - s.cs[r * nmx + xa];
+        const float cells = (float)((xb - xa + 1) * (yb - ya + 1));
+        const float rho = cnt > 0 ? (float)cnt * iw * ih / cells : s.rho;
+        const float fk = (float)kq;
+        t0 = (fk + 4.f * sqrtf(fk) + 4.f) / (3.14159265f * rho);
+    }
+    // t_fit: an object outside the staged margin is at least this far (in
+    // d^2, rounded like the exact distances); the threshold stays below it
+    float tcap = -1.f;
+    if (want) {
+        const float gx = fminf(__fsub_rd(qx, s.hx0), __fsub_rd(s.hx1, qx));
+        const float gy = fminf(__fsub_rd(qy, s.hy0), __fsub_rd(s.hy1, qy));
+        const float gm = fminf(gx, gy);
+        if (gm > 0.f) {
+            const float tf = __fmul_rd(gm, gm);
+            if (tf > 0.f) tcap = __uint_as_float(__float_as_uint(tf) - 1u);
+        }
+        if (!(tcap > 0.f)) fail = true;
+    }
+    float thr = fminf(t0, tcap);
+    bool ok = !want;
+    uint32_t lst[KC];
+#pragma unroll
+    for (int i = 0; i < KC; ++i) lst[i] = kPad32;
+    uint32_t disc = kPad32;
+    const unsigned long long qq = f2pack(qx, qy);
+
+    for (int attempt = 0; attempt < 3; ++attempt) {
+        bool run = want && !ok && !fail;
+        const float tstart = thr;
+        const float tmax = run ? thr : 1.f;
+        // codes: floor(d^2 * inv) <= kCodeMax for every d^2 <= tmax; a code c
+        // bounds d^2 from above by (c + 1) * rstep (a threshold so small or
+        // large that either factor leaves the normal range goes on)
+        const float inv = __fmul_rd(kCodeMax, __frcp_rd(tmax));
+        const float rstep = __fmul_ru(__frcp_ru(inv), 1.0000002f);
+        if (run && !(inv > 1.0e-30f && inv < 1.0e30f && rstep > 1.0e-30f && rstep < 1.0e30f)) {
+            fail = true;
+            run = false;
+        }
+        if (!__any_sync(kFull, run)) break;
+        if (run) {
+#pragma unroll
+            for (int i = 0; i < KC; ++i) lst[i] = i < KC - kq ? 0u : kPad32;
+            disc = kPad32;
+        }
+        float th = run ? thr : -1.f;
+        int mx_lo = 0, mx_hi = -1, my_lo = 0, my_hi = -1, omax = 0;
+        auto box = [&]() {
+            const float R = __fmul_ru(__fsqrt_ru(th), 1.0000010f);
+            mx_lo = mcell(__fsub_rd(qx, R), hx0, iw, nmx);
+            mx_hi = mcell(__fadd_ru(qx, R), hx0, iw, nmx);
+            my_lo = mcell(__fsub_rd(qy, R), hy0, ih, nmy);
+            my_hi = mcell(__fadd_ru(qy, R), hy0, ih, nmy);
+            omax = 2 * max(myq - my_lo, my_hi - myq);
+        };
+        int p = 0, e = 0, o = 0, cnt = 0;
+        if (run) {
+            box();
+            const int b = myq * nmx;
+            p = s.cs[b + mx_lo];
+            e = s.cs[b + mx_hi + 1];
+        }
+        for (;;) {
+            // the one merge site: the newest batch of every lane
+            if (__any_sync(kFull, cnt >= kTileFlush)) {
+                const int base = cnt > kBatch ? cnt - kBatch : 0;
+                uint32_t bt[kBatch];
+#pragma unroll
+                for (int t = 0; t < kBatch; ++t)
+                    bt[t] = base + t < cnt ? s.buf[base + t][tid] : kPad32;
+                sort8_32(bt);
+                merge32<KC>(lst, bt, disc);
+                cnt = base;
+                const uint32_t last = lst[KC - 1];
+                if (run && last != kPad32) {
+                    const float tf = __fmul_ru((float)((last >> 11) + 1u), rstep);
+                    if (tf < th) {
+                        th = tf;
+                        box();
+                    }
+                }
+                continue;
+            }
+            // next non-empty row of the box: offsets 0, +1, -1, +2, -2, ...
+            while (p >= e && o < omax) {
+                ++o;
+                const int r = myq + ((o & 1) ? ((o + 1) >> 1) : -(o >> 1));
+                if (r >= my_lo && r <= my_hi) {
+                    const int b = r * nmx;
+                    p = s.cs[b + mx_lo];
+                    e = s.cs[b + mx_hi + 1];
+                }
+            }
+            const bool okA = p < e;
+            if (!__any_sync(kFull, okA)) break;
+            const bool okB = p + 1 < e;
+            {
+                const float d = tile_d2(qq, s.xy[okA ? p : 0]);
+                if (okA && d <= th && p != selfp) {
+                    const uint32_t c = __float2uint_rz(__fmul_rn(d, inv));
+                    s.buf[cnt][tid] = (c << 11) | (uint32_t)(p + 1);
+                    ++cnt;
+                }
+            }
+            {
+                const float d = tile_d2(qq, s.xy[okB ? p + 1 : 0]);
+                if (okB && d <= th && p + 1 != selfp) {
+                    const uint32_t c = __float2uint_rz(__fmul_rn(d, inv));
+                    s.buf[cnt][tid] = (c << 11) | (uint32_t)(p + 2);
+                    ++cnt;
+                }
+            }
+            p += 2;
+        }
+        // drain the buffers
+        while (__any_sync(kFull, cnt > 0)) {
+            const int base = cnt > kBatch ? cnt - kBatch : 0;
+            uint32_t bt[kBatch];
+#pragma unroll
+            for (int t = 0; t < kBatch; ++t) bt[t] = base + t < cnt ? s.buf[base + t][tid] : kPad32;
+            sort8_32(bt);
+            merge32<KC>(lst, bt, disc);
+            cnt = base;
+        }
+        if (run) {
+            if (lst[KC - 1] != kPad32) {
+                ok = true;
+            } else if (tstart < tcap) {
+                // fewer than k objects within the threshold: grow it (the disc's
+                // expected count at least doubles past k), up to the margin
+                int found = 0;
+#pragma unroll
+                for (int i = 0; i < KC; ++i) found += (i >= KC - kq && lst[i] != kPad32) ? 1 : 0;
+                const float grow = fmaxf(4.f, 2.f * (float)(kq + 1) / (float)(found + 1));
+                thr = fminf(__fmul_ru(tstart, grow), tcap);
+            } else {
+                fail = true;
+            }
+        }
+    }
+    if (want && !ok) fail = true;
+    if (want && ok) {
+        // distinct codes among the k keys and above them: the order is exact
+        bool strict = (disc >> 11) != (lst[KC - 1] >> 11);
+#pragma unroll
+        for (int i = 0; i + 1 < KC; ++i)
+            if (i >= KC - kq) strict = strict && (lst[i] >> 11) != (lst[i + 1] >> 11);
+        if (!strict) fail = true;
+    }
+    if (__any_sync(kFull, fail)) {
+        if (lane == 0) {
+            const int32_t slot = atomicAdd(g.scalars + kScalarPackets, 1);
+            if (slot >= 0 && slot < g.pk_cap) {
+                g.pk_start[slot] = q0;
+                g.pk_len[slot] = ql;
+            }
+        }
+        return;
+    }
+    // a8: the row of this lane's query in caller order
+    if (!active || !KNN_IN_BOUNDS(orig, 0, g.n_q, g.err)) return;
+    const int k = g.k;
+    int32_t *orow = g.out_ids + (int64_t)orig * k;
+    float *drow = g.out_d2 + (int64_t)orig * k;
+    if (g.vec_out && k == KC && kq == KC) {
+#pragma unroll
+        for (int i = 0; i < KC; i += 4) {
+            int32_t idv[4];
+            float dv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                int x = (int)(lst[i + u] & 0x7FFu) - 1;
+                if (!KNN_IN_BOUNDS(x, 0, kTileObj, g.err)) x = 0;
+                idv[u] = s.id[x];
+                dv[u] = tile_d2(qq, s.xy[x]);
+            }
+            *reinterpret_cast<int4 *>(orow + i) = make_int4(idv[0], idv[1], idv[2], idv[3]);
+            *reinterpret_cast<float4 *>(drow + i) = make_float4(dv[0], dv[1], dv[2], dv[3]);
+        }
+    } else {
+#pragma unroll
+        for (int sl = 0; sl < KC; ++sl) {
+            const int i = sl - (KC - kq);
+            if (i >= 0) {
+                int x = (int)(lst[sl] & 0x7FFu) - 1;
+                if (!KNN_IN_BOUNDS(x, 0, kTileObj, g.err)) x = 0;
+                orow[i] = s.id[x];
+                drow[i] = tile_d2(qq, s.xy[x]);
+            }
+        }
+        for (int i = kq; i < k; ++i) {
+            orow[i] = -1;
+            drow[i] = kInf;
+        }
+    }
+}
+
+__device__ __forceinline__ int32_t clamp_leaf(int32_t b, int32_t m) {
+    return b < 0 ? 0 : (b > m ? m : b);
+}
+
+}  // namespace
+
+template <int KC>
+__global__ void __launch_bounds__(kTileThreads, KC <= 16 ? 3 : 2)
+    k_expand_tile(const TileArgs g) {
+    __shared__ TileSmem s;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const float kInf = __int_as_float(0x7f800000);
+    int32_t nv = g.scalars[kScalarValidQueries];
+    nv = nv < 0 ? 0 : (nv > g.n_q ? (int32_t)g.n_q : nv);
+    int32_t m = g.scalars[kScalarLeaves];
+    m = m < 0 ? 0 : (m > g.leaf_cap ? (int32_t)g.leaf_cap : m);
+    const int64_t ntiles = 1ll << (2 * g.Gp);
+    const int dsh = 2 * (g.G - g.Gp);
+    const float cside = ldexpf(g.side, -g.Gp);
+    for (;;) {
+        __syncthreads();  // the last tile's staged objects are no longer read
+        if (tid == 0) s.ticket = atomicAdd(g.tile_counter, 1u);
+        __syncthreads();
+        const int64_t t = s.ticket;
+        if (t >= ntiles) break;
+        int32_t qa = g.qcs[t], qb = g.qcs[t + 1];
+        qa = qa < 0 ? 0 : (qa > nv ? nv : qa);
+        qb = qb < qa ? qa : (qb > nv ? nv : qb);
+        const int32_t nq = qb - qa;
+        if (nq == 0) continue;
+
+        // the tile's query box
+        float bx0 = kInf, bx1 = -kInf, by0 = kInf, by1 = -kInf;
+        for (int32_t q = qa + tid; q < qb; q += kTileThreads) {
+            const float x = g.qs_x[q], y = g.qs_y[q];
+            bx0 = fminf(bx0, x);
+            bx1 = fmaxf(bx1, x);
+            by0 = fminf(by0, y);
+            by1 = fmaxf(by1, y);
+        }
+        bx0 = warp_min(bx0);
+        bx1 = warp_max(bx1);
+        by0 = warp_min(by0);
+        by1 = warp_max(by1);
+        if (lane == 0) {
+            s.red[0][wid] = bx0;
+            s.red[1][wid] = bx1;
+            s.red[2][wid] = by0;
+            s.red[3][wid] = by1;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            for (int w = 1; w < kTileWarps; ++w) {
+                bx0 = fminf(bx0, s.red[0][w]);
+                bx1 = fmaxf(bx1, s.red[1][w]);
+                by0 = fminf(by0, s.red[2][w]);
+                by1 = fmaxf(by1, s.red[3][w]);
+            }
+            // the tile's object density: its level-G cells are consecutive in
+            // the cell map
+            const int32_t la = clamp_leaf(g.cb[t << dsh], m);
+            const int32_t lb = clamp_leaf(g.cb[(t + 1) << dsh], m);
+            const int32_t cnt = g.bstart[lb] - g.bstart[la];
+            int ok = nq <= kTileMaxQ && cnt > 0 && bx0 <= bx1 && by0 <= by1;
+            const float rho = (float)cnt / (cside * cside);
+            // the margin: a disc of twice the area the first thresholds
+            // expect at the tile's density
+            const float fk = (float)g.k;
+            const float H = __fsqrt_ru(2.f * (fk + 4.f * sqrtf(fk) + 4.f) / (3.14159265f * rho));
+            const float hx0 = __fsub_rd(bx0, H), hx1 = __fadd_ru(bx1, H);
+            const float hy0 = __fsub_rd(by0, H), hy1 = __fadd_ru(by1, H);
+            ok = ok && H > 0.f && H < kInf && hx0 < hx1 && hy0 < hy1;
+            const int gx0 = cell_g(hx0, g.x0, g.scale_g, g.G), gx1 = cell_g(hx1, g.x0, g.scale_g, g.G);
+            const int gy0 = cell_g(hy0, g.y0, g.scale_g, g.G), gy1 = cell_g(hy1, g.y0, g.scale_g, g.G);
+            const int ngx = gx1 - gx0 + 1, ngy = gy1 - gy0 + 1;
+            ok = ok && (int64_t)ngx * ngy <= kTileStage;
+            // micro-cells of about one object, at most kTileCells
+            const float W = hx1 - hx0, Hh = hy1 - hy0;
+            float c = sqrtf(1.f / rho);
+            int nmx = 1, nmy = 1;
+            if (ok) {
+                nmx = max(1, min(kTileCells, (int)ceilf(W / c)));
+                nmy = max(1, min(kTileCells, (int)ceilf(Hh / c)));
+                if (nmx * nmy > kTileCells) {
+                    c *= sqrtf((float)(nmx * nmy) / (float)kTileCells) * 1.02f;
+                    nmx = max(1, min(kTileCells, (int)ceilf(W / c)));
+                    nmy = max(1, min(kTileCells / nmx, (int)ceilf(Hh / c)));
+                }
+            }
+            s.ok = ok;
+            s.hx0 = hx0;
+            s.hx1 = hx1;
+            s.hy0 = hy0;
+            s.hy1 = hy1;
+            s.nmx = nmx;
+            s.nmy = nmy;
+            s.iw = (float)nmx / W;
+            s.ih = (float)nmy / Hh;
+            s.rho = rho;
+            s.ngx = ngx;
+            s.ng = ok ? ngx * ngy : 0;
+            s.gx0 = gx0;
+            s.gy0 = gy0;
+        }
+        __syncthreads();
+        int ok = s.ok;
+        const int ng = s.ng, nmx = s.nmx, nmy = s.nmy, ncells = nmx * nmy;
+        uint32_t S = 0;
+        if (ok) {
+            // staged level-G cells: counts, then their first staged index
+            int32_t cc = 0, oa = 0;
+            if (tid < ng) {
+                const int cx = s.gx0 + tid % s.ngx, cy = s.gy0 + tid / s.ngx;
+                const uint32_t mc = interleave((uint32_t)cx, (uint32_t)cy);
+                const int32_t la = clamp_leaf(g.cb[mc], m);
+                const int32_t lb = clamp_leaf(g.cb[mc + 1], m);
+                oa = g.bstart[la];
+                cc = g.bstart[lb] - oa;
+                cc = cc > 0 ? cc : 0;
+            }
+            for (int i = tid; i <= ncells; i += kTileThreads) s.cs[i] = 0;
+            const uint32_t ex = block_excl_scan_256((uint32_t)cc, s.scan_tmp, &s.scan_total);
+            if (tid < ng) {
+                s.gofs[tid] = (int32_t)ex;
+                s.goa[tid] = oa;
+            }
+            S = s.scan_total;
+            if (tid == 0) s.gofs[ng] = (int32_t)S;
+            ok = S > 0 && S <= (uint32_t)kTileObj;
+            __syncthreads();
+        }
+        if (!ok) {
+            // the tile goes to the gathered form, as the packets k_packets cuts
+            const int32_t npk = (nq + 31) >> 5;
+            if (tid == 0) s.pk_base = atomicAdd(g.scalars + kScalarPackets, npk);
+            __syncthreads();
+            for (int32_t i = tid; i < npk; i += kTileThreads) {
+                const int64_t slot = (int64_t)s.pk_base + i;
+                if (slot >= 0 && slot < g.pk_cap) {
+                    g.pk_start[slot] = qa + 32 * i;
+                    g.pk_len[slot] = min(32, nq - 32 * i);
+                }
+            }
+            continue;
+        }
+        // stage the objects: counting sort by micro-cell (row-major)
+        {
+            const float hx0 = s.hx0, hy0 = s.hy0, iw = s.iw, ih = s.ih;
+            constexpr int kPer = (kTileObj + kTileThreads) / kTileThreads;
+            float lx[kPer], ly[kPer];
+            int32_t lid[kPer], lm[kPer], lr[kPer];
+#pragma unroll
+            for (int u = 0; u < kPer; ++u) {
+                const int si = tid + u * kTileThreads;
+                lm[u] = -1;
+                lx[u] = ly[u] = 0.f;
+                lid[u] = lr[u] = 0;
+                if (si < (int)S) {
+                    int lo = 0, hi = ng - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (s.gofs[mid] <= si) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    int64_t gi = (int64_t)s.goa[lo] + (si - s.gofs[lo]);
+                    if (!KNN_IN_BOUNDS(gi, 0, g.n, g.err)) gi = 0;
+                    lx[u] = g.xs[gi];
+                    ly[u] = g.ys[gi];
+                    lid[u] = g.sid[gi];
+                    const int mc = mcell(ly[u], hy0, ih, nmy) * nmx + mcell(lx[u], hx0, iw, nmx);
+                    lm[u] = mc;
+                    lr[u] = atomicAdd(&s.cs[mc], 1);
+                }
+            }
+            __syncthreads();
+            // exclusive scan of the micro-cell counts, four cells per thread
+            {
+                int32_t v[4];
+                uint32_t sum = 0;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int i = tid * 4 + u;
+                    v[u] = i < ncells ? s.cs[i] : 0;
+                    sum += (uint32_t)v[u];
+                }
+                uint32_t ex = block_excl_scan_256(sum, s.scan_tmp, nullptr);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int i = tid * 4 + u;
+                    if (i < ncells) s.cs[i] = (int32_t)ex;
+                    ex += (uint32_t)v[u];
+                }
+                if (tid == 0) s.cs[ncells] = (int32_t)S;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int u = 0; u < kPer; ++u) {
+                if (lm[u] >= 0) {
+                    int pos = s.cs[lm[u]] + lr[u];
+                    if (!KNN_IN_BOUNDS(pos, 0, kTileObj, g.err)) pos = 0;
+                    s.xy[pos] = make_float2(lx[u], ly[u]);
+                    s.id[pos] = lid[u];
+                }
+            }
+            __syncthreads();
+        }
+        // the tile's packets, one warp each
+        for (int32_t pw = wid; pw * 32 < nq; pw += kTileWarps)
+            tile_packet<KC>(g, s, qa + 32 * pw, min(32, nq - 32 * pw), tid);
+    }
+}
+
+namespace {
+
+template <int KC>
+int tile_blocks_per_sm(int device) {
+    static int cached[64] = {0};
+    const int slot = device >= 0 && device < 64 ? device : 0;
+    if (cached[slot] == 0) {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_expand_tile<KC>, kTileThreads, 0);
+        cached[slot] = per_sm < 1 ? 1 : per_sm;
+    }
+    return cached[slot];
+}
+
+template <int KC>
+void run_tile(const TileArgs &a, int device, cudaStream_t s) {
+    const int per_sm = tile_blocks_per_sm<KC>(device);
+    k_expand_tile<KC><<<num_sms(device) * per_sm, kTileThreads, 0, s>>>(a);
+}
+
+}  // namespace
+
+void prepare_expand_tile(int device) {
+    tile_blocks_per_sm<16>(device);
+    tile_blocks_per_sm<32>(device);
+}
+
+void launch_expand_tile(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t *out_ids,
+                        float *out_d2, const int32_t *q_k, cudaStream_t s) {
+    if (n_q <= 0) return;
+    TileArgs a;
+    a.xs = w.xs;
+    a.ys = w.ys;
+    a.sid = w.sid;
+    a.cb = w.cb;
+    a.bstart = w.bstart;
+    a.qs_x = w.qs_x;
+    a.qs_y = w.qs_y;
+    a.qs_id = w.qs_id;
+    a.qs_orig = w.qs_orig;
+    a.qcs = w.qcs;
+    a.scalars = w.scalars;
+    a.tile_counter = w.counters + kCtrTile;
+    a.pk_start = w.pk_start;
+    a.pk_len = w.pk_len;
+    a.out_ids = out_ids;
+    a.out_d2 = out_d2;
+    a.q_k = q_k;
+    a.err = w.err;
+    a.x0 = w.desc.x0;
+    a.y0 = w.desc.y0;
+    a.side = w.desc.side;
+    a.scale_g = ldexpf(w.scale, -(p.L - p.G));
+    a.G = p.G;
+    a.Gp = p.Gp;
+    a.k = k;
+    a.vec_out = q_k == nullptr && k % 4 == 0 &&
+                ((reinterpret_cast<uintptr_t>(out_ids) | reinterpret_cast<uintptr_t>(out_d2)) &
+                 15u) == 0;
+    a.n = w.n;
+    a.n_q = n_q;
+    a.pk_cap = packet_capacity(w);
+    a.leaf_cap = w.leaf_cap;
+    if (k <= 16) run_tile<16>(a, w.device, s);
+    else run_tile<32>(a, w.device, s);
+    ++w.launches;
+}
+
+}  // namespace knnq

@@ -1217,6 +1217,7 @@ void prepare_kernels() {
     prepare_expand(dev);   // must not run while a batch is being recorded
     prepare_expand_wide(dev);
     prepare_expand_gather(dev);
+    prepare_expand_tile(dev);
     done[dev] = true;
 }
 

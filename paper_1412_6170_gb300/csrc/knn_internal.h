@@ -49,7 +49,7 @@ enum Scalar : int { kScalarLeaves = 0, kScalarValidQueries = 1, kScalarPackets =
 enum Counter : int { kCtrObjSort = 0, kCtrQuerySort = 4, kCtrLeaves = 8, kCtrQueryScan = 9,
                      kCtrExpand = 11, kCtrReuseScan = 12,
                      kCtrIterLeft = 13 /* and 14: iterative expansion */, kCtrGather = 15,
-                     kCtrHandBack = 16 };
+                     kCtrHandBack = 16, kCtrTile = 17 };
 
 struct Plan {
     int L;           // max depth (key has 2L bits)
@@ -59,6 +59,8 @@ struct Plan {
     int passes;      // radix passes over 2L bits
     bool wide;       // expansion by one warp per query (else packets)
     bool gather;     // packets gather their search box at once (the rest: packet walk)
+    bool tile;       // queries at issuers: one block per level-Gp cell stages its margin once
+                     // and each lane scans its own box (the rest: gathered packets)
     bool iterative;  // expansion in the paper's multi-pass form (an ablation)
     int reuse_age;   // index reuse: rebuild at least every reuse_age ticks (0: every tick)
     int reuse_f16;   // and when the cost proxy grows past reuse_f16 / 16 of its built value
@@ -245,10 +247,18 @@ void launch_expand_iter(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t
 void launch_expand_handed_back(World &w, const Plan &p, int32_t k, int64_t n_q,
                                int32_t *out_ids, float *out_d2, const int32_t *q_k,
                                cudaStream_t s);
+// ---- launcher (knn_expand_tile.cu) -------------------------------------------
+// The tiled form over the level-Gp cells of the sorted queries (queries at
+// their issuers, packets not cut): what it cannot finish it appends to the
+// packet list, for launch_expand_gather.
+void launch_expand_tile(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t *out_ids,
+                        float *out_d2, const int32_t *q_k, cudaStream_t s);
 // ---- launcher (knn_expand_gather.cu) -----------------------------------------
-// The gathered form, then the packet walk over the packets it handed back.
+// The gathered form, then (then_walk) the packet walk over the packets it
+// handed back.
 void launch_expand_gather(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t *out_ids,
-                          float *out_d2, const int32_t *q_k, cudaStream_t s);
+                          float *out_d2, const int32_t *q_k, cudaStream_t s,
+                          bool then_walk = true);
 
 // ---- batched expansion over many worlds (knn_expand_gather.cu, knn_expand.cu)
 // A batch table holds one entry per world (the world's expansion arguments,
@@ -278,6 +288,7 @@ void prepare_kernels();
 void prepare_expand(int device);
 void prepare_expand_wide(int device);
 void prepare_expand_gather(int device);
+void prepare_expand_tile(int device);
 
 // Device memory layout of a world (knn_capi.cu).  base == nullptr only sizes.
 size_t carve_resident(World &w, char *base);
