@@ -302,8 +302,8 @@ knn_status knn_brute_force(const float *x_dev, const float *y_dev, int64_t n,
  *   the paper's multi-pass form (Section 4.2: first iteration on the query's
  *   own cell, then alternating left/right Morton sub-visits, one cell per
  *   iteration; k <= 64), an ablation with the same rows, never recorded in a
- *   tick graph; 5 = tiles (9 <= k <= 32, queries at their issuers; other
- *   ticks run form 4): one thread block per packet-level cell of the sorted
+ *   tick graph; 5 = tiles (k <= 32, queries at their issuers; other ticks
+ *   run form 4): one thread block per packet-level cell of the sorted
  *   queries stages the objects around the cell in shared memory once
  *   (counting-sorted into a fine grid) and each lane scans only its own
  *   query's search box, nearest rows first, shrinking it as its k-th

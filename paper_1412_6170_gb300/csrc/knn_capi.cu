@@ -77,9 +77,9 @@ Plan make_plan(const World &w, int64_t n_q, int k) {
                (w.tuning.expansion == 4 || w.tuning.expansion == 5 ||
                 (w.tuning.expansion == 0 && k <= 32));
     // the tiled form (queries at issuers; the gathered form finishes what it
-    // passes on) for 9 <= k <= 32, with about 200 queries per tile
-    p.tile = p.gather && k >= 9 && k <= 32 &&
-             (w.tuning.expansion == 5 || w.tuning.expansion == 0);
+    // passes on): automatic for 9 <= k <= 32, on request for any k <= 32
+    p.tile = p.gather && k <= 32 &&
+             (w.tuning.expansion == 5 || (w.tuning.expansion == 0 && k >= 9));
     if (p.tile && w.tuning.packet_level <= 0)
         p.Gp = clampi(round_log4((double)(n_q > 0 ? n_q : 1) / 200.0), 0, p.G);
     p.by_id = 2 * n_q >= w.n;

@@ -656,6 +656,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32, GatherShape<KC>::kMinBlocks
     GatherSmem<KC> &sm = smem[threadIdx.x >> 5];
     int32_t F, P, m;
     gather_counts(g, F, P, m);
+    if (P == 0) return;  // (the tiled form finished every packet)
     for (;;) {
         int32_t p = 0;
         if (lane == 0) p = (int32_t)atomicAdd(g.pk_counter, 1u);

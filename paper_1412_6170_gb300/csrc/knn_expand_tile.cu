@@ -46,8 +46,12 @@ constexpr int kTileObj = 2047;                  // staged objects (index + 1 fit
 constexpr int kTileCells = 1024;                // micro-cells
 constexpr int kTileStage = 256;                 // level-G cells staged per tile
 constexpr int kTileMaxQ = 4096;                 // a tile with more queries goes to the gathered form
+constexpr int kTileMaxCells = 4;                // level-Gp cells per tile
 constexpr int kTileSlots = 16;                  // candidate buffer slots per lane
-constexpr int kTileFlush = kTileSlots - kBatch; // a merge as soon as one lane holds a batch
+constexpr int kTileFlush = kBatch;              // a merge as soon as one lane holds a batch
+constexpr int kTileStep = 4;                    // objects a lane tests per step of its row
+static_assert(kTileFlush - 1 + kTileStep <= kTileSlots, "a step never overfills a buffer");
+constexpr float kTileAspect = 1.f;              // micro-cell height / width
 constexpr uint32_t kPad32 = 0xFFFFFFFFu;        // empty slot (above every real key)
 constexpr float kCodeMax = 2097150.f;           // 2^21 - 2: largest distance code
 
@@ -68,6 +72,7 @@ struct TileArgs {
     uint32_t *err;
     float x0, y0, side, scale_g;
     int G, Gp, k;
+    int tcells;  // level-Gp cells per tile (consecutive in Morton order): 1, 2 or 4
     int vec_out;
     int64_t n, n_q, pk_cap, leaf_cap;
 };
@@ -86,8 +91,38 @@ struct TileSmem {
     float hx0, hx1, hy0, hy1;  // the staged margin (a box around the tile's queries)
     float iw, ih;              // micro-cells per unit length
     float rho;                 // the tile's object density
-    int nmx, nmy, ngx, ng, gx0, gy0, ok, pk_base;
+    int nmx, nmy, ngx, ng, gx0, gx1, gy0, gy1, ok, pk_full, pk_part;
+    int32_t cq[kTileMaxCells];      // the tile's cells: first sorted query,
+    int32_t cn[kTileMaxCells];      // query count
+    int32_t pp[kTileMaxCells + 1];  // and first packet
+    int32_t pf[kTileMaxCells + 1];  // full packets before the cell
+    int32_t ppart[kTileMaxCells + 1];  // partial packets before the cell
+    int32_t next_pk;                // next packet to hand to a warp
 };
+
+// Passes packet (q0, ql) on to the gathered form: full packets to the front
+// of the packet list, partial ones to its back (the order k_packets gives).
+__device__ __forceinline__ void pass_on(const TileArgs &g, int32_t q0, int32_t ql) {
+    const int64_t slot = ql == 32 ? (int64_t)atomicAdd(g.scalars + kScalarPackets, 1)
+                                  : g.pk_cap - 1 - atomicAdd(g.scalars + kScalarPartialPackets, 1);
+    if (slot >= 0 && slot < g.pk_cap) {
+        g.pk_start[slot] = q0;
+        g.pk_len[slot] = ql;
+    }
+}
+
+// Packet pw of the current tile: the cell's queries 32 at a time (the packets
+// k_packets cuts).
+__device__ __forceinline__ void tile_pk(const TileSmem &s, int T, int32_t pw, int32_t &q0,
+                                        int32_t &ql) {
+    int c = 0;
+#pragma unroll
+    for (int i = 1; i < kTileMaxCells; ++i)
+        if (i < T && pw >= s.pp[i]) c = i;
+    const int32_t o = pw - s.pp[c];
+    q0 = s.cq[c] + 32 * o;
+    ql = min(32, s.cn[c] - 32 * o);
+}
 
 // Micro-cell coordinate of v in a grid starting at v0 with `inv` cells per
 // unit length and n cells: monotone in v (clamped at both ends).
@@ -115,15 +150,17 @@ __device__ __forceinline__ void sort8_32(uint32_t (&b)[kBatch]) {
 }
 
 // a (KC keys, ascending) := the KC smallest of a and b (8 keys, ascending), as
-// merge_batch does; `disc` becomes the smallest key dropped so far.
+// merge_batch does; d1 <= d2 become the two smallest keys dropped so far.
 template <int KC>
 __device__ __forceinline__ void merge32(uint32_t (&a)[KC], const uint32_t (&b)[kBatch],
-                                        uint32_t &disc) {
+                                        uint32_t &d1, uint32_t &d2) {
     static_assert(KC >= kBatch, "lists of at least one batch");
 #pragma unroll
     for (int i = KC - kBatch; i < KC; ++i) {
         const uint32_t v = b[KC - 1 - i];
-        disc = min(disc, max(v, a[i]));
+        const uint32_t h = max(v, a[i]);
+        d2 = min(d2, max(d1, h));
+        d1 = min(d1, h);
         a[i] = min(v, a[i]);
     }
 #pragma unroll
@@ -171,7 +208,7 @@ __device__ __forceinline__ void tile_packet(const TileArgs &g, TileSmem &s, int3
 
     bool fail = false;
     // the issuer's own staged object (its position is the query's, so it sits
-    // in the query's micro-cell); it never enters the list
+    // in the query's micro-cell); its key (code 0) is dropped at the merges
     int selfp = -1;
     if (want) {
         const int32_t me = g.qs_id[j];
@@ -181,7 +218,7 @@ __device__ __forceinline__ void tile_packet(const TileArgs &g, TileSmem &s, int3
             if (s.id[p] == me) selfp = p;
         if (me >= 0 && selfp < 0) fail = true;
     }
-    // first threshold: the squared radius holding about k + 4 sqrt(k) + 4
+    // first threshold: the squared radius holding about k + 3 sqrt(k) + 2
     // objects at the density of the 7 x 7 micro-cells around the query
     float t0 = kInf;
     if (want) {
@@ -192,16 +229,24 @@ __device__ __forceinline__ void tile_packet(const TileArgs &g, TileSmem &s, int3
         const float cells = (float)((xb - xa + 1) * (yb - ya + 1));
         const float rho = cnt > 0 ? (float)cnt * iw * ih / cells : s.rho;
         const float fk = (float)kq;
-        t0 = (fk + 4.f * sqrtf(fk) + 4.f) / (3.14159265f * rho);
+        t0 = (fk + 3.f * sqrtf(fk) + 2.f) / (3.14159265f * rho);
     }
     // t_fit: an object outside the staged margin is at least this far (in
     // d^2, rounded like the exact distances); the threshold stays below it
+    // (a side of the margin whose staged cells reach the edge of the cell map
+    // has nothing unstaged beyond it: every object past the world's edge lies
+    // in an edge cell)
     float tcap = -1.f;
     if (want) {
-        const float gx = fminf(__fsub_rd(qx, s.hx0), __fsub_rd(s.hx1, qx));
-        const float gy = fminf(__fsub_rd(qy, s.hy0), __fsub_rd(s.hy1, qy));
-        const float gm = fminf(gx, gy);
-        if (gm > 0.f) {
+        const int lim = (1 << g.G) - 1;
+        float gm = kInf;
+        if (s.gx0 > 0) gm = fminf(gm, __fsub_rd(qx, s.hx0));
+        if (s.gx1 < lim) gm = fminf(gm, __fsub_rd(s.hx1, qx));
+        if (s.gy0 > 0) gm = fminf(gm, __fsub_rd(qy, s.hy0));
+        if (s.gy1 < lim) gm = fminf(gm, __fsub_rd(s.hy1, qy));
+        if (gm == kInf) {
+            tcap = 3.0e38f;
+        } else if (gm > 0.f) {
             const float tf = __fmul_rd(gm, gm);
             if (tf > 0.f) tcap = __uint_as_float(__float_as_uint(tf) - 1u);
         }
@@ -212,8 +257,9 @@ __device__ __forceinline__ void tile_packet(const TileArgs &g, TileSmem &s, int3
     uint32_t lst[KC];
 #pragma unroll
     for (int i = 0; i < KC; ++i) lst[i] = kPad32;
-    uint32_t disc = kPad32;
+    uint32_t disc = kPad32, disc2 = kPad32;  // the two smallest keys dropped
     const unsigned long long qq = f2pack(qx, qy);
+    const uint32_t selfkey = selfp >= 0 ? (uint32_t)(selfp + 1) : 0u;  // 0: no real key
 
     for (int attempt = 0; attempt < 3; ++attempt) {
         bool run = want && !ok && !fail;
@@ -232,7 +278,7 @@ __device__ __forceinline__ void tile_packet(const TileArgs &g, TileSmem &s, int3
         if (run) {
 #pragma unroll
             for (int i = 0; i < KC; ++i) lst[i] = i < KC - kq ? 0u : kPad32;
-            disc = kPad32;
+            disc = disc2 = kPad32;
         }
         float th = run ? thr : -1.f;
         int mx_lo = 0, mx_hi = -1, my_lo = 0, my_hi = -1, omax = 0;
@@ -257,10 +303,12 @@ __device__ __forceinline__ void tile_packet(const TileArgs &g, TileSmem &s, int3
                 const int base = cnt > kBatch ? cnt - kBatch : 0;
                 uint32_t bt[kBatch];
 #pragma unroll
-                for (int t = 0; t < kBatch; ++t)
-                    bt[t] = base + t < cnt ? s.buf[base + t][tid] : kPad32;
+                for (int t = 0; t < kBatch; ++t) {
+                    const uint32_t v = base + t < cnt ? s.buf[base + t][tid] : kPad32;
+                    bt[t] = v == selfkey ? kPad32 : v;
+                }
                 sort8_32(bt);
-                merge32<KC>(lst, bt, disc);
+                merge32<KC>(lst, bt, disc, disc2);
                 cnt = base;
                 const uint32_t last = lst[KC - 1];
                 if (run && last != kPad32) {
@@ -282,35 +330,31 @@ __device__ __forceinline__ void tile_packet(const TileArgs &g, TileSmem &s, int3
                     e = s.cs[b + mx_hi + 1];
                 }
             }
-            const bool okA = p < e;
-            if (!__any_sync(kFull, okA)) break;
-            const bool okB = p + 1 < e;
-            {
-                const float d = tile_d2(qq, s.xy[okA ? p : 0]);
-                if (okA && d <= th && p != selfp) {
+            if (!__any_sync(kFull, p < e)) break;
+#pragma unroll
+            for (int u = 0; u < kTileStep; ++u) {
+                const int j = p + u;
+                const bool okj = j < e;
+                const float d = tile_d2(qq, s.xy[okj ? j : 0]);
+                if (okj && d <= th) {
                     const uint32_t c = __float2uint_rz(__fmul_rn(d, inv));
-                    s.buf[cnt][tid] = (c << 11) | (uint32_t)(p + 1);
+                    s.buf[cnt][tid] = (c << 11) | (uint32_t)(j + 1);
                     ++cnt;
                 }
             }
-            {
-                const float d = tile_d2(qq, s.xy[okB ? p + 1 : 0]);
-                if (okB && d <= th && p + 1 != selfp) {
-                    const uint32_t c = __float2uint_rz(__fmul_rn(d, inv));
-                    s.buf[cnt][tid] = (c << 11) | (uint32_t)(p + 2);
-                    ++cnt;
-                }
-            }
-            p += 2;
+            p += kTileStep;
         }
         // drain the buffers
         while (__any_sync(kFull, cnt > 0)) {
             const int base = cnt > kBatch ? cnt - kBatch : 0;
             uint32_t bt[kBatch];
 #pragma unroll
-            for (int t = 0; t < kBatch; ++t) bt[t] = base + t < cnt ? s.buf[base + t][tid] : kPad32;
+            for (int t = 0; t < kBatch; ++t) {
+                const uint32_t v = base + t < cnt ? s.buf[base + t][tid] : kPad32;
+                bt[t] = v == selfkey ? kPad32 : v;
+            }
             sort8_32(bt);
-            merge32<KC>(lst, bt, disc);
+            merge32<KC>(lst, bt, disc, disc2);
             cnt = base;
         }
         if (run) {
@@ -330,22 +374,53 @@ __device__ __forceinline__ void tile_packet(const TileArgs &g, TileSmem &s, int3
         }
     }
     if (want && !ok) fail = true;
+    // Codes that are equal among the k keys, or between the k-th and a dropped
+    // key, leave the order open: those keys are compared by their exact
+    // (d^2, id) keys (bubble passes within runs of equal codes, and the one
+    // dropped key with the k-th code against the k-th).  Two dropped keys with
+    // the k-th code, or runs too long for the passes, go on.
+    bool fix = false;
     if (want && ok) {
-        // distinct codes among the k keys and above them: the order is exact
-        bool strict = (disc >> 11) != (lst[KC - 1] >> 11);
+        const uint32_t ck = lst[KC - 1] >> 11;
+        fix = (disc >> 11) == ck;
 #pragma unroll
         for (int i = 0; i + 1 < KC; ++i)
-            if (i >= KC - kq) strict = strict && (lst[i] >> 11) != (lst[i + 1] >> 11);
-        if (!strict) fail = true;
+            if (i >= KC - kq) fix = fix || (lst[i] >> 11) == (lst[i + 1] >> 11);
+        if ((disc2 >> 11) == ck) fail = true;
+    }
+    if (__any_sync(kFull, fix && !fail)) {
+        auto exact = [&](uint32_t key) -> unsigned long long {
+            int x = (int)(key & 0x7FFu) - 1;
+            if (!KNN_IN_BOUNDS(x, 0, kTileObj, g.err)) x = 0;
+            const float d = tile_d2(qq, s.xy[x]);
+            return ((unsigned long long)__float_as_uint(d) << 32) | (uint32_t)(s.id[x] + 1);
+        };
+        auto order_runs = [&](bool &sorted) {
+            sorted = true;
+#pragma unroll
+            for (int i = 0; i + 1 < KC; ++i) {
+                if (i >= KC - kq && (lst[i] >> 11) == (lst[i + 1] >> 11) &&
+                    exact(lst[i]) > exact(lst[i + 1])) {
+                    const uint32_t t = lst[i];
+                    lst[i] = lst[i + 1];
+                    lst[i + 1] = t;
+                    sorted = false;
+                }
+            }
+        };
+        if (fix && !fail) {
+            bool sorted = false;
+            for (int pass = 0; pass < 4 && !sorted; ++pass) order_runs(sorted);
+            if ((disc >> 11) == (lst[KC - 1] >> 11) && exact(disc) < exact(lst[KC - 1])) {
+                lst[KC - 1] = disc;
+                sorted = false;
+                for (int pass = 0; pass < 4 && !sorted; ++pass) order_runs(sorted);
+            }
+            if (!sorted) fail = true;
+        }
     }
     if (__any_sync(kFull, fail)) {
-        if (lane == 0) {
-            const int32_t slot = atomicAdd(g.scalars + kScalarPackets, 1);
-            if (slot >= 0 && slot < g.pk_cap) {
-                g.pk_start[slot] = q0;
-                g.pk_len[slot] = ql;
-            }
-        }
+        if (lane == 0) pass_on(g, q0, ql);
         return;
     }
     // a8: the row of this lane's query in caller order
@@ -393,7 +468,7 @@ __device__ __forceinline__ int32_t clamp_leaf(int32_t b, int32_t m) {
 }  // namespace
 
 template <int KC>
-__global__ void __launch_bounds__(kTileThreads, KC <= 16 ? 3 : 2)
+__global__ void __launch_bounds__(kTileThreads, KC <= 16 ? 4 : 2)
     k_expand_tile(const TileArgs g) {
     __shared__ TileSmem s;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -402,7 +477,8 @@ __global__ void __launch_bounds__(kTileThreads, KC <= 16 ? 3 : 2)
     nv = nv < 0 ? 0 : (nv > g.n_q ? (int32_t)g.n_q : nv);
     int32_t m = g.scalars[kScalarLeaves];
     m = m < 0 ? 0 : (m > g.leaf_cap ? (int32_t)g.leaf_cap : m);
-    const int64_t ntiles = 1ll << (2 * g.Gp);
+    const int T = g.tcells;
+    const int64_t ntiles = (1ll << (2 * g.Gp)) / T;
     const int dsh = 2 * (g.G - g.Gp);
     const float cside = ldexpf(g.side, -g.Gp);
     for (;;) {
@@ -411,15 +487,47 @@ __global__ void __launch_bounds__(kTileThreads, KC <= 16 ? 3 : 2)
         __syncthreads();
         const int64_t t = s.ticket;
         if (t >= ntiles) break;
-        int32_t qa = g.qcs[t], qb = g.qcs[t + 1];
+        const int64_t c0 = t * T;  // the tile's first level-Gp cell
+        int32_t qa = g.qcs[c0], qb = g.qcs[c0 + T];
         qa = qa < 0 ? 0 : (qa > nv ? nv : qa);
         qb = qb < qa ? qa : (qb > nv ? nv : qb);
         const int32_t nq = qb - qa;
         if (nq == 0) continue;
+        // the tile's objects: its level-G cells are consecutive in the cell
+        // map; a tile that cannot be staged (too many objects or queries)
+        // goes on at once.  Its packets: each cell's queries 32 at a time.
+        if (tid == 0) {
+            const int32_t la = clamp_leaf(g.cb[c0 << dsh], m);
+            const int32_t lb = clamp_leaf(g.cb[(c0 + T) << dsh], m);
+            const int32_t cnt = g.bstart[lb] - g.bstart[la];
+            s.ok = nq <= kTileMaxQ && cnt > 0 && cnt <= kTileObj;
+            s.rho = (float)cnt / ((float)T * cside * cside);
+            int32_t acc = 0, af = 0, ap = 0;
+            for (int i = 0; i < T; ++i) {
+                int32_t a = g.qcs[c0 + i], b = g.qcs[c0 + i + 1];
+                a = a < qa ? qa : (a > qb ? qb : a);
+                b = b < a ? a : (b > qb ? qb : b);
+                s.cq[i] = a;
+                s.cn[i] = b - a;
+                s.pp[i] = acc;
+                s.pf[i] = af;
+                s.ppart[i] = ap;
+                acc += (b - a + 31) >> 5;
+                af += (b - a) >> 5;
+                ap += ((b - a) & 31) != 0 ? 1 : 0;
+            }
+            s.pp[T] = acc;
+            s.pf[T] = af;
+            s.ppart[T] = ap;
+            s.next_pk = 0;
+        }
+        __syncthreads();
+        bool early_ok = s.ok;
+        const int32_t npk = s.pp[T];
 
         // the tile's query box
         float bx0 = kInf, bx1 = -kInf, by0 = kInf, by1 = -kInf;
-        for (int32_t q = qa + tid; q < qb; q += kTileThreads) {
+        for (int32_t q = qa + tid; early_ok && q < qb; q += kTileThreads) {
             const float x = g.qs_x[q], y = g.qs_y[q];
             bx0 = fminf(bx0, x);
             bx1 = fmaxf(bx1, x);
@@ -437,20 +545,15 @@ __global__ void __launch_bounds__(kTileThreads, KC <= 16 ? 3 : 2)
             s.red[3][wid] = by1;
         }
         __syncthreads();
-        if (tid == 0) {
+        if (tid == 0 && early_ok) {
             for (int w = 1; w < kTileWarps; ++w) {
                 bx0 = fminf(bx0, s.red[0][w]);
                 bx1 = fmaxf(bx1, s.red[1][w]);
                 by0 = fminf(by0, s.red[2][w]);
                 by1 = fmaxf(by1, s.red[3][w]);
             }
-            // the tile's object density: its level-G cells are consecutive in
-            // the cell map
-            const int32_t la = clamp_leaf(g.cb[t << dsh], m);
-            const int32_t lb = clamp_leaf(g.cb[(t + 1) << dsh], m);
-            const int32_t cnt = g.bstart[lb] - g.bstart[la];
-            int ok = nq <= kTileMaxQ && cnt > 0 && bx0 <= bx1 && by0 <= by1;
-            const float rho = (float)cnt / (cside * cside);
+            int ok = bx0 <= bx1 && by0 <= by1;
+            const float rho = s.rho;
             // the margin: a disc of twice the area the first thresholds
             // expect at the tile's density
             const float fk = (float)g.k;
@@ -462,17 +565,18 @@ __global__ void __launch_bounds__(kTileThreads, KC <= 16 ? 3 : 2)
             const int gy0 = cell_g(hy0, g.y0, g.scale_g, g.G), gy1 = cell_g(hy1, g.y0, g.scale_g, g.G);
             const int ngx = gx1 - gx0 + 1, ngy = gy1 - gy0 + 1;
             ok = ok && (int64_t)ngx * ngy <= kTileStage;
-            // micro-cells of about one object, at most kTileCells
+            // micro-cells of about one object (kTileAspect times as high as
+            // wide), at most kTileCells
             const float W = hx1 - hx0, Hh = hy1 - hy0;
-            float c = sqrtf(1.f / rho);
+            float c = sqrtf(1.f / (kTileAspect * rho));
             int nmx = 1, nmy = 1;
             if (ok) {
                 nmx = max(1, min(kTileCells, (int)ceilf(W / c)));
-                nmy = max(1, min(kTileCells, (int)ceilf(Hh / c)));
+                nmy = max(1, min(kTileCells, (int)ceilf(Hh / (kTileAspect * c))));
                 if (nmx * nmy > kTileCells) {
                     c *= sqrtf((float)(nmx * nmy) / (float)kTileCells) * 1.02f;
                     nmx = max(1, min(kTileCells, (int)ceilf(W / c)));
-                    nmy = max(1, min(kTileCells / nmx, (int)ceilf(Hh / c)));
+                    nmy = max(1, min(kTileCells / nmx, (int)ceilf(Hh / (kTileAspect * c))));
                 }
             }
             s.ok = ok;
@@ -488,7 +592,9 @@ __global__ void __launch_bounds__(kTileThreads, KC <= 16 ? 3 : 2)
             s.ngx = ngx;
             s.ng = ok ? ngx * ngy : 0;
             s.gx0 = gx0;
+            s.gx1 = gx1;
             s.gy0 = gy0;
+            s.gy1 = gy1;
         }
         __syncthreads();
         int ok = s.ok;
@@ -519,14 +625,24 @@ __global__ void __launch_bounds__(kTileThreads, KC <= 16 ? 3 : 2)
         }
         if (!ok) {
             // the tile goes to the gathered form, as the packets k_packets cuts
-            const int32_t npk = (nq + 31) >> 5;
-            if (tid == 0) s.pk_base = atomicAdd(g.scalars + kScalarPackets, npk);
+            if (tid == 0) {
+                s.pk_full = atomicAdd(g.scalars + kScalarPackets, s.pf[T]);
+                s.pk_part = atomicAdd(g.scalars + kScalarPartialPackets, s.ppart[T]);
+            }
             __syncthreads();
             for (int32_t i = tid; i < npk; i += kTileThreads) {
-                const int64_t slot = (int64_t)s.pk_base + i;
+                int c = 0;
+#pragma unroll
+                for (int u = 1; u < kTileMaxCells; ++u)
+                    if (u < T && i >= s.pp[u]) c = u;
+                const int32_t o = i - s.pp[c];
+                const int32_t q0 = s.cq[c] + 32 * o, ql = min(32, s.cn[c] - 32 * o);
+                const int64_t slot = ql == 32
+                                         ? (int64_t)s.pk_full + s.pf[c] + o
+                                         : g.pk_cap - 1 - ((int64_t)s.pk_part + s.ppart[c]);
                 if (slot >= 0 && slot < g.pk_cap) {
-                    g.pk_start[slot] = qa + 32 * i;
-                    g.pk_len[slot] = min(32, nq - 32 * i);
+                    g.pk_start[slot] = q0;
+                    g.pk_len[slot] = ql;
                 }
             }
             continue;
@@ -592,9 +708,16 @@ __global__ void __launch_bounds__(kTileThreads, KC <= 16 ? 3 : 2)
             }
             __syncthreads();
         }
-        // the tile's packets, one warp each
-        for (int32_t pw = wid; pw * 32 < nq; pw += kTileWarps)
-            tile_packet<KC>(g, s, qa + 32 * pw, min(32, nq - 32 * pw), tid);
+        // the tile's packets, taken by the warps one at a time
+        for (;;) {
+            int32_t pw = 0;
+            if (lane == 0) pw = atomicAdd(&s.next_pk, 1);
+            pw = __shfl_sync(kFull, pw, 0);
+            if (pw >= npk) break;
+            int32_t q0, ql;
+            tile_pk(s, T, pw, q0, ql);
+            if (ql > 0) tile_packet<KC>(g, s, q0, ql, tid);
+        }
     }
 }
 
@@ -621,6 +744,7 @@ void run_tile(const TileArgs &a, int device, cudaStream_t s) {
 }  // namespace
 
 void prepare_expand_tile(int device) {
+    tile_blocks_per_sm<8>(device);
     tile_blocks_per_sm<16>(device);
     tile_blocks_per_sm<32>(device);
 }
@@ -654,6 +778,10 @@ void launch_expand_tile(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t
     a.G = p.G;
     a.Gp = p.Gp;
     a.k = k;
+    // two cells per tile while a cell holds fewer than about 400 queries
+    // (fewer barriers per query; a warp takes about two packets per tile)
+    const int64_t ncell = 1ll << (2 * p.Gp);
+    a.tcells = ncell >= 2 && (double)n_q < 400.0 * (double)ncell ? 2 : 1;
     a.vec_out = q_k == nullptr && k % 4 == 0 &&
                 ((reinterpret_cast<uintptr_t>(out_ids) | reinterpret_cast<uintptr_t>(out_d2)) &
                  15u) == 0;
@@ -661,7 +789,8 @@ void launch_expand_tile(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t
     a.n_q = n_q;
     a.pk_cap = packet_capacity(w);
     a.leaf_cap = w.leaf_cap;
-    if (k <= 16) run_tile<16>(a, w.device, s);
+    if (k <= 8) run_tile<8>(a, w.device, s);
+    else if (k <= 16) run_tile<16>(a, w.device, s);
     else run_tile<32>(a, w.device, s);
     ++w.launches;
 }

@@ -71,7 +71,7 @@ def test_tile_serves_the_uniform_workload():
         assert passed_on(info) <= packets // 50, info
 
 
-@pytest.mark.parametrize("k", [9, 12, 16, 20, 31, 32])
+@pytest.mark.parametrize("k", [1, 4, 8, 9, 12, 16, 20, 31, 32])
 def test_tile_uniform_every_row(k):
     w = synth.plain_uniform_moving(n=30_000, k=k, ticks=2, seed=42 + k)
     infos = ticks_vs_oracle(w, what=f"30k uniform k={k}")
