@@ -651,7 +651,7 @@ def k_sweep(dev, ks=(1, 4, 16, 32, 64, 128, 256, 512), iters=3):
             e1.record(stream)
             e1.synchronize()
             ms = e0.elapsed_time(e1) / iters
-            kernel = {1: "packets", 2: "warp per query", 4: "gathered packets"}.get(
+            kernel = {1: "packets", 2: "warp per query", 4: "gathered packets", 5: "tiles"}.get(
                 world.get_tuning(N_OBJ, k)["expansion"], "packets")
             out[str(k)] = {"tick_ms": ms, "queries_per_s": N_OBJ / (ms * 1e-3),
                            "expansion": kernel}

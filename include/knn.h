@@ -309,8 +309,7 @@ knn_status knn_brute_force(const float *x_dev, const float *y_dev, int64_t n,
  *   query's search box, nearest rows first, shrinking it as its k-th
  *   distance tightens (Alg. 1's per-cell scan); packets it cannot finish
  *   exactly (equal distances, a cell too full to stage) go to form 4, which
- *   finishes them.  The automatic choice is 4 for k <= 8, 5 for 9 <= k <= 32
- *   and 2 above.
+ *   finishes them.  The automatic choice is 5 for k <= 32 and 2 above.
  * Any field set to 0 keeps (or restores) the automatic choice. */
 typedef struct {
     int32_t leaf_capacity;
@@ -324,7 +323,8 @@ knn_status knn_world_set_tuning(knn_world w, const knn_tuning *t);
  * leaf capacities, cell-map levels and packet levels around the automatic
  * choice, then for the fastest of those each expansion form (threads per
  * query: a lane in packets or a warp per query; candidates staged along the
- * walk or gathered at once), with the given queries (device arrays as for
+ * walk, gathered at once per packet, or staged once per tile), with the given
+ * queries (device arrays as for
  * knn_tick; the output arrays receive the rows, identical for every setting),
  * keeps the fastest in the world and writes it to *chosen (may be NULL).  Each
  * setting is timed as a recorded CUDA graph of `trials` ticks (device time),

@@ -437,9 +437,13 @@ extern "C" knn_status knn_world_autotune(knn_world h, const int32_t *q_id_dev,
     }
     // then the expansion form on the best index setting: threads per query (one
     // lane in packets, or a whole warp) and how candidates are staged (leaf by
-    // leaf along the walk, or gathered for the whole search box at once)
+    // leaf along the walk, gathered for the whole search box at once, or
+    // staged once per tile of queries)
     std::vector<int> forms = {1, 2};
-    if (k <= 32) forms.push_back(4);
+    if (k <= 32) {
+        forms.push_back(4);
+        forms.push_back(5);
+    }
     const knn_tuning base_t = best_t;
     for (int f : forms) {
         knn_tuning t = base_t;

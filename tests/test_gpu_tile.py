@@ -50,12 +50,12 @@ def passed_on(info):
     return info["gathered"] + info["handed_back"]
 
 
-def test_tile_is_the_automatic_form_for_k_9_to_32():
+def test_tile_is_the_automatic_form_up_to_k_32():
     torch, dev = torch_dev()
     x, y = synth.uniform_positions(20_000, seed=40)
     world = make_world(x, y, k_max=64)
     try:
-        for k, form in ((8, 4), (9, 5), (16, 5), (32, 5), (33, 2)):
+        for k, form in ((1, 5), (8, 5), (9, 5), (16, 5), (32, 5), (33, 2)):
             assert world.get_tuning(20_000, k)["expansion"] == form, k
     finally:
         world.close()
