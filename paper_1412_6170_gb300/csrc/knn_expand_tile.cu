@@ -77,6 +77,20 @@ struct TileArgs {
     int64_t n, n_q, pk_cap, leaf_cap;
 };
 
+// What a tile's staging needs first, loaded by one thread (for the next tile
+// while the current one's packets are scanned): the ticket, its query range,
+// its object count, and per cell the first query, the query count and the
+// packets before it.
+struct TileMeta {
+    int64_t t;                      // ticket (>= the tile count: no tile left)
+    int32_t qa, qb, cnt;            // sorted queries [qa, qb); objects in its cells
+    int32_t cq[kTileMaxCells];      // the tile's cells: first sorted query,
+    int32_t cn[kTileMaxCells];      // query count
+    int32_t pp[kTileMaxCells + 1];  // and first packet,
+    int32_t pf[kTileMaxCells + 1];  // full packets before the cell
+    int32_t ppart[kTileMaxCells + 1];  // partial packets before the cell
+};
+
 struct TileSmem {
     float2 xy[kTileObj + 1];   // staged objects in micro-cell order
     int32_t id[kTileObj + 1];
@@ -87,16 +101,12 @@ struct TileSmem {
     float red[4][kTileWarps];
     uint32_t scan_tmp[8];
     uint32_t scan_total;
-    uint32_t ticket;
     float hx0, hx1, hy0, hy1;  // the staged margin (a box around the tile's queries)
     float iw, ih;              // micro-cells per unit length
     float rho;                 // the tile's object density
     int nmx, nmy, ngx, ng, gx0, gx1, gy0, gy1, ok, pk_full, pk_part;
-    int32_t cq[kTileMaxCells];      // the tile's cells: first sorted query,
-    int32_t cn[kTileMaxCells];      // query count
-    int32_t pp[kTileMaxCells + 1];  // and first packet
-    int32_t pf[kTileMaxCells + 1];  // full packets before the cell
-    int32_t ppart[kTileMaxCells + 1];  // partial packets before the cell
+    TileMeta meta[2];               // the current tile's and the next one's
+    int32_t mi;                     // which meta is the current tile's
     int32_t next_pk;                // next packet to hand to a warp
 };
 
@@ -113,15 +123,15 @@ __device__ __forceinline__ void pass_on(const TileArgs &g, int32_t q0, int32_t q
 
 // Packet pw of the current tile: the cell's queries 32 at a time (the packets
 // k_packets cuts).
-__device__ __forceinline__ void tile_pk(const TileSmem &s, int T, int32_t pw, int32_t &q0,
+__device__ __forceinline__ void tile_pk(const TileMeta &M, int T, int32_t pw, int32_t &q0,
                                         int32_t &ql) {
     int c = 0;
 #pragma unroll
     for (int i = 1; i < kTileMaxCells; ++i)
-        if (i < T && pw >= s.pp[i]) c = i;
-    const int32_t o = pw - s.pp[c];
-    q0 = s.cq[c] + 32 * o;
-    ql = min(32, s.cn[c] - 32 * o);
+        if (i < T && pw >= M.pp[i]) c = i;
+    const int32_t o = pw - M.pp[c];
+    q0 = M.cq[c] + 32 * o;
+    ql = min(32, M.cn[c] - 32 * o);
 }
 
 // Micro-cell coordinate of v in a grid starting at v0 with `inv` cells per
@@ -481,49 +491,68 @@ __global__ void __launch_bounds__(kTileThreads, KC <= 16 ? 4 : 2)
     const int64_t ntiles = (1ll << (2 * g.Gp)) / T;
     const int dsh = 2 * (g.G - g.Gp);
     const float cside = ldexpf(g.side, -g.Gp);
-    for (;;) {
-        __syncthreads();  // the last tile's staged objects are no longer read
-        if (tid == 0) s.ticket = atomicAdd(g.tile_counter, 1u);
-        __syncthreads();
-        const int64_t t = s.ticket;
-        if (t >= ntiles) break;
-        const int64_t c0 = t * T;  // the tile's first level-Gp cell
+    // (thread 0) the next tile's ticket and metadata into meta[slot]: the
+    // tile's level-G cells are consecutive in the cell map; its packets are
+    // each cell's queries 32 at a time
+    auto load_meta = [&](int slot) {
+        TileMeta &M = s.meta[slot];
+        M.t = atomicAdd(g.tile_counter, 1u);
+        if (M.t >= ntiles) return;
+        const int64_t c0 = M.t * T;
         int32_t qa = g.qcs[c0], qb = g.qcs[c0 + T];
         qa = qa < 0 ? 0 : (qa > nv ? nv : qa);
         qb = qb < qa ? qa : (qb > nv ? nv : qb);
-        const int32_t nq = qb - qa;
-        if (nq == 0) continue;
-        // the tile's objects: its level-G cells are consecutive in the cell
-        // map; a tile that cannot be staged (too many objects or queries)
-        // goes on at once.  Its packets: each cell's queries 32 at a time.
-        if (tid == 0) {
-            const int32_t la = clamp_leaf(g.cb[c0 << dsh], m);
-            const int32_t lb = clamp_leaf(g.cb[(c0 + T) << dsh], m);
-            const int32_t cnt = g.bstart[lb] - g.bstart[la];
-            s.ok = nq <= kTileMaxQ && cnt > 0 && cnt <= kTileObj;
-            s.rho = (float)cnt / ((float)T * cside * cside);
-            int32_t acc = 0, af = 0, ap = 0;
-            for (int i = 0; i < T; ++i) {
-                int32_t a = g.qcs[c0 + i], b = g.qcs[c0 + i + 1];
-                a = a < qa ? qa : (a > qb ? qb : a);
-                b = b < a ? a : (b > qb ? qb : b);
-                s.cq[i] = a;
-                s.cn[i] = b - a;
-                s.pp[i] = acc;
-                s.pf[i] = af;
-                s.ppart[i] = ap;
-                acc += (b - a + 31) >> 5;
-                af += (b - a) >> 5;
-                ap += ((b - a) & 31) != 0 ? 1 : 0;
+        M.qa = qa;
+        M.qb = qb;
+        M.cnt = 0;
+        if (qb == qa) return;
+        const int32_t la = clamp_leaf(g.cb[c0 << dsh], m);
+        const int32_t lb = clamp_leaf(g.cb[(c0 + T) << dsh], m);
+        M.cnt = g.bstart[lb] - g.bstart[la];
+        int32_t acc = 0, af = 0, ap = 0;
+        for (int i = 0; i < T; ++i) {
+            int32_t a = g.qcs[c0 + i], b = g.qcs[c0 + i + 1];
+            a = a < qa ? qa : (a > qb ? qb : a);
+            b = b < a ? a : (b > qb ? qb : b);
+            M.cq[i] = a;
+            M.cn[i] = b - a;
+            M.pp[i] = acc;
+            M.pf[i] = af;
+            M.ppart[i] = ap;
+            acc += (b - a + 31) >> 5;
+            af += (b - a) >> 5;
+            ap += ((b - a) & 31) != 0 ? 1 : 0;
+        }
+        M.pp[T] = acc;
+        M.pf[T] = af;
+        M.ppart[T] = ap;
+    };
+    if (tid == 0) {
+        s.mi = 0;
+        load_meta(0);
+    }
+    for (;;) {
+        __syncthreads();  // the last tile's staged objects are no longer read
+        const int mi = s.mi;  // this tile's metadata (thread 0 fills the other slot)
+        const TileMeta &M = s.meta[mi];
+        if (M.t >= ntiles) break;
+        const int32_t qa = M.qa, qb = M.qb, nq = qb - qa, npk = M.pp[T];
+        if (nq == 0) {
+            __syncthreads();  // every thread has read M
+            if (tid == 0) {
+                load_meta(mi ^ 1);
+                s.mi = mi ^ 1;
             }
-            s.pp[T] = acc;
-            s.pf[T] = af;
-            s.ppart[T] = ap;
+            continue;
+        }
+        // a tile that cannot be staged (too many objects or queries) goes on
+        // at once
+        const bool early_ok = nq <= kTileMaxQ && M.cnt > 0 && M.cnt <= kTileObj;
+        if (tid == 0) {
+            s.rho = (float)M.cnt / ((float)T * cside * cside);
+            s.ok = 0;
             s.next_pk = 0;
         }
-        __syncthreads();
-        bool early_ok = s.ok;
-        const int32_t npk = s.pp[T];
 
         // the tile's query box
         float bx0 = kInf, bx1 = -kInf, by0 = kInf, by1 = -kInf;
@@ -626,20 +655,24 @@ __global__ void __launch_bounds__(kTileThreads, KC <= 16 ? 4 : 2)
         if (!ok) {
             // the tile goes to the gathered form, as the packets k_packets cuts
             if (tid == 0) {
-                s.pk_full = atomicAdd(g.scalars + kScalarPackets, s.pf[T]);
-                s.pk_part = atomicAdd(g.scalars + kScalarPartialPackets, s.ppart[T]);
+                s.pk_full = atomicAdd(g.scalars + kScalarPackets, M.pf[T]);
+                s.pk_part = atomicAdd(g.scalars + kScalarPartialPackets, M.ppart[T]);
             }
             __syncthreads();
+            if (tid == 0) {
+                load_meta(mi ^ 1);
+                s.mi = mi ^ 1;
+            }
             for (int32_t i = tid; i < npk; i += kTileThreads) {
                 int c = 0;
 #pragma unroll
                 for (int u = 1; u < kTileMaxCells; ++u)
-                    if (u < T && i >= s.pp[u]) c = u;
-                const int32_t o = i - s.pp[c];
-                const int32_t q0 = s.cq[c] + 32 * o, ql = min(32, s.cn[c] - 32 * o);
+                    if (u < T && i >= M.pp[u]) c = u;
+                const int32_t o = i - M.pp[c];
+                const int32_t q0 = M.cq[c] + 32 * o, ql = min(32, M.cn[c] - 32 * o);
                 const int64_t slot = ql == 32
-                                         ? (int64_t)s.pk_full + s.pf[c] + o
-                                         : g.pk_cap - 1 - ((int64_t)s.pk_part + s.ppart[c]);
+                                         ? (int64_t)s.pk_full + M.pf[c] + o
+                                         : g.pk_cap - 1 - ((int64_t)s.pk_part + M.ppart[c]);
                 if (slot >= 0 && slot < g.pk_cap) {
                     g.pk_start[slot] = q0;
                     g.pk_len[slot] = ql;
@@ -708,14 +741,20 @@ __global__ void __launch_bounds__(kTileThreads, KC <= 16 ? 4 : 2)
             }
             __syncthreads();
         }
-        // the tile's packets, taken by the warps one at a time
+        // the next tile's metadata (thread 0, while the other warps start on
+        // the packets), then the tile's packets, taken by the warps one at a
+        // time
+        if (tid == 0) {
+            load_meta(mi ^ 1);
+            s.mi = mi ^ 1;
+        }
         for (;;) {
             int32_t pw = 0;
             if (lane == 0) pw = atomicAdd(&s.next_pk, 1);
             pw = __shfl_sync(kFull, pw, 0);
             if (pw >= npk) break;
             int32_t q0, ql;
-            tile_pk(s, T, pw, q0, ql);
+            tile_pk(M, T, pw, q0, ql);
             if (ql > 0) tile_packet<KC>(g, s, q0, ql, tid);
         }
     }
