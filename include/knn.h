@@ -184,7 +184,10 @@ knn_status knn_world_set_host_io(knn_world w, int32_t mode);
  * list size (4, 8, 16, 32, 64) one persistent grid takes the packets of every
  * world of that class through a device-built prefix of the worlds' packet
  * counts, and one packet-walk grid per list size finishes the packets the
- * gathered form handed back.  Worlds whose expansion is one warp per query
+ * gathered form handed back.  Worlds on the tiled form (queries at their
+ * issuers, k <= 32) run one batched tile grid per list size first, over the
+ * tiles of all of them, and what the tiles pass on joins their packets for
+ * the gathered grid.  Worlds whose expansion is one warp per query
  * (k > 32 by default) or the multi-pass ablation expand in their own chains.
  * While the same worlds, sizes and pointers come back, the recorded graph is
  * replayed without recording.  Asynchronous on `stream`; a call that has to

@@ -60,7 +60,9 @@ struct ExpandClass {
     int kc = 0;
     bool walk = false;             // worlds on the packet walk (else the gathered form)
     std::vector<int32_t> members;  // world indices
+    std::vector<int32_t> tiled;    // the members whose tiles run first (a gathered class)
     size_t gather_off = 0, walk_off = 0, pfx_g_off = 0, pfx_w_off = 0, ctr_off = 0;
+    size_t tile_off = 0, pfx_t_off = 0, ctr_t_off = 0;
 };
 
 constexpr int kClasses[5] = {4, 8, 16, 32, 64};
@@ -107,21 +109,31 @@ knn_status ensure_streams(BatchGraph &g) {
 }
 
 // Lays out the batched-expansion table of the worlds whose plan is the
-// gathered form, fills its host copy and copies it to the device (growing the
-// device buffer), after the graph's last replay has finished with it.
+// gathered form (and, for the tiled ones among them, their tile arguments and
+// tile-count prefix), fills its host copy and copies it to the device
+// (growing the device buffer), after the graph's last replay has finished
+// with it.
 knn_status build_expand_table(BatchGraph &g, int32_t n_worlds, const knn_world *worlds,
                               const knn_tick_args *args, const std::vector<knnq::Plan> &plans,
-                              std::vector<ExpandClass> &classes, std::vector<char> &batched) {
+                              std::vector<ExpandClass> &classes, std::vector<char> &batched,
+                              std::vector<char> &tiled) {
     classes.clear();
     batched.assign(n_worlds, 0);
+    tiled.assign(n_worlds, 0);
     ExpandClass by[10];  // gathered form by list size, then the packet walk by list size
     for (int32_t i = 0; i < n_worlds; ++i) {
         const knnq::Plan &p = plans[i];
         if (p.wide || p.iterative || args[i].n_q <= 0) continue;
         batched[i] = 1;
-        by[(p.gather ? 0 : 5) + class_of(args[i].k)].members.push_back(i);
+        ExpandClass &e = by[(p.gather ? 0 : 5) + class_of(args[i].k)];
+        e.members.push_back(i);
+        if (p.gather && p.tile && args[i].q_x_dev == nullptr) {
+            tiled[i] = 1;
+            e.tiled.push_back(i);
+        }
     }
     const size_t gsz = knnq::gather_batch_entry_bytes(), wsz = knnq::walk_batch_entry_bytes();
+    const size_t tsz = knnq::tile_batch_entry_bytes();
     size_t off = 0;
     for (int c = 0; c < 10; ++c) {
         ExpandClass &e = by[c];
@@ -139,6 +151,15 @@ knn_status build_expand_table(BatchGraph &g, int32_t n_worlds, const knn_world *
         off = align16(off + (n + 1) * sizeof(long long));
         e.ctr_off = off;
         off = align16(off + 2 * sizeof(unsigned long long));
+        if (!e.tiled.empty()) {
+            const size_t nt = e.tiled.size();
+            e.tile_off = off;
+            off = align16(off + nt * tsz);
+            e.pfx_t_off = off;
+            off = align16(off + (nt + 1) * sizeof(long long));
+            e.ctr_t_off = off;
+            off = align16(off + sizeof(unsigned long long));
+        }
         classes.push_back(e);
     }
     if (classes.empty()) return KNN_OK;
@@ -153,6 +174,15 @@ knn_status build_expand_table(BatchGraph &g, int32_t n_worlds, const knn_world *
             knnq::walk_batch_entry(w, plans[i], args[i], !e.walk,
                                    g.host.data() + e.walk_off + j * wsz);
         }
+        long long *pfx = reinterpret_cast<long long *>(g.host.data() + e.pfx_t_off);
+        long long acc = 0;
+        for (size_t j = 0; j < e.tiled.size(); ++j) {
+            const int32_t i = e.tiled[j];
+            pfx[j] = acc;
+            acc += knnq::tile_batch_entry(worlds[i]->w, plans[i], args[i],
+                                          g.host.data() + e.tile_off + j * tsz);
+        }
+        if (!e.tiled.empty()) pfx[e.tiled.size()] = acc;
     }
     if (g.pending && cudaEventSynchronize(g.done) != cudaSuccess)
         return bad(KNN_ERR_CUDA, "knn_batch_tick: waiting for the last batch failed");
@@ -212,7 +242,7 @@ extern "C" knn_status knn_batch_tick(int32_t n_worlds, const knn_world *worlds,
         const knnq::Plan p = knnq::plan_for(worlds[i]->w, args[i].n_q, args[i].k);
         plans.push_back(p);
         const knnq::World &wi = worlds[i]->w;
-        shape.insert(shape.end(), {p.th, p.G, p.Gp, (int)p.wide, (int)p.gather,
+        shape.insert(shape.end(), {p.th, p.G, p.Gp, (int)p.wide, (int)p.gather, (int)p.tile,
                                    args[i].n_upd > 0, args[i].q_x_dev != nullptr,
                                    args[i].n_q > 0, (int)(wi.uid & 0x7fffffffu),
                                    (int)(wi.uid >> 31), (int)wi.scratch_gen});
@@ -227,8 +257,8 @@ extern "C" knn_status knn_batch_tick(int32_t n_worlds, const knn_world *worlds,
         g.worlds.clear();
         g.shape.clear();
         std::vector<ExpandClass> classes;
-        std::vector<char> batched;
-        st = build_expand_table(g, n_worlds, worlds, args, plans, classes, batched);
+        std::vector<char> batched, tiled;
+        st = build_expand_table(g, n_worlds, worlds, args, plans, classes, batched, tiled);
         if (st != KNN_OK) return st;
         cudaGraph_t graph = nullptr;
         cudaStream_t origin = g.streams[0];
@@ -262,7 +292,8 @@ extern "C" knn_status knn_batch_tick(int32_t n_worlds, const knn_world *worlds,
             const size_t c = corder[r];
             const ExpandClass &x = classes[c];
             for (int32_t i : x.members)
-                knnq::enqueue_tick(worlds[i]->w, args[i], g.streams[pos++ % ns], false, false);
+                knnq::enqueue_tick(worlds[i]->w, args[i], g.streams[pos++ % ns], false, false,
+                                   tiled[i] != 0);
             cudaStream_t cs = g.cstreams[r];
             for (int i = 0; i < ns; ++i) {
                 cudaEventRecord(g.cls_done[r][i], g.streams[i]);
@@ -270,6 +301,15 @@ extern "C" knn_status knn_batch_tick(int32_t n_worlds, const knn_world *worlds,
             }
             const int n = (int)x.members.size();
             unsigned long long *ctr = reinterpret_cast<unsigned long long *>(tb + x.ctr_off);
+            if (!x.tiled.empty()) {
+                // the tiles of the class's tiled worlds; what they pass on joins
+                // those worlds' packet lists for the gathered grid
+                knnq::launch_tile_batch(
+                    x.kc, tb + x.tile_off, (int)x.tiled.size(),
+                    reinterpret_cast<const long long *>(tb + x.pfx_t_off),
+                    reinterpret_cast<unsigned long long *>(tb + x.ctr_t_off), dev, cs);
+                batch_launches += 1;
+            }
             if (!x.walk) {
                 knnq::launch_gather_batch(x.kc, tb + x.gather_off, n,
                                           reinterpret_cast<long long *>(tb + x.pfx_g_off), ctr,

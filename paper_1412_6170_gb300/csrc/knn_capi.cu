@@ -417,7 +417,8 @@ knn_status check_tick_args(const World &w, const knn_tick_args &a, const char *w
 }
 
 // The stages of one tick, in order, on stream s (no synchronisation, no allocation).
-void enqueue_tick(World &w, const knn_tick_args &a, cudaStream_t s, bool marks, bool expand) {
+void enqueue_tick(World &w, const knn_tick_args &a, cudaStream_t s, bool marks, bool expand,
+                  bool batch_tiles) {
     const Plan p = make_plan(w, a.n_q, a.k);
     const bool m = marks && w.profiling;
     launch_tick_begin(w, p, s);
@@ -450,7 +451,7 @@ void enqueue_tick(World &w, const knn_tick_args &a, cudaStream_t s, bool marks, 
     if (m) mark(w, 4, s);
     // the tiled form takes the level-Gp cells of the sorted queries directly
     // and cuts packets only for what it passes on
-    const bool tile = p.tile && expand && a.q_x_dev == nullptr;
+    const bool tile = p.tile && (expand || batch_tiles) && a.q_x_dev == nullptr;
     if (a.n_q > 0 && !p.wide && !p.iterative) {
         if (tile) launch_query_cells(w, p, a.n_q, s);
         else launch_packets(w, p, a.n_q, s);

@@ -82,7 +82,11 @@ struct TileArgs {
 // its object count, and per cell the first query, the query count and the
 // packets before it.
 struct TileMeta {
-    int64_t t;                      // ticket (>= the tile count: no tile left)
+    int64_t t;                      // the tile within its world
+    int32_t valid;                  // 0: no tile left
+    int32_t as;                     // which world-argument slot (batched form)
+    int64_t w;                      // its world (batched form)
+    int32_t nv, m, T;               // the world's valid queries, leaves, cells per tile
     int32_t qa, qb, cnt;            // sorted queries [qa, qb); objects in its cells
     int32_t cq[kTileMaxCells];      // the tile's cells: first sorted query,
     int32_t cn[kTileMaxCells];      // query count
@@ -475,14 +479,10 @@ __device__ __forceinline__ int32_t clamp_leaf(int32_t b, int32_t m) {
     return b < 0 ? 0 : (b > m ? m : b);
 }
 
-}  // namespace
-
-template <int KC>
-__global__ void __launch_bounds__(kTileThreads, KC <= 16 ? 4 : 2)
-    k_expand_tile(const TileArgs g) {
-    __shared__ TileSmem s;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const float kInf = __int_as_float(0x7f800000);
+// (one thread) the metadata of tile t of world g: the tile's level-G cells
+// are consecutive in the cell map; its packets are each cell's queries 32 at
+// a time
+__device__ __forceinline__ void meta_fill(const TileArgs &g, TileMeta &M, int64_t t) {
     int32_t nv = g.scalars[kScalarValidQueries];
     nv = nv < 0 ? 0 : (nv > g.n_q ? (int32_t)g.n_q : nv);
     int32_t m = g.scalars[kScalarLeaves];
@@ -490,277 +490,368 @@ __global__ void __launch_bounds__(kTileThreads, KC <= 16 ? 4 : 2)
     const int T = g.tcells;
     const int64_t ntiles = (1ll << (2 * g.Gp)) / T;
     const int dsh = 2 * (g.G - g.Gp);
+    M.t = t;
+    M.valid = t >= 0 && t < ntiles;
+    M.nv = nv;
+    M.m = m;
+    M.T = T;
+    M.qa = M.qb = M.cnt = 0;
+    M.pp[T] = 0;
+    if (!M.valid) return;
+    const int64_t c0 = t * T;
+    int32_t qa = g.qcs[c0], qb = g.qcs[c0 + T];
+    qa = qa < 0 ? 0 : (qa > nv ? nv : qa);
+    qb = qb < qa ? qa : (qb > nv ? nv : qb);
+    M.qa = qa;
+    M.qb = qb;
+    if (qb == qa) return;
+    const int32_t la = clamp_leaf(g.cb[c0 << dsh], m);
+    const int32_t lb = clamp_leaf(g.cb[(c0 + T) << dsh], m);
+    M.cnt = g.bstart[lb] - g.bstart[la];
+    int32_t acc = 0, af = 0, ap = 0;
+    for (int i = 0; i < T; ++i) {
+        int32_t a = g.qcs[c0 + i], b = g.qcs[c0 + i + 1];
+        a = a < qa ? qa : (a > qb ? qb : a);
+        b = b < a ? a : (b > qb ? qb : b);
+        M.cq[i] = a;
+        M.cn[i] = b - a;
+        M.pp[i] = acc;
+        M.pf[i] = af;
+        M.ppart[i] = ap;
+        acc += (b - a + 31) >> 5;
+        af += (b - a) >> 5;
+        ap += ((b - a) & 31) != 0 ? 1 : 0;
+    }
+    M.pp[T] = acc;
+    M.pf[T] = af;
+    M.ppart[T] = ap;
+}
+
+}  // namespace
+
+// One tile of world g (its metadata M, already loaded): query box, margin,
+// staging, then the packets; `prefetch` (called by every thread once, while
+// no thread reads the other metadata slot) starts loading the next tile.
+template <int KC, class Prefetch>
+__device__ __forceinline__ void tile_body(const TileArgs &g, TileSmem &s, const TileMeta &M,
+                                          const Prefetch &prefetch) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const float kInf = __int_as_float(0x7f800000);
+    const int T = M.T;
+    const int32_t m = M.m;
     const float cside = ldexpf(g.side, -g.Gp);
-    // (thread 0) the next tile's ticket and metadata into meta[slot]: the
-    // tile's level-G cells are consecutive in the cell map; its packets are
-    // each cell's queries 32 at a time
-    auto load_meta = [&](int slot) {
-        TileMeta &M = s.meta[slot];
-        M.t = atomicAdd(g.tile_counter, 1u);
-        if (M.t >= ntiles) return;
-        const int64_t c0 = M.t * T;
-        int32_t qa = g.qcs[c0], qb = g.qcs[c0 + T];
-        qa = qa < 0 ? 0 : (qa > nv ? nv : qa);
-        qb = qb < qa ? qa : (qb > nv ? nv : qb);
-        M.qa = qa;
-        M.qb = qb;
-        M.cnt = 0;
-        if (qb == qa) return;
-        const int32_t la = clamp_leaf(g.cb[c0 << dsh], m);
-        const int32_t lb = clamp_leaf(g.cb[(c0 + T) << dsh], m);
-        M.cnt = g.bstart[lb] - g.bstart[la];
-        int32_t acc = 0, af = 0, ap = 0;
-        for (int i = 0; i < T; ++i) {
-            int32_t a = g.qcs[c0 + i], b = g.qcs[c0 + i + 1];
-            a = a < qa ? qa : (a > qb ? qb : a);
-            b = b < a ? a : (b > qb ? qb : b);
-            M.cq[i] = a;
-            M.cn[i] = b - a;
-            M.pp[i] = acc;
-            M.pf[i] = af;
-            M.ppart[i] = ap;
-            acc += (b - a + 31) >> 5;
-            af += (b - a) >> 5;
-            ap += ((b - a) & 31) != 0 ? 1 : 0;
-        }
-        M.pp[T] = acc;
-        M.pf[T] = af;
-        M.ppart[T] = ap;
-    };
+    const int32_t qa = M.qa, qb = M.qb, nq = qb - qa, npk = M.pp[T];
+    if (nq == 0) {
+        __syncthreads();  // every thread has read M
+        prefetch();
+        return;
+    }
+    // a tile that cannot be staged (too many objects or queries) goes on
+    // at once
+    const bool early_ok = nq <= kTileMaxQ && M.cnt > 0 && M.cnt <= kTileObj;
     if (tid == 0) {
+        s.rho = (float)M.cnt / ((float)T * cside * cside);
+        s.ok = 0;
+        s.next_pk = 0;
+    }
+
+    // the tile's query box
+    float bx0 = kInf, bx1 = -kInf, by0 = kInf, by1 = -kInf;
+    for (int32_t q = qa + tid; early_ok && q < qb; q += kTileThreads) {
+        const float x = g.qs_x[q], y = g.qs_y[q];
+        bx0 = fminf(bx0, x);
+        bx1 = fmaxf(bx1, x);
+        by0 = fminf(by0, y);
+        by1 = fmaxf(by1, y);
+    }
+    bx0 = warp_min(bx0);
+    bx1 = warp_max(bx1);
+    by0 = warp_min(by0);
+    by1 = warp_max(by1);
+    if (lane == 0) {
+        s.red[0][wid] = bx0;
+        s.red[1][wid] = bx1;
+        s.red[2][wid] = by0;
+        s.red[3][wid] = by1;
+    }
+    __syncthreads();
+    if (tid == 0 && early_ok) {
+        for (int w = 1; w < kTileWarps; ++w) {
+            bx0 = fminf(bx0, s.red[0][w]);
+            bx1 = fmaxf(bx1, s.red[1][w]);
+            by0 = fminf(by0, s.red[2][w]);
+            by1 = fmaxf(by1, s.red[3][w]);
+        }
+        int ok = bx0 <= bx1 && by0 <= by1;
+        const float rho = s.rho;
+        // the margin: a disc of twice the area the first thresholds
+        // expect at the tile's density
+        const float fk = (float)g.k;
+        const float H = __fsqrt_ru(2.f * (fk + 4.f * sqrtf(fk) + 4.f) / (3.14159265f * rho));
+        const float hx0 = __fsub_rd(bx0, H), hx1 = __fadd_ru(bx1, H);
+        const float hy0 = __fsub_rd(by0, H), hy1 = __fadd_ru(by1, H);
+        ok = ok && H > 0.f && H < kInf && hx0 < hx1 && hy0 < hy1;
+        const int gx0 = cell_g(hx0, g.x0, g.scale_g, g.G), gx1 = cell_g(hx1, g.x0, g.scale_g, g.G);
+        const int gy0 = cell_g(hy0, g.y0, g.scale_g, g.G), gy1 = cell_g(hy1, g.y0, g.scale_g, g.G);
+        const int ngx = gx1 - gx0 + 1, ngy = gy1 - gy0 + 1;
+        ok = ok && (int64_t)ngx * ngy <= kTileStage;
+        // micro-cells of about one object (kTileAspect times as high as
+        // wide), at most kTileCells
+        const float W = hx1 - hx0, Hh = hy1 - hy0;
+        float c = sqrtf(1.f / (kTileAspect * rho));
+        int nmx = 1, nmy = 1;
+        if (ok) {
+            nmx = max(1, min(kTileCells, (int)ceilf(W / c)));
+            nmy = max(1, min(kTileCells, (int)ceilf(Hh / (kTileAspect * c))));
+            if (nmx * nmy > kTileCells) {
+                c *= sqrtf((float)(nmx * nmy) / (float)kTileCells) * 1.02f;
+                nmx = max(1, min(kTileCells, (int)ceilf(W / c)));
+                nmy = max(1, min(kTileCells / nmx, (int)ceilf(Hh / (kTileAspect * c))));
+            }
+        }
+        s.ok = ok;
+        s.hx0 = hx0;
+        s.hx1 = hx1;
+        s.hy0 = hy0;
+        s.hy1 = hy1;
+        s.nmx = nmx;
+        s.nmy = nmy;
+        s.iw = (float)nmx / W;
+        s.ih = (float)nmy / Hh;
+        s.rho = rho;
+        s.ngx = ngx;
+        s.ng = ok ? ngx * ngy : 0;
+        s.gx0 = gx0;
+        s.gx1 = gx1;
+        s.gy0 = gy0;
+        s.gy1 = gy1;
+    }
+    __syncthreads();
+    int ok = s.ok;
+    const int ng = s.ng, nmx = s.nmx, nmy = s.nmy, ncells = nmx * nmy;
+    uint32_t S = 0;
+    if (ok) {
+        // staged level-G cells: counts, then their first staged index
+        int32_t cc = 0, oa = 0;
+        if (tid < ng) {
+            const int cx = s.gx0 + tid % s.ngx, cy = s.gy0 + tid / s.ngx;
+            const uint32_t mc = interleave((uint32_t)cx, (uint32_t)cy);
+            const int32_t la = clamp_leaf(g.cb[mc], m);
+            const int32_t lb = clamp_leaf(g.cb[mc + 1], m);
+            oa = g.bstart[la];
+            cc = g.bstart[lb] - oa;
+            cc = cc > 0 ? cc : 0;
+        }
+        for (int i = tid; i <= ncells; i += kTileThreads) s.cs[i] = 0;
+        const uint32_t ex = block_excl_scan_256((uint32_t)cc, s.scan_tmp, &s.scan_total);
+        if (tid < ng) {
+            s.gofs[tid] = (int32_t)ex;
+            s.goa[tid] = oa;
+        }
+        S = s.scan_total;
+        if (tid == 0) s.gofs[ng] = (int32_t)S;
+        ok = S > 0 && S <= (uint32_t)kTileObj;
+        __syncthreads();
+    }
+    if (!ok) {
+        // the tile goes to the gathered form, as the packets k_packets cuts
+        if (tid == 0) {
+            s.pk_full = atomicAdd(g.scalars + kScalarPackets, M.pf[T]);
+            s.pk_part = atomicAdd(g.scalars + kScalarPartialPackets, M.ppart[T]);
+        }
+        __syncthreads();
+        prefetch();
+        for (int32_t i = tid; i < npk; i += kTileThreads) {
+            int c = 0;
+#pragma unroll
+            for (int u = 1; u < kTileMaxCells; ++u)
+                if (u < T && i >= M.pp[u]) c = u;
+            const int32_t o = i - M.pp[c];
+            const int32_t q0 = M.cq[c] + 32 * o, ql = min(32, M.cn[c] - 32 * o);
+            const int64_t slot = ql == 32
+                                     ? (int64_t)s.pk_full + M.pf[c] + o
+                                     : g.pk_cap - 1 - ((int64_t)s.pk_part + M.ppart[c]);
+            if (slot >= 0 && slot < g.pk_cap) {
+                g.pk_start[slot] = q0;
+                g.pk_len[slot] = ql;
+            }
+        }
+        return;
+    }
+    // stage the objects: counting sort by micro-cell (row-major)
+    {
+        const float hx0 = s.hx0, hy0 = s.hy0, iw = s.iw, ih = s.ih;
+        constexpr int kPer = (kTileObj + kTileThreads) / kTileThreads;
+        float lx[kPer], ly[kPer];
+        int32_t lid[kPer], lm[kPer], lr[kPer];
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            const int si = tid + u * kTileThreads;
+            lm[u] = -1;
+            lx[u] = ly[u] = 0.f;
+            lid[u] = lr[u] = 0;
+            if (si < (int)S) {
+                int lo = 0, hi = ng - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (s.gofs[mid] <= si) lo = mid;
+                    else hi = mid - 1;
+                }
+                int64_t gi = (int64_t)s.goa[lo] + (si - s.gofs[lo]);
+                if (!KNN_IN_BOUNDS(gi, 0, g.n, g.err)) gi = 0;
+                lx[u] = g.xs[gi];
+                ly[u] = g.ys[gi];
+                lid[u] = g.sid[gi];
+                const int mc = mcell(ly[u], hy0, ih, nmy) * nmx + mcell(lx[u], hx0, iw, nmx);
+                lm[u] = mc;
+                lr[u] = atomicAdd(&s.cs[mc], 1);
+            }
+        }
+        __syncthreads();
+        // exclusive scan of the micro-cell counts, four cells per thread
+        {
+            int32_t v[4];
+            uint32_t sum = 0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = tid * 4 + u;
+                v[u] = i < ncells ? s.cs[i] : 0;
+                sum += (uint32_t)v[u];
+            }
+            uint32_t ex = block_excl_scan_256(sum, s.scan_tmp, nullptr);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = tid * 4 + u;
+                if (i < ncells) s.cs[i] = (int32_t)ex;
+                ex += (uint32_t)v[u];
+            }
+            if (tid == 0) s.cs[ncells] = (int32_t)S;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            if (lm[u] >= 0) {
+                int pos = s.cs[lm[u]] + lr[u];
+                if (!KNN_IN_BOUNDS(pos, 0, kTileObj, g.err)) pos = 0;
+                s.xy[pos] = make_float2(lx[u], ly[u]);
+                s.id[pos] = lid[u];
+            }
+        }
+        __syncthreads();
+    }
+    // the next tile's metadata (thread 0, while the other warps start on
+    // the packets), then the tile's packets, taken by the warps one at a
+    // time
+    prefetch();
+    for (;;) {
+        int32_t pw = 0;
+        if (lane == 0) pw = atomicAdd(&s.next_pk, 1);
+        pw = __shfl_sync(kFull, pw, 0);
+        if (pw >= npk) break;
+        int32_t q0, ql;
+        tile_pk(M, T, pw, q0, ql);
+        if (ql > 0) tile_packet<KC>(g, s, q0, ql, tid);
+    }
+}
+
+template <int KC>
+__global__ void __launch_bounds__(kTileThreads, KC <= 16 ? 4 : 2)
+    k_expand_tile(const TileArgs g) {
+    __shared__ TileSmem s;
+    if (threadIdx.x == 0) {
         s.mi = 0;
-        load_meta(0);
+        meta_fill(g, s.meta[0], atomicAdd(g.tile_counter, 1u));
     }
     for (;;) {
         __syncthreads();  // the last tile's staged objects are no longer read
         const int mi = s.mi;  // this tile's metadata (thread 0 fills the other slot)
         const TileMeta &M = s.meta[mi];
-        if (M.t >= ntiles) break;
-        const int32_t qa = M.qa, qb = M.qb, nq = qb - qa, npk = M.pp[T];
-        if (nq == 0) {
-            __syncthreads();  // every thread has read M
-            if (tid == 0) {
-                load_meta(mi ^ 1);
+        if (!M.valid) break;
+        tile_body<KC>(g, s, M, [&]() {
+            if (threadIdx.x == 0) {
+                meta_fill(g, s.meta[mi ^ 1], atomicAdd(g.tile_counter, 1u));
                 s.mi = mi ^ 1;
             }
-            continue;
-        }
-        // a tile that cannot be staged (too many objects or queries) goes on
-        // at once
-        const bool early_ok = nq <= kTileMaxQ && M.cnt > 0 && M.cnt <= kTileObj;
-        if (tid == 0) {
-            s.rho = (float)M.cnt / ((float)T * cside * cside);
-            s.ok = 0;
-            s.next_pk = 0;
-        }
+        });
+    }
+}
 
-        // the tile's query box
-        float bx0 = kInf, bx1 = -kInf, by0 = kInf, by1 = -kInf;
-        for (int32_t q = qa + tid; early_ok && q < qb; q += kTileThreads) {
-            const float x = g.qs_x[q], y = g.qs_y[q];
-            bx0 = fminf(bx0, x);
-            bx1 = fmaxf(bx1, x);
-            by0 = fminf(by0, y);
-            by1 = fmaxf(by1, y);
+// Batched form: one grid takes the tiles of many worlds (same list size
+// class).  pfx[w] counts the tiles of the worlds before w (from the worlds'
+// plans, on the host); a ticket's world is found by binary search, and its
+// arguments are copied into one of two shared-memory slots when the world
+// changes (the other slot may still serve the tile being scanned).
+struct TileBatch {
+    const TileArgs *worlds;
+    const long long *pfx;  // n + 1 entries
+    unsigned long long *counter;
+    int n;
+};
+static_assert(sizeof(TileArgs) % 4 == 0, "copied by 32-bit words");
+
+template <int KC>
+__global__ void __launch_bounds__(kTileThreads, KC <= 16 ? 4 : 2)
+    k_expand_tile_batch(const TileBatch b) {
+    __shared__ TileSmem s;
+    __shared__ TileArgs wa[2];
+    const long long total = b.pfx[b.n];
+    // (thread 0) the next ticket's world and tile metadata into meta[slot]
+    auto next = [&](int slot, int as_prev, int64_t w_prev) {
+        TileMeta &M = s.meta[slot];
+        const long long t = (long long)atomicAdd(b.counter, 1ull);
+        if (t >= total) {
+            M.valid = 0;
+            return;
         }
-        bx0 = warp_min(bx0);
-        bx1 = warp_max(bx1);
-        by0 = warp_min(by0);
-        by1 = warp_max(by1);
-        if (lane == 0) {
-            s.red[0][wid] = bx0;
-            s.red[1][wid] = bx1;
-            s.red[2][wid] = by0;
-            s.red[3][wid] = by1;
+        int lo = 0, hi = b.n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (b.pfx[mid] <= t) lo = mid;
+            else hi = mid - 1;
         }
-        __syncthreads();
-        if (tid == 0 && early_ok) {
-            for (int w = 1; w < kTileWarps; ++w) {
-                bx0 = fminf(bx0, s.red[0][w]);
-                bx1 = fmaxf(bx1, s.red[1][w]);
-                by0 = fminf(by0, s.red[2][w]);
-                by1 = fmaxf(by1, s.red[3][w]);
-            }
-            int ok = bx0 <= bx1 && by0 <= by1;
-            const float rho = s.rho;
-            // the margin: a disc of twice the area the first thresholds
-            // expect at the tile's density
-            const float fk = (float)g.k;
-            const float H = __fsqrt_ru(2.f * (fk + 4.f * sqrtf(fk) + 4.f) / (3.14159265f * rho));
-            const float hx0 = __fsub_rd(bx0, H), hx1 = __fadd_ru(bx1, H);
-            const float hy0 = __fsub_rd(by0, H), hy1 = __fadd_ru(by1, H);
-            ok = ok && H > 0.f && H < kInf && hx0 < hx1 && hy0 < hy1;
-            const int gx0 = cell_g(hx0, g.x0, g.scale_g, g.G), gx1 = cell_g(hx1, g.x0, g.scale_g, g.G);
-            const int gy0 = cell_g(hy0, g.y0, g.scale_g, g.G), gy1 = cell_g(hy1, g.y0, g.scale_g, g.G);
-            const int ngx = gx1 - gx0 + 1, ngy = gy1 - gy0 + 1;
-            ok = ok && (int64_t)ngx * ngy <= kTileStage;
-            // micro-cells of about one object (kTileAspect times as high as
-            // wide), at most kTileCells
-            const float W = hx1 - hx0, Hh = hy1 - hy0;
-            float c = sqrtf(1.f / (kTileAspect * rho));
-            int nmx = 1, nmy = 1;
-            if (ok) {
-                nmx = max(1, min(kTileCells, (int)ceilf(W / c)));
-                nmy = max(1, min(kTileCells, (int)ceilf(Hh / (kTileAspect * c))));
-                if (nmx * nmy > kTileCells) {
-                    c *= sqrtf((float)(nmx * nmy) / (float)kTileCells) * 1.02f;
-                    nmx = max(1, min(kTileCells, (int)ceilf(W / c)));
-                    nmy = max(1, min(kTileCells / nmx, (int)ceilf(Hh / (kTileAspect * c))));
-                }
-            }
-            s.ok = ok;
-            s.hx0 = hx0;
-            s.hx1 = hx1;
-            s.hy0 = hy0;
-            s.hy1 = hy1;
-            s.nmx = nmx;
-            s.nmy = nmy;
-            s.iw = (float)nmx / W;
-            s.ih = (float)nmy / Hh;
-            s.rho = rho;
-            s.ngx = ngx;
-            s.ng = ok ? ngx * ngy : 0;
-            s.gx0 = gx0;
-            s.gx1 = gx1;
-            s.gy0 = gy0;
-            s.gy1 = gy1;
+        int as = as_prev;
+        if (lo != w_prev) {
+            as = as_prev ^ 1;
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(b.worlds + lo);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(&wa[as]);
+            for (int i = 0; i < (int)(sizeof(TileArgs) / 4); ++i) dst[i] = src[i];
         }
-        __syncthreads();
-        int ok = s.ok;
-        const int ng = s.ng, nmx = s.nmx, nmy = s.nmy, ncells = nmx * nmy;
-        uint32_t S = 0;
-        if (ok) {
-            // staged level-G cells: counts, then their first staged index
-            int32_t cc = 0, oa = 0;
-            if (tid < ng) {
-                const int cx = s.gx0 + tid % s.ngx, cy = s.gy0 + tid / s.ngx;
-                const uint32_t mc = interleave((uint32_t)cx, (uint32_t)cy);
-                const int32_t la = clamp_leaf(g.cb[mc], m);
-                const int32_t lb = clamp_leaf(g.cb[mc + 1], m);
-                oa = g.bstart[la];
-                cc = g.bstart[lb] - oa;
-                cc = cc > 0 ? cc : 0;
-            }
-            for (int i = tid; i <= ncells; i += kTileThreads) s.cs[i] = 0;
-            const uint32_t ex = block_excl_scan_256((uint32_t)cc, s.scan_tmp, &s.scan_total);
-            if (tid < ng) {
-                s.gofs[tid] = (int32_t)ex;
-                s.goa[tid] = oa;
-            }
-            S = s.scan_total;
-            if (tid == 0) s.gofs[ng] = (int32_t)S;
-            ok = S > 0 && S <= (uint32_t)kTileObj;
-            __syncthreads();
-        }
-        if (!ok) {
-            // the tile goes to the gathered form, as the packets k_packets cuts
-            if (tid == 0) {
-                s.pk_full = atomicAdd(g.scalars + kScalarPackets, M.pf[T]);
-                s.pk_part = atomicAdd(g.scalars + kScalarPartialPackets, M.ppart[T]);
-            }
-            __syncthreads();
-            if (tid == 0) {
-                load_meta(mi ^ 1);
+        meta_fill(wa[as], M, t - b.pfx[lo]);
+        M.as = as;
+        M.w = lo;
+    };
+    if (threadIdx.x == 0) {
+        s.mi = 0;
+        next(0, 1, -1);
+    }
+    for (;;) {
+        __syncthreads();  // the last tile's staged objects are no longer read
+        const int mi = s.mi;
+        const TileMeta &M = s.meta[mi];
+        if (!M.valid) break;
+        tile_body<KC>(wa[M.as], s, M, [&]() {
+            if (threadIdx.x == 0) {
+                next(mi ^ 1, M.as, M.w);
                 s.mi = mi ^ 1;
             }
-            for (int32_t i = tid; i < npk; i += kTileThreads) {
-                int c = 0;
-#pragma unroll
-                for (int u = 1; u < kTileMaxCells; ++u)
-                    if (u < T && i >= M.pp[u]) c = u;
-                const int32_t o = i - M.pp[c];
-                const int32_t q0 = M.cq[c] + 32 * o, ql = min(32, M.cn[c] - 32 * o);
-                const int64_t slot = ql == 32
-                                         ? (int64_t)s.pk_full + M.pf[c] + o
-                                         : g.pk_cap - 1 - ((int64_t)s.pk_part + M.ppart[c]);
-                if (slot >= 0 && slot < g.pk_cap) {
-                    g.pk_start[slot] = q0;
-                    g.pk_len[slot] = ql;
-                }
-            }
-            continue;
-        }
-        // stage the objects: counting sort by micro-cell (row-major)
-        {
-            const float hx0 = s.hx0, hy0 = s.hy0, iw = s.iw, ih = s.ih;
-            constexpr int kPer = (kTileObj + kTileThreads) / kTileThreads;
-            float lx[kPer], ly[kPer];
-            int32_t lid[kPer], lm[kPer], lr[kPer];
-#pragma unroll
-            for (int u = 0; u < kPer; ++u) {
-                const int si = tid + u * kTileThreads;
-                lm[u] = -1;
-                lx[u] = ly[u] = 0.f;
-                lid[u] = lr[u] = 0;
-                if (si < (int)S) {
-                    int lo = 0, hi = ng - 1;
-                    while (lo < hi) {
-                        const int mid = (lo + hi + 1) >> 1;
-                        if (s.gofs[mid] <= si) lo = mid;
-                        else hi = mid - 1;
-                    }
-                    int64_t gi = (int64_t)s.goa[lo] + (si - s.gofs[lo]);
-                    if (!KNN_IN_BOUNDS(gi, 0, g.n, g.err)) gi = 0;
-                    lx[u] = g.xs[gi];
-                    ly[u] = g.ys[gi];
-                    lid[u] = g.sid[gi];
-                    const int mc = mcell(ly[u], hy0, ih, nmy) * nmx + mcell(lx[u], hx0, iw, nmx);
-                    lm[u] = mc;
-                    lr[u] = atomicAdd(&s.cs[mc], 1);
-                }
-            }
-            __syncthreads();
-            // exclusive scan of the micro-cell counts, four cells per thread
-            {
-                int32_t v[4];
-                uint32_t sum = 0;
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int i = tid * 4 + u;
-                    v[u] = i < ncells ? s.cs[i] : 0;
-                    sum += (uint32_t)v[u];
-                }
-                uint32_t ex = block_excl_scan_256(sum, s.scan_tmp, nullptr);
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int i = tid * 4 + u;
-                    if (i < ncells) s.cs[i] = (int32_t)ex;
-                    ex += (uint32_t)v[u];
-                }
-                if (tid == 0) s.cs[ncells] = (int32_t)S;
-            }
-            __syncthreads();
-#pragma unroll
-            for (int u = 0; u < kPer; ++u) {
-                if (lm[u] >= 0) {
-                    int pos = s.cs[lm[u]] + lr[u];
-                    if (!KNN_IN_BOUNDS(pos, 0, kTileObj, g.err)) pos = 0;
-                    s.xy[pos] = make_float2(lx[u], ly[u]);
-                    s.id[pos] = lid[u];
-                }
-            }
-            __syncthreads();
-        }
-        // the next tile's metadata (thread 0, while the other warps start on
-        // the packets), then the tile's packets, taken by the warps one at a
-        // time
-        if (tid == 0) {
-            load_meta(mi ^ 1);
-            s.mi = mi ^ 1;
-        }
-        for (;;) {
-            int32_t pw = 0;
-            if (lane == 0) pw = atomicAdd(&s.next_pk, 1);
-            pw = __shfl_sync(kFull, pw, 0);
-            if (pw >= npk) break;
-            int32_t q0, ql;
-            tile_pk(M, T, pw, q0, ql);
-            if (ql > 0) tile_packet<KC>(g, s, q0, ql, tid);
-        }
+        });
     }
 }
 
 namespace {
+
+template <int KC>
+int tile_batch_blocks_per_sm(int device) {
+    static int cached[64] = {0};
+    const int slot = device >= 0 && device < 64 ? device : 0;
+    if (cached[slot] == 0) {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_expand_tile_batch<KC>,
+                                                      kTileThreads, 0);
+        cached[slot] = per_sm < 1 ? 1 : per_sm;
+    }
+    return cached[slot];
+}
 
 template <int KC>
 int tile_blocks_per_sm(int device) {
@@ -786,11 +877,13 @@ void prepare_expand_tile(int device) {
     tile_blocks_per_sm<8>(device);
     tile_blocks_per_sm<16>(device);
     tile_blocks_per_sm<32>(device);
+    tile_batch_blocks_per_sm<8>(device);
+    tile_batch_blocks_per_sm<16>(device);
+    tile_batch_blocks_per_sm<32>(device);
 }
 
-void launch_expand_tile(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t *out_ids,
-                        float *out_d2, const int32_t *q_k, cudaStream_t s) {
-    if (n_q <= 0) return;
+static TileArgs tile_args(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t *out_ids,
+                          float *out_d2, const int32_t *q_k) {
     TileArgs a;
     a.xs = w.xs;
     a.ys = w.ys;
@@ -828,10 +921,46 @@ void launch_expand_tile(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t
     a.n_q = n_q;
     a.pk_cap = packet_capacity(w);
     a.leaf_cap = w.leaf_cap;
+    return a;
+}
+
+void launch_expand_tile(World &w, const Plan &p, int32_t k, int64_t n_q, int32_t *out_ids,
+                        float *out_d2, const int32_t *q_k, cudaStream_t s) {
+    if (n_q <= 0) return;
+    const TileArgs a = tile_args(w, p, k, n_q, out_ids, out_d2, q_k);
     if (k <= 8) run_tile<8>(a, w.device, s);
     else if (k <= 16) run_tile<16>(a, w.device, s);
     else run_tile<32>(a, w.device, s);
     ++w.launches;
+}
+
+// ---------------------------------------------------------------------------
+// Batched tiles (many worlds, one grid per list size)
+
+size_t tile_batch_entry_bytes() { return sizeof(TileArgs); }
+
+int64_t tile_batch_entry(World &w, const Plan &p, const knn_tick_args &t, void *dst) {
+    const TileArgs a = tile_args(w, p, t.k, t.n_q, t.out_ids_dev, t.out_d2_dev, t.q_k_dev);
+    std::memcpy(dst, &a, sizeof(a));
+    return (1ll << (2 * p.Gp)) / a.tcells;
+}
+
+namespace {
+template <int KC>
+void run_tile_batch(const TileBatch &b, int device, cudaStream_t s) {
+    const int per_sm = tile_batch_blocks_per_sm<KC>(device);
+    k_expand_tile_batch<KC><<<num_sms(device) * per_sm, kTileThreads, 0, s>>>(b);
+}
+}  // namespace
+
+void launch_tile_batch(int kc, const void *table, int n, const long long *pfx,
+                       unsigned long long *counter, int device, cudaStream_t s) {
+    if (n <= 0) return;
+    cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
+    const TileBatch b{static_cast<const TileArgs *>(table), pfx, counter, n};
+    if (kc <= 8) run_tile_batch<8>(b, device, s);
+    else if (kc <= 16) run_tile_batch<16>(b, device, s);
+    else run_tile_batch<32>(b, device, s);
 }
 
 }  // namespace knnq

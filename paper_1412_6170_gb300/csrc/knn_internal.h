@@ -273,6 +273,16 @@ size_t gather_batch_entry_bytes();
 void gather_batch_entry(World &w, const Plan &p, const knn_tick_args &t, void *dst);
 void launch_gather_batch(int kc, const void *table, int n, long long *pfx,
                          unsigned long long *counter, int device, cudaStream_t s);
+// The tiled form over many worlds (queries at their issuers, k <= 32): the
+// worlds' tile arguments, their tile counts as a prefix (pfx, n + 1 entries,
+// filled on the host: a world's tile count follows from its plan), and one
+// grid per list size that takes tiles of every world; what the tiles pass on
+// goes to each world's packet list, for the batched gathered form.
+size_t tile_batch_entry_bytes();
+// Fills dst with the world's tile arguments; returns its tile count.
+int64_t tile_batch_entry(World &w, const Plan &p, const knn_tick_args &t, void *dst);
+void launch_tile_batch(int kc, const void *table, int n, const long long *pfx,
+                       unsigned long long *counter, int device, cudaStream_t s);
 size_t walk_batch_entry_bytes();
 // handed_back: the entry covers the packets the gathered form handed back
 // (else the world's own packet list, for worlds on the packet walk)
@@ -307,9 +317,10 @@ void set_last_error(const char *msg);
 knn_status check_tick_args(const World &w, const knn_tick_args &a, const char *who);
 // Enqueue every stage of one tick on s; `marks` records stage events when
 // the world's profiling is on.  expand == false stops after the packets are
-// cut (a batch expands them).
+// cut (a batch expands them), or, with batch_tiles, after the query cells of
+// the tiled form (a batch runs its tiles).
 void enqueue_tick(World &w, const knn_tick_args &a, cudaStream_t s, bool marks,
-                  bool expand = true);
+                  bool expand = true, bool batch_tiles = false);
 // One tick through the world's graph cache when graphs are on (else direct).
 knn_status tick_launch(World &w, const knn_tick_args &a, cudaStream_t s);
 // The index / expansion parameters a tick with n_q queries and this k uses.
