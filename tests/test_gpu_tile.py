@@ -164,3 +164,53 @@ def test_tile_headline_size_sampled_rows():
                             what="1M uniform k=16")
     for info in infos:
         assert passed_on(info) <= 1_000_000 // 32 // 50, info
+
+
+def test_tile_batch_every_row_and_tiles_used():
+    # knn_batch_tick over worlds of several sizes and list sizes, uniform and
+    # clustered, one with explicit centres (no tiles): every row against the
+    # oracle, twice (the second call replays the recorded batch); the uniform
+    # worlds' tiles finish nearly all their packets (the batched tile grid ran)
+    torch, dev = torch_dev()
+    specs = [(3_000, 4, "u"), (20_000, 8, "u"), (60_000, 16, "u"), (45_000, 32, "u"),
+             (30_000, 16, "c"), (25_000, 12, "u"), (15_000, 16, "x")]
+    worlds, bufs, pos = [], [], []
+    try:
+        for si, (n, k, kind) in enumerate(specs):
+            if kind == "c":
+                x, y = synth.clustered_positions(n, seed=60 + si)
+            else:
+                x, y = synth.uniform_positions(n, seed=60 + si)
+            worlds.append(knnq.World(to_dev(x), to_dev(y), k_max=32, max_queries=n))
+            q = np.arange(n, dtype=np.int32)
+            b = {"q": to_dev(q),
+                 "oi": torch.empty((n, k), dtype=torch.int32, device=dev),
+                 "od": torch.empty((n, k), dtype=torch.float32, device=dev)}
+            if kind == "x":  # explicit centres, shifted off the issuers
+                b["qx"] = to_dev((x + np.float32(1e-4)).astype(np.float32))
+                b["qy"] = to_dev(y)
+            bufs.append(b)
+            pos.append((x, y, k, kind))
+        args = [knnq.tick_args(p[2], b["q"], q_x=b.get("qx"), q_y=b.get("qy"), out_ids=b["oi"],
+                               out_d2=b["od"]) for b, p in zip(bufs, pos)]
+        s = torch.cuda.current_stream().cuda_stream
+        for call in range(2):
+            for b in bufs:
+                b["oi"].fill_(-7)
+            knnq.knn_batch_tick([w.handle for w in worlds], args, s)
+            torch.cuda.synchronize()
+            for i, ((x, y, k, kind), b, w) in enumerate(zip(pos, bufs, worlds)):
+                q = b["q"].cpu().numpy()
+                if kind == "x":
+                    qx, qy = b["qx"].cpu().numpy(), b["qy"].cpu().numpy()
+                    rid, rd2, _ = oracle.knn(x, y, q, k, qx, qy)
+                else:
+                    rid, rd2, _ = oracle.knn(x, y, q, k)
+                assert_rows_equal(b["oi"].cpu().numpy(), b["od"].cpu().numpy(), rid, rd2,
+                                  what=f"world {i} ({kind}, k={k}) call {call}")
+                if kind == "u":
+                    assert passed_on(w.expand_info()) <= q.shape[0] // 32 // 10, (i, w.expand_info())
+                assert w.status()[0] == knnq.KNN_OK
+    finally:
+        for w in worlds:
+            w.close()
