@@ -1,17 +1,20 @@
 // a7 + a8, tiled form -- per-query expansion with top-k and the covered-disc
 // check, and the rows in caller order (Sections 4.2.1-4.2.2, Alg. 1).
 //
-// One block serves one level-Gp cell of the sorted queries (a tile; queries
-// at their issuers only).  The block first stages, once for all of the tile's
-// queries, every object of the level-G cells within a margin H of the tile's
-// queries (the paper's per-cell shared scan of Alg. 1, with the neighbouring
-// cells' objects brought in once per cell instead of once per query): the
-// objects are counting-sorted in shared memory into a row-major grid of
-// micro-cells of about one object each.  Then every lane (one query) scans
-// only its own search box, one micro-cell row at a time, its own row first
-// and then alternately the rows above and below (near objects first), and
-// shrinks the box whenever its threshold tightens (Alg. 1's "keep only what
-// is closer than dist_k").
+// A persistent grid of blocks takes tiles by ticket: a tile is one or two
+// consecutive level-Gp cells of the sorted queries (queries at their issuers
+// only).  The block first stages, once for all of the tile's queries, every
+// object of the level-G cells within a margin H of the tile's queries (the
+// paper's per-cell shared scan of Alg. 1, with the neighbouring cells' objects
+// brought in once per tile instead of once per query): the objects are
+// counting-sorted in shared memory into a row-major grid of micro-cells of
+// about one object each.  Then the warps take the tile's packets of 32
+// queries, and every lane (one query) scans only its own search box, one
+// micro-cell row at a time, its own row first and then alternately the rows
+// above and below (near objects first), and shrinks the box whenever its
+// threshold tightens (Alg. 1's "keep only what is closer than dist_k").  One
+// thread loads the next tile's metadata while the packets are scanned.  The
+// batched form runs the same per-tile work over the tiles of many worlds.
 //
 // Selection keys are 32-bit: (code of d^2 << 11) | (staged index + 1), where
 // the code is floor(d^2 * 2^21 / t) for the lane's first threshold t, so the
@@ -19,11 +22,13 @@
 // is monotone in d^2, so the 32-bit order is the (d^2, id) order wherever the
 // codes differ.  A lane is exact when the codes of its k keys are distinct
 // and the smallest code it dropped is above its k-th: then its keys are the k
-// nearest by (d^2, id) and in order.  Equal codes (ties or near-ties of d^2),
-// a lane that still holds fewer than k keys after its threshold reached the
-// staged margin, and tiles whose margin holds too many objects go to the
-// gathered form as packets of up to 32 consecutive queries (the packets
-// k_packets would cut), which finishes them exactly.
+// nearest by (d^2, id) and in order.  Equal codes (ties or near-ties of d^2)
+// are settled by exact (d^2, id) keys recomputed from the staged positions;
+// what that cannot settle (two dropped keys with the k-th code), a lane that
+// still holds fewer than k keys after its threshold reached the staged margin,
+// and tiles whose margin holds too many objects go to the gathered form as
+// packets of up to 32 consecutive queries (the packets k_packets would cut),
+// which finishes them exactly.
 //
 // Exactness of the box: every object within a lane's threshold lies in its
 // box (the box bounds round outward), every object of the box is staged, and
